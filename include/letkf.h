@@ -1,0 +1,209 @@
+/*
+ * letkf.h -- C ABI of the single-GPU LBM-LETKF hot path (sm_103a).
+ *
+ * One handle holds one data-assimilation experiment of the paper's OSSE
+ * (Sec. V): an ensemble of k D2Q9 lattice-Boltzmann members on a periodic
+ * nx x ny grid (Sec. II-A), a static observation network with diagonal
+ * observation-error covariance R, and an R-localized LETKF analysis solved
+ * independently at every grid point (Sec. II-B, Algorithm 1).
+ *
+ * Conventions shared by every entry point
+ *   - Return value: LETKF_OK (0) or a negative LETKF_E* code.  No entry
+ *     point aborts, throws or exits; letkf_strerror() names a code.
+ *   - Kernels run asynchronously on the handle's stream.  Errors found on
+ *     the device (non-convergence, non-finite output) are latched in a
+ *     status word and returned by the next letkf_sync().
+ *   - Host pointers passed in are only read/written during the call;
+ *     device pointers must stay valid until the stream passes that point.
+ *   - Populations are indexed q = 3 (j + 1) + (i + 1) for the lattice
+ *     velocity c_q = (i, j), (i, j) in {-1, 0, 1}^2 (Eq. 1).
+ *   - Ensemble states cross the ABI in the paper's LBM layout: FP32,
+ *     member-major structure of arrays f[m][q][y][x] (Sec. IV-A, X[m,N_v,N_x]).
+ *   - A handle is not thread safe; distinct handles are independent.
+ */
+#ifndef LETKF_H
+#define LETKF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define LETKF_OK          0
+#define LETKF_EINVAL     (-1)  /* an argument is out of range or NULL          */
+#define LETKF_ENOMEM     (-2)  /* workspace too small or device allocation failed */
+#define LETKF_ENOTCONV   (-3)  /* the eigensolver hit its iteration cap somewhere */
+#define LETKF_ENONFINITE (-4)  /* a non-finite value appeared in the analysis  */
+#define LETKF_ETIMEOUT   (-5)  /* a bounded device wait expired                */
+#define LETKF_ECUDA      (-6)  /* a CUDA runtime call failed                   */
+#define LETKF_ESTATE     (-7)  /* call not valid in the handle's current state */
+
+/* ---- enumerations ------------------------------------------------------- */
+#define LETKF_HOST    0        /* pointer argument is host memory             */
+#define LETKF_DEVICE  1        /* pointer argument is device memory           */
+
+#define LETKF_OBS_RHO 1        /* observed variable bits, output order rho,u,v */
+#define LETKF_OBS_U   2
+#define LETKF_OBS_V   4
+
+#define LETKF_LOC_NONE  0      /* G = 1 for every observation ("infinite")    */
+#define LETKF_LOC_GAUSS 1      /* G = exp(-d^2/(2 r^2)) for d^2 < cutoff^2    */
+
+#define LETKF_FP32  0          /* plain FP32 CUDA-core analysis               */
+#define LETKF_MIXED 1          /* reserved for the split-precision form       */
+
+/* ---- problem statement --------------------------------------------------
+ * Follows the paper's statement of the problem (Sec. II-B): the grid, the
+ * ensemble size M (= k), the observation operator H (observation points and
+ * observed variables), R (diagonal) and the localization (Sec. II-B,
+ * R-localization paragraph).  Host arrays are copied during letkf_init.
+ */
+typedef struct letkf_config {
+    int32_t nx, ny;            /* periodic grid, N_x = nx * ny points (>= 1 each)      */
+    int32_t k;                 /* ensemble size M, 2 <= k <= 128                        */
+    int32_t n_aux;             /* extra members advanced by lbm_forecast but never
+                                  analysed (e.g. the nature run), 0 <= n_aux <= 4      */
+    float   tau;               /* BGK relaxation time, > 0.5                            */
+    const float *force;        /* host [2][ny][nx]: F_x then F_y; NULL = no body force  */
+    int32_t n_obs;             /* L observation points, >= 0                            */
+    const int32_t *obs_xy;     /* host [L][2] grid coordinates (x, y), 0 <= x < nx      */
+    int32_t obs_vars;          /* LETKF_OBS_* bit mask, V = number of bits set (>= 1)   */
+    const float *obs_err_var;  /* host [L*V] diagonal of R, index l*V + v, > 0          */
+    int32_t loc_kind;          /* LETKF_LOC_*                                           */
+    float   loc_radius;        /* Gaussian radius r in cells (> 0 for LOC_GAUSS)        */
+    float   loc_cutoff2;       /* squared cutoff distance; <= 0 selects (40/3) r^2,
+                                  i.e. cutoff 2 sqrt(10/3) r                            */
+    float   infl;              /* multiplicative inflation rho: Q = (k-1)/rho I + ...;
+                                  1 = none (the paper's Eq. letkf_q)                    */
+    int32_t precision;         /* LETKF_FP32 (LETKF_MIXED is rejected for now)          */
+    int64_t chunk_bytes;       /* device bytes for the per-point k x k Gram buffer;
+                                  0 = default (64 MiB)                                  */
+    void   *stream;            /* cudaStream_t to run on; NULL = a stream the handle
+                                  creates and owns                                       */
+} letkf_config;
+
+typedef struct letkf_stats {
+    int32_t status;            /* last latched LETKF_* code (0 when clean)              */
+    int32_t n_points;          /* N_x                                                    */
+    int32_t n_zero_obs;        /* grid points with no local observation                 */
+    int32_t max_local_obs;     /* l_max: most observation points local to one point     */
+    double  mean_local_obs;    /* average observation points per grid point             */
+    int32_t n_chunks;          /* Gram/eigensolve launch pairs per analysis             */
+} letkf_stats;
+
+/* Device time of the phases of the most recent forecast and analysis (milliseconds, CUDA
+ * events on the handle's stream), the breakdown of Fig. 3 of the paper for one GPU. */
+typedef struct letkf_timings {
+    float   forecast_ms;       /* all D2Q9 steps of the last forecast                   */
+    int32_t forecast_steps;    /* steps (= kernel launches) in it                       */
+    float   obs_ms;            /* observation operator                                   */
+    float   transpose_in_ms;   /* member-major -> grid-point-major                       */
+    float   gram_ms;           /* localized Gram + innovation projection, all chunks     */
+    float   eigen_ms;          /* eigensolve + transform + update, all chunks            */
+    float   transpose_out_ms;  /* grid-point-major -> member-major                       */
+    int32_t n_chunks;          /* Gram/eigensolve launch pairs                           */
+} letkf_timings;
+
+typedef struct letkf_handle letkf_handle;
+
+/* Per-point intermediates of one analysis, for checking (all host, may be NULL). */
+typedef struct letkf_probe {
+    int32_t n_points;          /* sampled points                                        */
+    const int32_t *points;     /* [n_points] linear grid index y*nx + x                 */
+    int32_t *nloc;             /* [n_points] local observation points                   */
+    float   *gram;             /* [n_points][k][k] dY^T R_loc^-1 dY (Eq. letkf_q)        */
+    float   *cvec;             /* [n_points][k]    dY^T R_loc^-1 (yo - ybar) (Eq. letkf_wa) */
+    float   *eigval;           /* [n_points][k]    eigenvalues of Q, ascending          */
+    float   *xf;               /* [n_points][9][k] forecast block, grid-point-major     */
+} letkf_probe;
+
+/* ---- lifecycle ------------------------------------------------------------ */
+
+/* Device bytes a handle for *cfg needs (state, transposed state, observation
+ * buffers, Gram chunk).  Validates cfg; LETKF_EINVAL if it is inconsistent. */
+int letkf_workspace_size(const letkf_config *cfg, size_t *bytes);
+
+/* Create a handle on the current CUDA device.  workspace: device memory of at
+ * least letkf_workspace_size() bytes, 256-byte aligned, owned by the caller
+ * and kept alive until letkf_destroy; NULL makes the handle allocate (and
+ * free) its own.  Copies the force field, observation network and R, bins
+ * the observation points, counts local observations per grid point, and
+ * sets every member to rest (f = w_q).  *out is NULL on failure. */
+int letkf_init(const letkf_config *cfg, void *workspace, size_t workspace_bytes,
+               letkf_handle **out);
+
+/* Wait for the handle's stream, return and clear the latched device status. */
+int letkf_sync(letkf_handle *h);
+
+/* Release the handle (waits for its stream first).  NULL is accepted. */
+int letkf_destroy(letkf_handle *h);
+
+/* Static text for a status code. */
+const char *letkf_strerror(int code);
+
+/* Grid, observation and local-count figures fixed at init. */
+int letkf_get_stats(letkf_handle *h, letkf_stats *st);
+
+/* on != 0: lbm_forecast, letkf_analyze and letkf_cycle record CUDA events between their
+ * phases (cached cycle graphs are re-captured with the event records).  letkf_get_timings
+ * waits for the last recorded event and fills *t; LETKF_ESTATE if timing is off or nothing
+ * was recorded yet. */
+int letkf_enable_timing(letkf_handle *h, int32_t on);
+int letkf_get_timings(letkf_handle *h, letkf_timings *t);
+
+/* ---- state in / out ------------------------------------------------------- */
+
+/* Copy members [m0, m0+count) in or out, layout f[m][q][y][x] FP32
+ * (count*9*nx*ny floats).  Members k..k+n_aux-1 are the auxiliary ones.
+ * where = LETKF_HOST or LETKF_DEVICE.  Ordered on the handle's stream;
+ * letkf_get_state to host memory returns after the copy has landed. */
+int letkf_set_state(letkf_handle *h, const float *f, int32_t m0, int32_t count, int32_t where);
+int letkf_get_state(letkf_handle *h, float *f, int32_t m0, int32_t count, int32_t where);
+
+/* The same copies for the deviation from the rest state g_q = f_q - w_q (w_q the exact D2Q9
+ * weights 4/9, 1/9, 1/36), which is what the device stores: near rest |g| ~ 1e-3 |f|, and an
+ * FP32 f rounds away digits of the ensemble perturbations that g keeps (all of them below
+ * ~1e-8 absolute, i.e. about 1e-5 of the rest population's perturbations). */
+int letkf_set_deviation(letkf_handle *h, const float *g, int32_t m0, int32_t count, int32_t where);
+int letkf_get_deviation(letkf_handle *h, float *g, int32_t m0, int32_t count, int32_t where);
+
+/* Set members [m0, m0+count) to the D2Q9 equilibrium f^eq(rho, u) of the
+ * given macroscopic fields, each [count][ny][nx] FP32 (Sec. II-A moments). */
+int letkf_set_macro(letkf_handle *h, const float *rho, const float *ux, const float *uy,
+                    int32_t m0, int32_t count, int32_t where);
+
+/* ---- the hot path -------------------------------------------------------- */
+
+/* Advance every member (ensemble and auxiliary) by nsteps time steps of the
+ * lattice Boltzmann equation (Eq. 1): BGK collision with body force, then
+ * periodic streaming (Sec. II-A).  nsteps >= 0. */
+int lbm_forecast(letkf_handle *h, int32_t nsteps);
+
+/* Forecast observations Y^f[m][l*V+v] = h(x_m) of the ensemble members
+ * (Algorithm 1, first step), copied out as [k][L*V] FP32. */
+int letkf_get_obs(letkf_handle *h, float *yf, int32_t where);
+
+/* One LETKF analysis of the ensemble in place (Sec. II-B, Algorithm 1):
+ * observation operator and obs-space perturbations (Eqs. enkf_ybar,
+ * enkf_deltay), transpose to grid-point-major layout (Sec. IV-A), at every
+ * grid point the localized Gram matrix and innovation projection
+ * (Eqs. letkf_q, letkf_wa), the symmetric eigensolve of Q, the transform
+ * (Eqs. letkf_wa, letkf_dwa) and the update (Eq. letkf_xa), then the
+ * transpose back.  yo: [L*V] observations (where = LETKF_HOST/DEVICE). */
+int letkf_analyze(letkf_handle *h, const float *yo, int32_t where);
+
+/* letkf_analyze that also returns per-point intermediates in *probe. */
+int letkf_analyze_probe(letkf_handle *h, const float *yo, int32_t where, letkf_probe *probe);
+
+/* One data-assimilation cycle (Sec. II-B, cycle steps 2-3): lbm_forecast(nsteps)
+ * followed by letkf_analyze(yo).  The device work of a cycle is captured
+ * once per nsteps into a CUDA graph and replayed. */
+int letkf_cycle(letkf_handle *h, int32_t nsteps, const float *yo, int32_t where);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LETKF_H */

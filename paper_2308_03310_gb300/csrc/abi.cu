@@ -1,0 +1,772 @@
+// C ABI of libletkf: handle lifecycle, device workspace, and the hot-path entry points.
+//
+// Host code only; every arithmetic step of the method runs in the kernels of
+// lbm.cu, obs.cu, transpose.cu, gram.cu and eigen.cu.  The host builds the
+// static observation bins once at init and orders the launches of a cycle:
+//   lbm_forecast:   nsteps x D2Q9 step (ping-pong between two state buffers)
+//   letkf_analyze:  yo -> device, observation operator, transpose to
+//                   grid-point-major, then per chunk of grid rows the Gram
+//                   kernel and the eigensolve/transform/update kernel, then the
+//                   transpose back.
+//   letkf_cycle:    both, captured once per (nsteps, buffer parity) into a
+//                   CUDA graph and replayed.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "kernels.h"
+#include "letkf.h"
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int64_t kDefaultChunkBytes = 64ll << 20;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int kp_of(int k) { return k <= 8 ? 8 : k <= 16 ? 16 : k <= 32 ? 32 : k <= 64 ? 64 : 128; }
+
+int popcount3(int v) { return (v & 1) + ((v >> 1) & 1) + ((v >> 2) & 1); }
+
+// Everything derived from the configuration that fixes sizes.
+struct Plan {
+    size_t npts = 0;
+    int nmem = 0, V = 0, LV = 0, kp = 0;
+    int tile_w = 1, tile_h = 1;
+    int chunk_rows = 0;
+    size_t chunk_pts = 0;
+    int cs = 8, ncx = 1, ncy = 1;
+    int d2max = 0, cr = 0;
+    float inv2r2 = 0.0f;
+    // byte offsets inside the workspace
+    size_t off_state[2], off_force, off_xg, off_obs_xy, off_cell_start, off_cell_obs, off_rinv,
+        off_yf, off_yb, off_ybar, off_yo, off_gram, off_cvec, off_nloc, off_nloc_all, off_eigval,
+        off_status, total;
+};
+
+int validate(const letkf_config *c) {
+    if (!c) return LETKF_EINVAL;
+    if (c->nx < 1 || c->ny < 1 || (int64_t)c->nx * c->ny > (1ll << 30)) return LETKF_EINVAL;
+    if (c->k < 2 || c->k > 128 || c->n_aux < 0 || c->n_aux > 4) return LETKF_EINVAL;
+    if (!(c->tau > 0.5f) || !isfinite(c->tau)) return LETKF_EINVAL;
+    if (c->n_obs < 0 || (c->n_obs > 0 && (!c->obs_xy || !c->obs_err_var))) return LETKF_EINVAL;
+    if (c->obs_vars < 1 || c->obs_vars > 7) return LETKF_EINVAL;
+    if (c->loc_kind != LETKF_LOC_NONE && c->loc_kind != LETKF_LOC_GAUSS) return LETKF_EINVAL;
+    if (c->loc_kind == LETKF_LOC_GAUSS && !(c->loc_radius > 0.0f && isfinite(c->loc_radius)))
+        return LETKF_EINVAL;
+    if (!(c->infl > 0.0f) || !isfinite(c->infl)) return LETKF_EINVAL;
+    if (c->precision != LETKF_FP32) return LETKF_EINVAL;
+    if (c->chunk_bytes < 0) return LETKF_EINVAL;
+    const int V = popcount3(c->obs_vars);
+    for (int l = 0; l < c->n_obs; ++l) {
+        const int x = c->obs_xy[2 * l], y = c->obs_xy[2 * l + 1];
+        if (x < 0 || x >= c->nx || y < 0 || y >= c->ny) return LETKF_EINVAL;
+        for (int v = 0; v < V; ++v) {
+            const float r = c->obs_err_var[(size_t)l * V + v];
+            if (!(r > 0.0f) || !isfinite(r)) return LETKF_EINVAL;
+        }
+    }
+    return LETKF_OK;
+}
+
+int make_plan(const letkf_config *c, Plan *p) {
+    const int rc = validate(c);
+    if (rc != LETKF_OK) return rc;
+    p->npts = (size_t)c->nx * c->ny;
+    p->nmem = c->k + c->n_aux;
+    p->V = popcount3(c->obs_vars);
+    p->LV = c->n_obs * p->V;
+    p->kp = kp_of(c->k);
+    p->tile_w = lk::gram_tile_width(p->kp);
+    p->tile_h = lk::gram_tile_height(p->kp);
+    // localization: integer threshold of the strict cutoff d^2 < c^2 (Sec. II-B)
+    if (c->loc_kind == LETKF_LOC_GAUSS) {
+        const double r = c->loc_radius;
+        const double c2 = c->loc_cutoff2 > 0.0f ? (double)c->loc_cutoff2 : 40.0 * r * r / 3.0;
+        const double lim = ceil(c2) - 1.0;
+        p->d2max = lim > 2.0e9 ? 2000000000 : (int)lim;
+        if (p->d2max < 0) p->d2max = -1;
+        int cr = (int)sqrt((double)std::max(p->d2max, 0));
+        while ((long long)(cr + 1) * (cr + 1) <= p->d2max) ++cr;
+        while (cr > 0 && (long long)cr * cr > p->d2max) --cr;
+        p->cr = p->d2max < 0 ? 0 : cr;
+        p->inv2r2 = (float)(1.0 / (2.0 * r * r));
+    }
+    // bins: smallest power-of-two edge (>= 8) whose patch of one Gram tile fits the kernel
+    const int maxc = lk::gram_max_cells();
+    for (p->cs = 8;; p->cs *= 2) {
+        p->ncx = (c->nx + p->cs - 1) / p->cs;
+        p->ncy = (c->ny + p->cs - 1) / p->cs;
+        long long bx, by;
+        if (c->loc_kind == LETKF_LOC_NONE) {
+            bx = p->ncx;
+            by = p->ncy;
+        } else {
+            bx = std::min<long long>(p->ncx, (p->tile_w + 2 * p->cr + p->cs - 1) / p->cs + 2);
+            by = std::min<long long>(p->ncy, (p->tile_h + 2 * p->cr + p->cs - 1) / p->cs + 2);
+        }
+        if (bx * by <= maxc) break;
+    }
+    // Gram chunk: whole multiples of the tile height, within chunk_bytes
+    const int64_t budget = c->chunk_bytes > 0 ? c->chunk_bytes : kDefaultChunkBytes;
+    const size_t row_bytes = (size_t)c->nx * c->k * c->k * sizeof(float);
+    int rows = (int)std::max<int64_t>(1, budget / (int64_t)row_bytes);
+    rows = std::max(p->tile_h, rows / p->tile_h * p->tile_h);
+    if (rows >= c->ny) rows = c->ny;
+    p->chunk_rows = rows;
+    p->chunk_pts = (size_t)rows * c->nx;
+
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        off = align_up(off, kAlign);
+        const size_t o = off;
+        off += std::max<size_t>(bytes, 1);
+        return o;
+    };
+    const size_t state_bytes = (size_t)p->nmem * 9 * p->npts * sizeof(float);
+    p->off_state[0] = take(state_bytes);
+    p->off_state[1] = take(state_bytes);
+    p->off_force = take(c->force ? p->npts * sizeof(float2) : 0);
+    p->off_xg = take(p->npts * 9 * c->k * sizeof(float));
+    p->off_obs_xy = take((size_t)c->n_obs * sizeof(int2));
+    p->off_cell_start = take(((size_t)p->ncx * p->ncy + 1) * sizeof(int));
+    p->off_cell_obs = take((size_t)c->n_obs * sizeof(int));
+    p->off_rinv = take((size_t)p->LV * sizeof(float));
+    p->off_yf = take((size_t)p->nmem * p->LV * sizeof(float));
+    p->off_yb = take((size_t)p->LV * p->kp * sizeof(float));
+    p->off_ybar = take((size_t)p->LV * sizeof(float));
+    p->off_yo = take((size_t)p->LV * sizeof(float));
+    p->off_gram = take(p->chunk_pts * c->k * c->k * sizeof(float));
+    p->off_cvec = take(p->chunk_pts * c->k * sizeof(float));
+    p->off_nloc = take(p->chunk_pts * sizeof(int));
+    p->off_nloc_all = take(p->npts * sizeof(int));
+    p->off_eigval = take(p->chunk_pts * c->k * sizeof(float));
+    p->off_status = take(kAlign);
+    p->total = align_up(off, kAlign);
+    return LETKF_OK;
+}
+
+}  // namespace
+
+struct letkf_handle {
+    letkf_config cfg;
+    Plan plan;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    unsigned char *ws = nullptr;
+    bool own_ws = false;
+    float *state[2] = {nullptr, nullptr};
+    int cur = 0;
+    float2 *force = nullptr;
+    float *xg = nullptr, *rinv = nullptr, *yf = nullptr, *yb = nullptr, *ybar = nullptr,
+          *yo = nullptr, *gram = nullptr, *cvec = nullptr, *eigval = nullptr;
+    int2 *obs_xy = nullptr;
+    int *cell_start = nullptr, *cell_obs = nullptr, *nloc = nullptr, *nloc_all = nullptr,
+        *status = nullptr;
+    lk::ObsNet net;
+    float yref[3] = {0, 0, 0};
+    int eig_blocks = 0;
+    letkf_stats stats;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int graph_nsteps[2] = {-1, -1};
+    int latched = 0;  // host-side error waiting for letkf_sync
+    // phase timing: forecast start/end, then analysis boundaries
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;  // [0..1] forecast, [2..] analysis (4 + 2 * chunks)
+    int fc_steps = -1;            // steps of the last timed forecast
+    bool an_done = false;         // an analysis has been timed
+};
+
+namespace {
+
+int cuda_fail(letkf_handle *h, cudaError_t e) {
+    if (e == cudaSuccess) return LETKF_OK;
+    if (h && !h->latched) h->latched = LETKF_ECUDA;
+    return e == cudaErrorMemoryAllocation ? LETKF_ENOMEM : LETKF_ECUDA;
+}
+
+#define CK(expr)                                            \
+    do {                                                    \
+        cudaError_t e__ = (expr);                           \
+        if (e__ != cudaSuccess) return cuda_fail(h, e__);   \
+    } while (0)
+
+int device_check(letkf_handle *h) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LETKF_ECUDA;
+    if (dev != h->device) CK(cudaSetDevice(h->device));
+    return LETKF_OK;
+}
+
+int copy_in(letkf_handle *h, void *dst, const void *src, size_t bytes, int where) {
+    if (where != LETKF_HOST && where != LETKF_DEVICE) return LETKF_EINVAL;
+    if (bytes == 0) return LETKF_OK;
+    CK(cudaMemcpyAsync(dst, src, bytes,
+                       where == LETKF_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                       h->stream));
+    return LETKF_OK;
+}
+
+int copy_out(letkf_handle *h, void *dst, const void *src, size_t bytes, int where) {
+    if (where != LETKF_HOST && where != LETKF_DEVICE) return LETKF_EINVAL;
+    if (bytes == 0) return LETKF_OK;
+    CK(cudaMemcpyAsync(dst, src, bytes,
+                       where == LETKF_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                       h->stream));
+    if (where == LETKF_HOST) CK(cudaStreamSynchronize(h->stream));
+    return LETKF_OK;
+}
+
+int n_chunks(const letkf_handle *h) {
+    return (h->cfg.ny + h->plan.chunk_rows - 1) / h->plan.chunk_rows;
+}
+
+// Phase boundary event.  Inside a stream capture the record must be an external event node,
+// otherwise the capture only uses it as an internal dependency and never records it.
+int mark(letkf_handle *h, int idx) {
+    if (!h->timing) return LETKF_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(h->stream, &cs));
+    if (cs == cudaStreamCaptureStatusActive)
+        CK(cudaEventRecordWithFlags(h->ev[idx], h->stream, cudaEventRecordExternal));
+    else
+        CK(cudaEventRecord(h->ev[idx], h->stream));
+    return LETKF_OK;
+}
+
+int enqueue_forecast(letkf_handle *h, int nsteps) {
+    const Plan &p = h->plan;
+    int rc = mark(h, 0);
+    if (rc) return rc;
+    for (int s = 0; s < nsteps; ++s) {
+        CK(lk::launch_lbm_step(h->state[h->cur], h->state[h->cur ^ 1], h->force, h->cfg.nx,
+                               h->cfg.ny, p.nmem, h->cfg.tau, h->stream));
+        h->cur ^= 1;
+    }
+    if (h->timing) h->fc_steps = nsteps;
+    return mark(h, 1);
+}
+
+int enqueue_obs(letkf_handle *h) {
+    const Plan &p = h->plan;
+    lk::ObsOpArgs o;
+    o.g = h->state[h->cur];
+    o.xy = h->obs_xy;
+    o.L = h->cfg.n_obs;
+    o.nx = h->cfg.nx;
+    o.ny = h->cfg.ny;
+    o.k = h->cfg.k;
+    o.kp = p.kp;
+    o.nmem = p.nmem;
+    o.obs_vars = h->cfg.obs_vars;
+    o.yf = h->yf;
+    o.yb = h->yb;
+    o.ybar = h->ybar;
+    CK(lk::launch_obs_operator(o, h->stream));
+    return LETKF_OK;
+}
+
+// Analysis kernels after yo is on the device.  probe may be NULL.
+int enqueue_analysis(letkf_handle *h, letkf_probe *probe) {
+    const Plan &p = h->plan;
+    const letkf_config &c = h->cfg;
+    const int k = c.k;
+    int rc = mark(h, 2);
+    if (!rc) rc = enqueue_obs(h);
+    if (!rc) rc = mark(h, 3);
+    if (rc) return rc;
+    CK(lk::launch_transpose_in(h->state[h->cur], h->xg, k, p.npts, h->stream));
+    if ((rc = mark(h, 4))) return rc;
+    int chunk = 0;
+    if (probe && probe->xf)
+        for (int i = 0; i < probe->n_points; ++i)
+            CK(cudaMemcpyAsync(probe->xf + (size_t)i * 9 * k,
+                               h->xg + (size_t)probe->points[i] * 9 * k, 9 * k * sizeof(float),
+                               cudaMemcpyDeviceToHost, h->stream));
+    for (int y0 = 0; y0 < c.ny; y0 += p.chunk_rows) {
+        const int y1 = std::min(c.ny, y0 + p.chunk_rows);
+        lk::GramArgs g;
+        g.net = h->net;
+        g.nx = c.nx;
+        g.ny = c.ny;
+        g.k = k;
+        g.kp = p.kp;
+        g.yb = h->yb;
+        g.ybar = h->ybar;
+        g.yo = h->yo;
+        g.rinv = h->rinv;
+        for (int v = 0; v < 3; ++v) g.yref[v] = h->yref[v];
+        g.y_begin = y0;
+        g.y_end = y1;
+        g.gram = h->gram;
+        g.cvec = h->cvec;
+        g.nloc = h->nloc;
+        CK(lk::launch_gram(g, h->stream));
+        if ((rc = mark(h, 5 + 2 * chunk))) return rc;
+        const long long pt0 = (long long)y0 * c.nx;
+        const int npts = (y1 - y0) * c.nx;
+        if (probe) {
+            for (int i = 0; i < probe->n_points; ++i) {
+                const long long lp = probe->points[i] - pt0;
+                if (lp < 0 || lp >= npts) continue;
+                if (probe->nloc)
+                    CK(cudaMemcpyAsync(probe->nloc + i, h->nloc + lp, sizeof(int),
+                                       cudaMemcpyDeviceToHost, h->stream));
+                if (probe->gram)
+                    CK(cudaMemcpyAsync(probe->gram + (size_t)i * k * k, h->gram + lp * k * k,
+                                       (size_t)k * k * sizeof(float), cudaMemcpyDeviceToHost,
+                                       h->stream));
+                if (probe->cvec)
+                    CK(cudaMemcpyAsync(probe->cvec + (size_t)i * k, h->cvec + lp * k,
+                                       (size_t)k * sizeof(float), cudaMemcpyDeviceToHost,
+                                       h->stream));
+            }
+        }
+        lk::EigArgs e;
+        e.k = k;
+        e.diag = (float)((double)(k - 1) / (double)c.infl);
+        e.gram = h->gram;
+        e.cvec = h->cvec;
+        e.nloc = h->nloc;
+        e.x = h->xg;
+        e.pt0 = pt0;
+        e.npts = npts;
+        e.eigval = (probe && probe->eigval) ? h->eigval : nullptr;
+        e.status = h->status;
+        e.max_blocks = h->eig_blocks;
+        CK(lk::launch_eigen_update(e, h->stream));
+        if ((rc = mark(h, 6 + 2 * chunk))) return rc;
+        ++chunk;
+        if (probe && probe->eigval)
+            for (int i = 0; i < probe->n_points; ++i) {
+                const long long lp = probe->points[i] - pt0;
+                if (lp < 0 || lp >= npts) continue;
+                CK(cudaMemcpyAsync(probe->eigval + (size_t)i * k, h->eigval + lp * k,
+                                   (size_t)k * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+            }
+    }
+    CK(lk::launch_transpose_out(h->xg, h->state[h->cur], k, p.npts, h->stream));
+    if ((rc = mark(h, 5 + 2 * chunk))) return rc;
+    if (h->timing) h->an_done = true;
+    return LETKF_OK;
+}
+
+int status_to_code(int bits) {
+    if (bits & lk::ST_NONFINITE) return LETKF_ENONFINITE;
+    if (bits & lk::ST_NOTCONV) return LETKF_ENOTCONV;
+    if (bits & lk::ST_TIMEOUT) return LETKF_ETIMEOUT;
+    if (bits & lk::ST_BADINDEX) return LETKF_EINVAL;
+    return LETKF_OK;
+}
+
+void destroy_graphs(letkf_handle *h) {
+    for (int i = 0; i < 2; ++i) {
+        if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
+        h->graph[i] = nullptr;
+        h->graph_nsteps[i] = -1;
+    }
+}
+
+void destroy_events(letkf_handle *h) {
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    h->ev.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *letkf_strerror(int code) {
+    switch (code) {
+        case LETKF_OK: return "success";
+        case LETKF_EINVAL: return "invalid argument";
+        case LETKF_ENOMEM: return "out of device memory or workspace too small";
+        case LETKF_ENOTCONV: return "eigensolver did not converge at some grid point";
+        case LETKF_ENONFINITE: return "non-finite value in the analysis";
+        case LETKF_ETIMEOUT: return "bounded device wait expired";
+        case LETKF_ECUDA: return "CUDA runtime error";
+        case LETKF_ESTATE: return "call not valid in the handle's current state";
+        default: return "unknown status code";
+    }
+}
+
+int letkf_workspace_size(const letkf_config *cfg, size_t *bytes) {
+    if (!bytes) return LETKF_EINVAL;
+    Plan p;
+    const int rc = make_plan(cfg, &p);
+    if (rc) return rc;
+    *bytes = p.total;
+    return LETKF_OK;
+}
+
+int letkf_init(const letkf_config *cfg, void *workspace, size_t workspace_bytes,
+               letkf_handle **out) {
+    if (!out) return LETKF_EINVAL;
+    *out = nullptr;
+    Plan plan;
+    int rc = make_plan(cfg, &plan);
+    if (rc) return rc;
+    if (workspace && (workspace_bytes < plan.total || ((uintptr_t)workspace % kAlign)))
+        return LETKF_ENOMEM;
+    letkf_handle *h = new (std::nothrow) letkf_handle();
+    if (!h) return LETKF_ENOMEM;
+    h->cfg = *cfg;
+    h->cfg.force = nullptr;
+    h->cfg.obs_xy = nullptr;
+    h->cfg.obs_err_var = nullptr;
+    h->plan = plan;
+    memset(&h->stats, 0, sizeof(h->stats));
+    auto fail = [&](int code) {
+        letkf_destroy(h);
+        return code;
+    };
+    if (cudaGetDevice(&h->device) != cudaSuccess) return fail(LETKF_ECUDA);
+    if (cfg->stream) {
+        h->stream = (cudaStream_t)cfg->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(LETKF_ECUDA);
+        h->own_stream = true;
+    }
+    if (workspace) {
+        h->ws = (unsigned char *)workspace;
+    } else {
+        void *w = nullptr;
+        const cudaError_t e = cudaMalloc(&w, plan.total);
+        if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? LETKF_ENOMEM : LETKF_ECUDA);
+        h->ws = (unsigned char *)w;
+        h->own_ws = true;
+    }
+    unsigned char *w = h->ws;
+    h->state[0] = (float *)(w + plan.off_state[0]);
+    h->state[1] = (float *)(w + plan.off_state[1]);
+    h->force = cfg->force ? (float2 *)(w + plan.off_force) : nullptr;
+    h->xg = (float *)(w + plan.off_xg);
+    h->obs_xy = (int2 *)(w + plan.off_obs_xy);
+    h->cell_start = (int *)(w + plan.off_cell_start);
+    h->cell_obs = (int *)(w + plan.off_cell_obs);
+    h->rinv = (float *)(w + plan.off_rinv);
+    h->yf = (float *)(w + plan.off_yf);
+    h->yb = (float *)(w + plan.off_yb);
+    h->ybar = (float *)(w + plan.off_ybar);
+    h->yo = (float *)(w + plan.off_yo);
+    h->gram = (float *)(w + plan.off_gram);
+    h->cvec = (float *)(w + plan.off_cvec);
+    h->nloc = (int *)(w + plan.off_nloc);
+    h->nloc_all = (int *)(w + plan.off_nloc_all);
+    h->eigval = (float *)(w + plan.off_eigval);
+    h->status = (int *)(w + plan.off_status);
+
+    const size_t npts = plan.npts;
+    // body force, interleaved per node
+    if (cfg->force) {
+        std::vector<float2> f(npts);
+        for (size_t i = 0; i < npts; ++i) f[i] = make_float2(cfg->force[i], cfg->force[npts + i]);
+        if (cudaMemcpy(h->force, f.data(), npts * sizeof(float2), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+            return fail(LETKF_ECUDA);
+    }
+    // observation network, bins (ascending observation index within each bin) and R^-1
+    const int L = cfg->n_obs;
+    std::vector<int2> xy(L);
+    for (int l = 0; l < L; ++l) xy[l] = make_int2(cfg->obs_xy[2 * l], cfg->obs_xy[2 * l + 1]);
+    const int ncell = plan.ncx * plan.ncy;
+    std::vector<int> cstart(ncell + 1, 0), cobs(L);
+    for (int l = 0; l < L; ++l) cstart[(xy[l].y / plan.cs) * plan.ncx + xy[l].x / plan.cs + 1]++;
+    for (int c = 0; c < ncell; ++c) cstart[c + 1] += cstart[c];
+    {
+        std::vector<int> fill(cstart.begin(), cstart.end() - 1);
+        for (int l = 0; l < L; ++l) cobs[fill[(xy[l].y / plan.cs) * plan.ncx + xy[l].x / plan.cs]++] = l;
+    }
+    std::vector<float> rinv(plan.LV);
+    for (int s = 0; s < plan.LV; ++s) rinv[s] = (float)(1.0 / (double)cfg->obs_err_var[s]);
+    if ((L && cudaMemcpy(h->obs_xy, xy.data(), L * sizeof(int2), cudaMemcpyHostToDevice)) ||
+        cudaMemcpy(h->cell_start, cstart.data(), cstart.size() * sizeof(int),
+                   cudaMemcpyHostToDevice) ||
+        (L && cudaMemcpy(h->cell_obs, cobs.data(), L * sizeof(int), cudaMemcpyHostToDevice)) ||
+        (plan.LV && cudaMemcpy(h->rinv, rinv.data(), plan.LV * sizeof(float),
+                               cudaMemcpyHostToDevice)))
+        return fail(LETKF_ECUDA);
+    {
+        int col = 0;
+        for (int vid = 0; vid < 3; ++vid)
+            if (cfg->obs_vars & (1 << vid)) h->yref[col++] = vid == 0 ? 1.0f : 0.0f;
+    }
+    h->net.xy = h->obs_xy;
+    h->net.cell_start = h->cell_start;
+    h->net.cell_obs = h->cell_obs;
+    h->net.L = L;
+    h->net.V = plan.V;
+    h->net.cs = plan.cs;
+    h->net.ncx = plan.ncx;
+    h->net.ncy = plan.ncy;
+    h->net.loc_none = cfg->loc_kind == LETKF_LOC_NONE;
+    h->net.d2max = plan.d2max;
+    h->net.cr = plan.cr;
+    h->net.inv2r2 = plan.inv2r2;
+
+    if (lk::gram_prepare(plan.kp) != cudaSuccess ||
+        lk::eigen_prepare(cfg->k, &h->eig_blocks) != cudaSuccess)
+        return fail(LETKF_ECUDA);
+    // rest state, clean status, zero Gram buffers
+    if (cudaMemsetAsync(h->state[0], 0, (size_t)plan.nmem * 9 * npts * sizeof(float), h->stream) ||
+        cudaMemsetAsync(h->status, 0, kAlign, h->stream) ||
+        cudaMemsetAsync(h->yb, 0, (size_t)plan.LV * plan.kp * sizeof(float), h->stream))
+        return fail(LETKF_ECUDA);
+    h->cur = 0;
+    // static local-observation counts
+    if (lk::launch_count_local(h->net, cfg->nx, cfg->ny, h->nloc_all, h->stream) != cudaSuccess)
+        return fail(LETKF_ECUDA);
+    std::vector<int> nl(npts);
+    if (cudaMemcpyAsync(nl.data(), h->nloc_all, npts * sizeof(int), cudaMemcpyDeviceToHost,
+                        h->stream) ||
+        cudaStreamSynchronize(h->stream))
+        return fail(LETKF_ECUDA);
+    long long sum = 0;
+    int mx = 0, zeros = 0;
+    for (size_t i = 0; i < npts; ++i) {
+        sum += nl[i];
+        mx = std::max(mx, nl[i]);
+        zeros += nl[i] == 0;
+    }
+    h->stats.n_points = (int32_t)npts;
+    h->stats.n_zero_obs = zeros;
+    h->stats.max_local_obs = mx;
+    h->stats.mean_local_obs = (double)sum / (double)npts;
+    h->stats.n_chunks = n_chunks(h);
+    *out = h;
+    return LETKF_OK;
+}
+
+int letkf_sync(letkf_handle *h) {
+    if (!h) return LETKF_EINVAL;
+    int rc = device_check(h);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(h->stream));
+    int bits = 0;
+    CK(cudaMemcpy(&bits, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (bits) CK(cudaMemset(h->status, 0, sizeof(int)));
+    int code = status_to_code(bits);
+    if (!code && h->latched) code = h->latched;
+    h->latched = 0;
+    h->stats.status = code;
+    return code;
+}
+
+int letkf_destroy(letkf_handle *h) {
+    if (!h) return LETKF_OK;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != h->device) cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    destroy_graphs(h);
+    destroy_events(h);
+    if (h->own_ws && h->ws) cudaFree(h->ws);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    if (dev >= 0 && dev != h->device) cudaSetDevice(dev);
+    delete h;
+    return LETKF_OK;
+}
+
+int letkf_get_stats(letkf_handle *h, letkf_stats *st) {
+    if (!h || !st) return LETKF_EINVAL;
+    *st = h->stats;
+    return LETKF_OK;
+}
+
+int letkf_enable_timing(letkf_handle *h, int32_t on) {
+    if (!h) return LETKF_EINVAL;
+    int rc = device_check(h);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(h->stream));
+    destroy_graphs(h);  // graphs captured with (or without) event records are stale
+    destroy_events(h);
+    h->timing = false;
+    h->fc_steps = -1;
+    h->an_done = false;
+    if (!on) return LETKF_OK;
+    const int n = 2 + 4 + 2 * n_chunks(h);
+    h->ev.resize(n, nullptr);
+    for (int i = 0; i < n; ++i) CK(cudaEventCreate(&h->ev[i]));
+    h->timing = true;
+    return LETKF_OK;
+}
+
+int letkf_get_timings(letkf_handle *h, letkf_timings *t) {
+    if (!h || !t) return LETKF_EINVAL;
+    if (!h->timing || (h->fc_steps < 0 && !h->an_done)) return LETKF_ESTATE;
+    int rc = device_check(h);
+    if (rc) return rc;
+    memset(t, 0, sizeof(*t));
+    const int nc = n_chunks(h);
+    t->n_chunks = nc;
+    auto el = [&](int a, int b, float *out) -> int {
+        CK(cudaEventSynchronize(h->ev[b]));
+        CK(cudaEventElapsedTime(out, h->ev[a], h->ev[b]));
+        return LETKF_OK;
+    };
+    if (h->fc_steps >= 0) {
+        t->forecast_steps = h->fc_steps;
+        if ((rc = el(0, 1, &t->forecast_ms))) return rc;
+    }
+    if (h->an_done) {
+        if ((rc = el(2, 3, &t->obs_ms)) || (rc = el(3, 4, &t->transpose_in_ms))) return rc;
+        for (int c = 0; c < nc; ++c) {
+            float a = 0.0f, b = 0.0f;
+            if ((rc = el(4 + 2 * c, 5 + 2 * c, &a)) || (rc = el(5 + 2 * c, 6 + 2 * c, &b))) return rc;
+            t->gram_ms += a;
+            t->eigen_ms += b;
+        }
+        if ((rc = el(4 + 2 * nc, 5 + 2 * nc, &t->transpose_out_ms))) return rc;
+    }
+    return LETKF_OK;
+}
+
+int letkf_set_state(letkf_handle *h, const float *f, int32_t m0, int32_t count, int32_t where) {
+    if (!h || !f || m0 < 0 || count < 0 || m0 + count > h->plan.nmem) return LETKF_EINVAL;
+    int rc = device_check(h);
+    if (rc) return rc;
+    const size_t n = (size_t)count * 9 * h->plan.npts;
+    float *dst = h->state[h->cur] + (size_t)m0 * 9 * h->plan.npts;
+    rc = copy_in(h, dst, f, n * sizeof(float), where);
+    if (rc) return rc;
+    CK(lk::launch_f_to_g(dst, dst, count, h->plan.npts, h->stream));
+    if (where == LETKF_HOST) CK(cudaStreamSynchronize(h->stream));
+    return LETKF_OK;
+}
+
+int letkf_get_state(letkf_handle *h, float *f, int32_t m0, int32_t count, int32_t where) {
+    if (!h || !f || m0 < 0 || count < 0 || m0 + count > h->plan.nmem) return LETKF_EINVAL;
+    int rc = device_check(h);
+    if (rc) return rc;
+    const size_t n = (size_t)count * 9 * h->plan.npts;
+    const size_t off = (size_t)m0 * 9 * h->plan.npts;
+    float *scratch = h->state[h->cur ^ 1] + off;  // the idle ping-pong buffer
+    CK(lk::launch_g_to_f(h->state[h->cur] + off, scratch, count, h->plan.npts, h->stream));
+    return copy_out(h, f, scratch, n * sizeof(float), where);
+}
+
+int letkf_set_deviation(letkf_handle *h, const float *g, int32_t m0, int32_t count,
+                        int32_t where) {
+    if (!h || !g || m0 < 0 || count < 0 || m0 + count > h->plan.nmem) return LETKF_EINVAL;
+    int rc = device_check(h);
+    if (rc) return rc;
+    const size_t n = (size_t)count * 9 * h->plan.npts;
+    rc = copy_in(h, h->state[h->cur] + (size_t)m0 * 9 * h->plan.npts, g, n * sizeof(float), where);
+    if (rc) return rc;
+    if (where == LETKF_HOST) CK(cudaStreamSynchronize(h->stream));
+    return LETKF_OK;
+}
+
+int letkf_get_deviation(letkf_handle *h, float *g, int32_t m0, int32_t count, int32_t where) {
+    if (!h || !g || m0 < 0 || count < 0 || m0 + count > h->plan.nmem) return LETKF_EINVAL;
+    int rc = device_check(h);
+    if (rc) return rc;
+    const size_t n = (size_t)count * 9 * h->plan.npts;
+    return copy_out(h, g, h->state[h->cur] + (size_t)m0 * 9 * h->plan.npts, n * sizeof(float),
+                    where);
+}
+
+int letkf_set_macro(letkf_handle *h, const float *rho, const float *ux, const float *uy,
+                    int32_t m0, int32_t count, int32_t where) {
+    if (!h || !rho || !ux || !uy || m0 < 0 || count < 0 || m0 + count > h->plan.nmem)
+        return LETKF_EINVAL;
+    int rc = device_check(h);
+    if (rc) return rc;
+    const size_t npts = h->plan.npts;
+    const size_t n = (size_t)count * npts;
+    const float *dr = rho, *du = ux, *dv = uy;
+    if (where == LETKF_HOST) {  // stage through the idle state buffer (9 x larger than needed)
+        float *s = h->state[h->cur ^ 1];
+        if ((rc = copy_in(h, s, rho, n * sizeof(float), where)) ||
+            (rc = copy_in(h, s + n, ux, n * sizeof(float), where)) ||
+            (rc = copy_in(h, s + 2 * n, uy, n * sizeof(float), where)))
+            return rc;
+        dr = s;
+        du = s + n;
+        dv = s + 2 * n;
+    } else if (where != LETKF_DEVICE) {
+        return LETKF_EINVAL;
+    }
+    CK(lk::launch_macro_to_g(dr, du, dv, h->state[h->cur] + (size_t)m0 * 9 * npts, count, npts,
+                             h->stream));
+    if (where == LETKF_HOST) CK(cudaStreamSynchronize(h->stream));
+    return LETKF_OK;
+}
+
+int lbm_forecast(letkf_handle *h, int32_t nsteps) {
+    if (!h || nsteps < 0) return LETKF_EINVAL;
+    int rc = device_check(h);
+    if (rc) return rc;
+    return enqueue_forecast(h, nsteps);
+}
+
+int letkf_get_obs(letkf_handle *h, float *yf, int32_t where) {
+    if (!h || !yf) return LETKF_EINVAL;
+    int rc = device_check(h);
+    if (rc) return rc;
+    if ((rc = enqueue_obs(h))) return rc;
+    return copy_out(h, yf, h->yf, (size_t)h->plan.nmem * h->plan.LV * sizeof(float), where);
+}
+
+int letkf_analyze_probe(letkf_handle *h, const float *yo, int32_t where, letkf_probe *probe) {
+    if (!h || (h->plan.LV > 0 && !yo)) return LETKF_EINVAL;
+    if (probe) {
+        if (probe->n_points < 0 || (probe->n_points > 0 && !probe->points)) return LETKF_EINVAL;
+        for (int i = 0; i < probe->n_points; ++i)
+            if (probe->points[i] < 0 || (size_t)probe->points[i] >= h->plan.npts)
+                return LETKF_EINVAL;
+    }
+    int rc = device_check(h);
+    if (rc) return rc;
+    if ((rc = copy_in(h, h->yo, yo, (size_t)h->plan.LV * sizeof(float), where))) return rc;
+    if ((rc = enqueue_analysis(h, probe))) return rc;
+    if (probe) CK(cudaStreamSynchronize(h->stream));
+    if (probe && probe->eigval)  // ascending order per point
+        for (int i = 0; i < probe->n_points; ++i)
+            std::sort(probe->eigval + (size_t)i * h->cfg.k, probe->eigval + (size_t)(i + 1) * h->cfg.k);
+    return LETKF_OK;
+}
+
+int letkf_analyze(letkf_handle *h, const float *yo, int32_t where) {
+    return letkf_analyze_probe(h, yo, where, nullptr);
+}
+
+int letkf_cycle(letkf_handle *h, int32_t nsteps, const float *yo, int32_t where) {
+    if (!h || nsteps < 0 || (h->plan.LV > 0 && !yo)) return LETKF_EINVAL;
+    int rc = device_check(h);
+    if (rc) return rc;
+    if ((rc = copy_in(h, h->yo, yo, (size_t)h->plan.LV * sizeof(float), where))) return rc;
+    const int slot = h->cur;
+    if (h->graph_nsteps[slot] != nsteps) {
+        if (h->graph[slot]) {
+            cudaGraphExecDestroy(h->graph[slot]);
+            h->graph[slot] = nullptr;
+        }
+        CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed));
+        const int cur0 = h->cur;
+        rc = enqueue_forecast(h, nsteps);
+        if (!rc) rc = enqueue_analysis(h, nullptr);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(h->stream, &g);
+        h->cur = cur0;
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (ec != cudaSuccess) return cuda_fail(h, ec);
+        const cudaError_t ei = cudaGraphInstantiate(&h->graph[slot], g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) return cuda_fail(h, ei);
+        h->graph_nsteps[slot] = nsteps;
+    }
+    CK(cudaGraphLaunch(h->graph[slot], h->stream));
+    h->cur ^= (nsteps & 1);
+    return LETKF_OK;
+}
+
+}  // extern "C"

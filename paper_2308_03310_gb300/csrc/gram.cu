@@ -1,0 +1,304 @@
+// Localized Gram matrix and innovation projection at every grid point (FP32, CUDA cores).
+//
+// For grid point p with local observations o (R-localization, Sec. II-B):
+//     A_p = sum_o G_po / sigma_o^2  dy_o dy_o^T        (the k x k term of Eq. letkf_q)
+//     c_p = sum_o G_po / sigma_o^2  dy_o (yo_o - ybar_o) (the vector of Eq. letkf_wa)
+// with G_po = exp(-d^2 / (2 r^2)) for integer periodic d^2 <= d2max, else 0.
+//
+// Design (GB300): a CTA owns a TW x TH tile of grid points and a team of
+// (KP/8)^2 threads per point, each thread accumulating one 8 x 8 block of A_p in
+// registers.  The CTA gathers the observation patch of its tile once -- the
+// observations of every bin (cs x cs cell) that the tile's cutoff disks touch --
+// and stages it through shared memory 32 observation points at a time: their
+// perturbation rows dy_o (k floats each, read from L2, where the whole dY lives),
+// innovations and inverse variances.  The weight of each (point, observation)
+// pair is computed once per chunk into shared memory; a team skips observations
+// outside its point's cutoff.  Nothing per-point is materialized in HBM except the
+// k x k result (the paper's padded Y_loc[M, N_x, l_max V] array is never formed).
+// Summation order is fixed by the bin order, so results are bitwise reproducible.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace lk {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kChunk = 32;     // observation points per staged chunk
+constexpr int kMaxCells = 1024;  // bins in one tile's patch (the host sizes bins to fit)
+
+template <int KP>
+struct GramShape {
+    static constexpr int KB = KP / 8;
+    static constexpr int T = KB * KB;         // threads per grid point
+    static constexpr int P = kThreads / T;    // grid points per CTA
+    static constexpr int TW = P >= 256 ? 16 : P >= 64 ? 8 : P >= 16 ? 4 : P >= 4 ? 2 : 1;
+    static constexpr int TH = P / TW;
+};
+
+// Exclusive prefix sum in place over s[0..n], n <= 4 * kThreads; s[n] receives the total.
+__device__ void block_exclusive_scan(int *s, int n, int *warp_tot) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    int v[4], local = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int idx = tid * 4 + i;
+        v[i] = idx < n ? s[idx] : 0;
+        local += v[i];
+    }
+    int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int t = lane < kThreads / 32 ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += u;
+        }
+        if (lane < kThreads / 32) warp_tot[lane] = t;  // inclusive warp totals
+    }
+    __syncthreads();
+    int run = incl - local + (wid > 0 ? warp_tot[wid - 1] : 0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int idx = tid * 4 + i;
+        if (idx < n) s[idx] = run;
+        run += v[i];
+    }
+    if (tid == kThreads - 1) s[n] = run;
+    __syncthreads();
+}
+
+__device__ __forceinline__ int range_len(const BinRanges &r) {
+    int n = 0;
+    for (int i = 0; i < r.n; ++i) n += r.hi[i] - r.lo[i] + 1;
+    return n;
+}
+__device__ __forceinline__ int range_at(const BinRanges &r, int i) {
+    const int l0 = r.hi[0] - r.lo[0] + 1;
+    return i < l0 ? r.lo[0] + i : r.lo[1] + (i - l0);
+}
+
+template <int KP>
+__global__ void __launch_bounds__(kThreads) gram_kernel(GramArgs a) {
+    using S = GramShape<KP>;
+    constexpr int KB = S::KB, T = S::T, P = S::P, TW = S::TW, TH = S::TH;
+
+    __shared__ int cell_base[kMaxCells];
+    __shared__ int cell_pre[kMaxCells + 1];
+    __shared__ int warp_tot[kThreads / 32];
+    __shared__ int2 opos[kChunk];
+    __shared__ int oidx[kChunk];
+    __shared__ float dv[kChunk * 3];
+    __shared__ float rv[kChunk * 3];
+    extern __shared__ float4 dyn4[];
+    float *ys = reinterpret_cast<float *>(dyn4);       // [kChunk * V][KP]
+    float *wts = ys + kChunk * 3 * KP;                 // [P][kChunk]
+
+    const ObsNet &net = a.net;
+    const int V = net.V;
+    const int tid = threadIdx.x;
+    const int tx0 = blockIdx.x * TW;
+    const int ty0 = a.y_begin + blockIdx.y * TH;
+
+    // ---- the tile's observation patch: bins touched by any cutoff disk of the tile
+    BinRanges rx, ry;
+    if (net.loc_none) {
+        rx.n = ry.n = 1;
+        rx.lo[0] = ry.lo[0] = 0;
+        rx.hi[0] = net.ncx - 1;
+        ry.hi[0] = net.ncy - 1;
+    } else {
+        rx = bin_ranges(tx0 - net.cr, tx0 + TW - 1 + net.cr, a.nx, net.cs);
+        ry = bin_ranges(ty0 - net.cr, ty0 + TH - 1 + net.cr, a.ny, net.cs);
+    }
+    const int ncx_p = range_len(rx);
+    const int nc = ncx_p * range_len(ry);  // <= kMaxCells by construction of the bin size
+    for (int c = tid; c < nc; c += kThreads) {
+        const int cell = range_at(ry, c / ncx_p) * net.ncx + range_at(rx, c % ncx_p);
+        const int b0 = net.cell_start[cell];
+        cell_base[c] = b0;
+        cell_pre[c] = net.cell_start[cell + 1] - b0;
+    }
+    __syncthreads();
+    block_exclusive_scan(cell_pre, nc, warp_tot);
+    const int total = cell_pre[nc];
+
+    // ---- this thread's role: point p of the tile, 8 x 8 block (ti, tj) of A_p
+    const int p = tid / T, r = tid % T, ti = r / KB, tj = r % KB;
+    const int px = tx0 + p % TW, py = ty0 + p / TW;
+    const bool valid = p < P && px < a.nx && py < a.y_end;
+
+    float acc[8][8];
+    float cacc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        cacc[i] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+    }
+    int nl = 0;
+
+    for (int base = 0; base < total; base += kChunk) {
+        const int nch = min(kChunk, total - base);
+        if (tid < nch) {
+            const int j = base + tid;
+            int lo = 0, hi = nc - 1;  // last bin whose prefix is <= j
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (cell_pre[mid] <= j) lo = mid; else hi = mid - 1;
+            }
+            const int o = net.cell_obs[cell_base[lo] + (j - cell_pre[lo])];
+            oidx[tid] = o;
+            opos[tid] = net.xy[o];
+            for (int v = 0; v < V; ++v) {
+                const int s = o * V + v;
+                dv[tid * V + v] = (a.yo[s] - a.yref[v]) - a.ybar[s];
+                rv[tid * V + v] = a.rinv[s];
+            }
+        }
+        __syncthreads();
+        // perturbation rows of the chunk: nch * V rows of KP floats, 16-byte copies
+        constexpr int Q4 = KP / 4;
+        for (int e = tid; e < nch * V * Q4; e += kThreads) {
+            const int row = e / Q4, c4 = e % Q4;
+            const int s = oidx[row / V] * V + row % V;
+            reinterpret_cast<float4 *>(ys + row * KP)[c4] =
+                __ldg(reinterpret_cast<const float4 *>(a.yb + (size_t)s * KP) + c4);
+        }
+        // localization weights of every (point, observation) pair of the chunk
+        for (int e = tid; e < P * nch; e += kThreads) {
+            const int pp = e / nch, t = e % nch;
+            const int qx = tx0 + pp % TW, qy = ty0 + pp / TW;
+            float w = 0.0f;
+            if (qx < a.nx && qy < a.y_end) {
+                if (net.loc_none) {
+                    w = 1.0f;
+                } else {
+                    const int dx = min_image(opos[t].x - qx, a.nx);
+                    const int dy = min_image(opos[t].y - qy, a.ny);
+                    const int d2 = dx * dx + dy * dy;
+                    if (d2 <= net.d2max) w = expf(-(float)d2 * net.inv2r2);
+                }
+            }
+            wts[pp * kChunk + t] = w;
+        }
+        __syncthreads();
+        if (valid) {
+            for (int t = 0; t < nch; ++t) {
+                const float w = wts[p * kChunk + t];
+                if (w == 0.0f) continue;
+                nl += (r == 0);
+                for (int v = 0; v < V; ++v) {
+                    const float sw = w * rv[t * V + v];
+                    const float *row = ys + (t * V + v) * KP;
+                    const float4 a0 = reinterpret_cast<const float4 *>(row + ti * 8)[0];
+                    const float4 a1 = reinterpret_cast<const float4 *>(row + ti * 8)[1];
+                    const float4 b0 = reinterpret_cast<const float4 *>(row + tj * 8)[0];
+                    const float4 b1 = reinterpret_cast<const float4 *>(row + tj * 8)[1];
+                    const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+                    const float dvs = dv[t * V + v];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const float sa = sw * av[i];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(sa, bv[j], acc[i][j]);
+                        if (tj == 0) cacc[i] = fmaf(sa, dvs, cacc[i]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    if (!valid) return;
+    const size_t lp = (size_t)(py - a.y_begin) * a.nx + px;
+    const int k = a.k;
+    float *A = a.gram + lp * k * k;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int row = ti * 8 + i;
+        if (row >= k) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int col = tj * 8 + j;
+            if (col < k) A[row * k + col] = acc[i][j];
+        }
+        if (tj == 0) a.cvec[lp * k + row] = cacc[i];
+    }
+    if (r == 0) a.nloc[lp] = nl;
+}
+
+template <int KP>
+size_t gram_smem() {
+    return (size_t)(kChunk * 3 * KP + GramShape<KP>::P * kChunk) * sizeof(float);
+}
+
+template <int KP>
+cudaError_t prepare_kp() {
+    return cudaFuncSetAttribute(gram_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)gram_smem<KP>());
+}
+
+template <int KP>
+cudaError_t launch_kp(const GramArgs &a, cudaStream_t s) {
+    using S = GramShape<KP>;
+    const size_t smem = gram_smem<KP>();
+    const int rows = a.y_end - a.y_begin;
+    dim3 grid((a.nx + S::TW - 1) / S::TW, (rows + S::TH - 1) / S::TH);
+    gram_kernel<KP><<<grid, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int gram_tile_height(int kp) {
+    switch (kp) {
+        case 8: return GramShape<8>::TH;
+        case 16: return GramShape<16>::TH;
+        case 32: return GramShape<32>::TH;
+        case 64: return GramShape<64>::TH;
+        default: return GramShape<128>::TH;
+    }
+}
+int gram_tile_width(int kp) {
+    switch (kp) {
+        case 8: return GramShape<8>::TW;
+        case 16: return GramShape<16>::TW;
+        case 32: return GramShape<32>::TW;
+        case 64: return GramShape<64>::TW;
+        default: return GramShape<128>::TW;
+    }
+}
+int gram_max_cells() { return kMaxCells; }
+
+cudaError_t gram_prepare(int kp) {
+    switch (kp) {
+        case 8: return prepare_kp<8>();
+        case 16: return prepare_kp<16>();
+        case 32: return prepare_kp<32>();
+        case 64: return prepare_kp<64>();
+        case 128: return prepare_kp<128>();
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_gram(const GramArgs &a, cudaStream_t s) {
+    if (a.y_end <= a.y_begin) return cudaSuccess;
+    switch (a.kp) {
+        case 8: return launch_kp<8>(a, s);
+        case 16: return launch_kp<16>(a, s);
+        case 32: return launch_kp<32>(a, s);
+        case 64: return launch_kp<64>(a, s);
+        case 128: return launch_kp<128>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace lk

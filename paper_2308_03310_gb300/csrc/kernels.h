@@ -1,0 +1,96 @@
+// Host-side launchers of the library's kernels (internal to libletkf).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace lk {
+
+// Device status bits latched with atomicOr and turned into LETKF_E* codes by the host.
+enum : int {
+    ST_NOTCONV = 1,
+    ST_NONFINITE = 2,
+    ST_TIMEOUT = 4,
+    ST_BADINDEX = 8,
+};
+
+// Static observation network, binned into cs x cs cells, and the localization.
+struct ObsNet {
+    const int2 *xy;         // [L] observation points (x, y)
+    const int *cell_start;  // [ncx*ncy + 1] CSR offsets into cell_obs
+    const int *cell_obs;    // [L] observation indices, grouped by cell, ascending within a cell
+    int L, V;               // points and observed variables per point
+    int cs, ncx, ncy;       // cell edge and number of cells per axis
+    int loc_none;           // 1: every observation is local with weight 1
+    int d2max;              // local iff integer squared periodic distance <= d2max
+    int cr;                 // largest |dx| with dx^2 <= d2max (search half-width in cells)
+    float inv2r2;           // 1 / (2 r^2) of the Gaussian weight
+};
+
+// ---- lbm.cu -------------------------------------------------------------------
+cudaError_t launch_lbm_step(const float *gin, float *gout, const float2 *force, int nx, int ny,
+                            int nmem, float tau, cudaStream_t s);
+cudaError_t launch_f_to_g(const float *f, float *g, int nmem, size_t npts, cudaStream_t s);
+cudaError_t launch_g_to_f(const float *g, float *f, int nmem, size_t npts, cudaStream_t s);
+cudaError_t launch_macro_to_g(const float *rho, const float *ux, const float *uy, float *g,
+                              int nmem, size_t npts, cudaStream_t s);
+
+// ---- obs.cu -------------------------------------------------------------------
+struct ObsOpArgs {
+    const float *g;         // state [nmem][9][N] (shifted populations)
+    const int2 *xy;         // [L]
+    int L, nx, ny, k, kp;
+    int nmem;               // members observed (k ensemble members first, then auxiliary)
+    int obs_vars;           // LETKF_OBS_* mask
+    float *yf;              // [nmem][L*V] h(x_m)
+    float *yb;              // [L*V][kp]  h(x_m) - mean, zero in columns k..kp-1
+    float *ybar;            // [L*V]      mean minus the variable's reference (1 for rho)
+};
+cudaError_t launch_obs_operator(const ObsOpArgs &a, cudaStream_t s);
+cudaError_t launch_count_local(const ObsNet &net, int nx, int ny, int *nloc, cudaStream_t s);
+
+// ---- transpose.cu -------------------------------------------------------------
+// member-major g[m][q][p] <-> grid-point-major x[p][q][m], members 0..k-1, p in [0, npts).
+cudaError_t launch_transpose_in(const float *g, float *x, int k, size_t npts, cudaStream_t s);
+cudaError_t launch_transpose_out(const float *x, float *g, int k, size_t npts, cudaStream_t s);
+
+// ---- gram.cu ------------------------------------------------------------------
+struct GramArgs {
+    ObsNet net;
+    int nx, ny, k, kp;
+    const float *yb;        // [L*V][kp]
+    const float *ybar;      // [L*V]
+    const float *yo;        // [L*V]
+    const float *rinv;      // [L*V] 1 / sigma^2
+    float yref[3];          // reference of each observed variable (1 for rho, else 0)
+    int y_begin, y_end;     // grid rows of this chunk
+    float *gram;            // [(y_end-y_begin)*nx][k][k]
+    float *cvec;            // [(y_end-y_begin)*nx][k]
+    int *nloc;              // [(y_end-y_begin)*nx]
+};
+cudaError_t gram_prepare(int kp);            // once per process and kp
+cudaError_t launch_gram(const GramArgs &a, cudaStream_t s);
+int gram_tile_width(int kp);
+int gram_tile_height(int kp);
+int gram_max_cells();
+
+// ---- eigen.cu -----------------------------------------------------------------
+struct EigArgs {
+    int k;
+    float diag;             // (k - 1) / rho_infl
+    const float *gram;      // [npts][k][k]
+    const float *cvec;      // [npts][k]
+    const int *nloc;        // [npts]
+    float *x;               // grid-point-major ensemble [N][9][k], updated in place
+    long long pt0;          // first grid point of the chunk
+    int npts;
+    float *eigval;          // optional [npts][k] eigenvalues (ascending), NULL normally
+    int *status;            // device status word
+    int max_blocks;         // resident grid from eigen_prepare
+};
+cudaError_t eigen_prepare(int k, int *max_blocks);  // once per process and k
+cudaError_t launch_eigen_update(const EigArgs &a, cudaStream_t s);
+size_t eigen_smem_per_warp(int k);
+
+}  // namespace lk

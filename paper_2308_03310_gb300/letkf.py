@@ -1,0 +1,370 @@
+"""Thin ctypes binding of libletkf (``include/letkf.h``), same names as the C entry points.
+
+Only argument marshalling happens here: every step of the forecast and the
+analysis runs in the library's CUDA kernels.  PyTorch supplies device memory
+(the handle's workspace) and the CUDA stream.  There is no CPU fallback: if the
+shared library has not been built, importing the binding's functions raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from ._build import LIB
+
+LETKF_OK = 0
+LETKF_EINVAL = -1
+LETKF_ENOMEM = -2
+LETKF_ENOTCONV = -3
+LETKF_ENONFINITE = -4
+LETKF_ETIMEOUT = -5
+LETKF_ECUDA = -6
+LETKF_ESTATE = -7
+
+LETKF_HOST = 0
+LETKF_DEVICE = 1
+
+LETKF_OBS_RHO = 1
+LETKF_OBS_U = 2
+LETKF_OBS_V = 4
+
+LETKF_LOC_NONE = 0
+LETKF_LOC_GAUSS = 1
+
+LETKF_FP32 = 0
+LETKF_MIXED = 1
+
+# Every symbol include/letkf.h declares, in declaration order.
+EXPORTED = (
+    "letkf_workspace_size", "letkf_init", "letkf_sync", "letkf_destroy", "letkf_strerror",
+    "letkf_get_stats", "letkf_enable_timing", "letkf_get_timings", "letkf_set_state", "letkf_get_state", "letkf_set_deviation",
+    "letkf_get_deviation", "letkf_set_macro", "lbm_forecast",
+    "letkf_get_obs", "letkf_analyze", "letkf_analyze_probe", "letkf_cycle",
+)
+
+
+class letkf_config(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("k", C.c_int32), ("n_aux", C.c_int32),
+        ("tau", C.c_float), ("force", C.POINTER(C.c_float)),
+        ("n_obs", C.c_int32), ("obs_xy", C.POINTER(C.c_int32)), ("obs_vars", C.c_int32),
+        ("obs_err_var", C.POINTER(C.c_float)), ("loc_kind", C.c_int32),
+        ("loc_radius", C.c_float), ("loc_cutoff2", C.c_float), ("infl", C.c_float),
+        ("precision", C.c_int32), ("chunk_bytes", C.c_int64), ("stream", C.c_void_p),
+    ]
+
+
+class letkf_stats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n_points", C.c_int32), ("n_zero_obs", C.c_int32),
+                ("max_local_obs", C.c_int32), ("mean_local_obs", C.c_double),
+                ("n_chunks", C.c_int32)]
+
+
+class letkf_timings(C.Structure):
+    _fields_ = [("forecast_ms", C.c_float), ("forecast_steps", C.c_int32), ("obs_ms", C.c_float),
+                ("transpose_in_ms", C.c_float), ("gram_ms", C.c_float), ("eigen_ms", C.c_float),
+                ("transpose_out_ms", C.c_float), ("n_chunks", C.c_int32)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class letkf_probe(C.Structure):
+    _fields_ = [("n_points", C.c_int32), ("points", C.POINTER(C.c_int32)),
+                ("nloc", C.POINTER(C.c_int32)), ("gram", C.POINTER(C.c_float)),
+                ("cvec", C.POINTER(C.c_float)), ("eigval", C.POINTER(C.c_float)),
+                ("xf", C.POINTER(C.c_float))]
+
+
+class LetkfError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+_lib = None
+
+
+def load(path: str = LIB):
+    """Load libletkf.so (built in tree by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libletkf.so not found at {path}: build it first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    sig = {
+        "letkf_workspace_size": (C.c_int, [C.POINTER(letkf_config), C.POINTER(C.c_size_t)]),
+        "letkf_init": (C.c_int, [C.POINTER(letkf_config), P, C.c_size_t, C.POINTER(P)]),
+        "letkf_sync": (C.c_int, [P]),
+        "letkf_destroy": (C.c_int, [P]),
+        "letkf_strerror": (C.c_char_p, [C.c_int]),
+        "letkf_get_stats": (C.c_int, [P, C.POINTER(letkf_stats)]),
+        "letkf_enable_timing": (C.c_int, [P, C.c_int32]),
+        "letkf_get_timings": (C.c_int, [P, C.POINTER(letkf_timings)]),
+        "letkf_set_state": (C.c_int, [P, P, C.c_int32, C.c_int32, C.c_int32]),
+        "letkf_get_state": (C.c_int, [P, P, C.c_int32, C.c_int32, C.c_int32]),
+        "letkf_set_deviation": (C.c_int, [P, P, C.c_int32, C.c_int32, C.c_int32]),
+        "letkf_get_deviation": (C.c_int, [P, P, C.c_int32, C.c_int32, C.c_int32]),
+        "letkf_set_macro": (C.c_int, [P, P, P, P, C.c_int32, C.c_int32, C.c_int32]),
+        "lbm_forecast": (C.c_int, [P, C.c_int32]),
+        "letkf_get_obs": (C.c_int, [P, P, C.c_int32]),
+        "letkf_analyze": (C.c_int, [P, P, C.c_int32]),
+        "letkf_analyze_probe": (C.c_int, [P, P, C.c_int32, C.POINTER(letkf_probe)]),
+        "letkf_cycle": (C.c_int, [P, C.c_int32, P, C.c_int32]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    return load().letkf_strerror(int(code)).decode()
+
+
+def _check(rc, where):
+    if rc != LETKF_OK:
+        raise LetkfError(rc, where)
+
+
+# ---------------------------------------------------------------- raw ABI, same names
+
+def letkf_workspace_size(cfg: letkf_config) -> int:
+    n = C.c_size_t(0)
+    _check(load().letkf_workspace_size(C.byref(cfg), C.byref(n)), "letkf_workspace_size")
+    return n.value
+
+
+def letkf_init(cfg: letkf_config, workspace_ptr: int = 0, workspace_bytes: int = 0) -> int:
+    h = C.c_void_p(0)
+    _check(load().letkf_init(C.byref(cfg), C.c_void_p(workspace_ptr or None), workspace_bytes,
+                             C.byref(h)), "letkf_init")
+    return h.value
+
+
+def letkf_sync(h: int) -> int:
+    return load().letkf_sync(C.c_void_p(h))
+
+
+def letkf_destroy(h: int) -> None:
+    load().letkf_destroy(C.c_void_p(h))
+
+
+def letkf_get_stats(h: int) -> letkf_stats:
+    st = letkf_stats()
+    _check(load().letkf_get_stats(C.c_void_p(h), C.byref(st)), "letkf_get_stats")
+    return st
+
+
+def letkf_enable_timing(h, on):
+    _check(load().letkf_enable_timing(C.c_void_p(h), int(bool(on))), "letkf_enable_timing")
+
+
+def letkf_get_timings(h) -> letkf_timings:
+    t = letkf_timings()
+    _check(load().letkf_get_timings(C.c_void_p(h), C.byref(t)), "letkf_get_timings")
+    return t
+
+
+def letkf_set_state(h, ptr, m0, count, where):
+    _check(load().letkf_set_state(C.c_void_p(h), C.c_void_p(ptr), m0, count, where), "letkf_set_state")
+
+
+def letkf_get_state(h, ptr, m0, count, where):
+    _check(load().letkf_get_state(C.c_void_p(h), C.c_void_p(ptr), m0, count, where), "letkf_get_state")
+
+
+def letkf_set_deviation(h, ptr, m0, count, where):
+    _check(load().letkf_set_deviation(C.c_void_p(h), C.c_void_p(ptr), m0, count, where),
+           "letkf_set_deviation")
+
+
+def letkf_get_deviation(h, ptr, m0, count, where):
+    _check(load().letkf_get_deviation(C.c_void_p(h), C.c_void_p(ptr), m0, count, where),
+           "letkf_get_deviation")
+
+
+def letkf_set_macro(h, rho, ux, uy, m0, count, where):
+    _check(load().letkf_set_macro(C.c_void_p(h), C.c_void_p(rho), C.c_void_p(ux), C.c_void_p(uy),
+                                  m0, count, where), "letkf_set_macro")
+
+
+def lbm_forecast(h, nsteps):
+    _check(load().lbm_forecast(C.c_void_p(h), int(nsteps)), "lbm_forecast")
+
+
+def letkf_get_obs(h, ptr, where):
+    _check(load().letkf_get_obs(C.c_void_p(h), C.c_void_p(ptr), where), "letkf_get_obs")
+
+
+def letkf_analyze(h, yo_ptr, where):
+    _check(load().letkf_analyze(C.c_void_p(h), C.c_void_p(yo_ptr), where), "letkf_analyze")
+
+
+def letkf_analyze_probe(h, yo_ptr, where, probe: letkf_probe):
+    _check(load().letkf_analyze_probe(C.c_void_p(h), C.c_void_p(yo_ptr), where, C.byref(probe)),
+           "letkf_analyze_probe")
+
+
+def letkf_cycle(h, nsteps, yo_ptr, where):
+    _check(load().letkf_cycle(C.c_void_p(h), int(nsteps), C.c_void_p(yo_ptr), where), "letkf_cycle")
+
+
+# ---------------------------------------------------------------- marshalling helpers
+
+def _f32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def _ptr_where(t):
+    """(address, LETKF_HOST/DEVICE) of a float32 numpy array or torch tensor (kept alive by caller)."""
+    if isinstance(t, np.ndarray):
+        if t.dtype != np.float32 or not t.flags.c_contiguous:
+            raise ValueError("expected a C-contiguous float32 array")
+        return t.ctypes.data, LETKF_HOST
+    import torch
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError("expected a contiguous float32 tensor")
+    return t.data_ptr(), (LETKF_DEVICE if t.is_cuda else LETKF_HOST)
+
+
+class Experiment:
+    """One DA experiment: owns a libletkf handle, its torch-allocated workspace and stream."""
+
+    def __init__(self, nx, ny, k, tau, obs_xy, obs_err_var, obs_vars=LETKF_OBS_U | LETKF_OBS_V,
+                 loc_radius=None, loc_cutoff2=0.0, force=None, n_aux=0, infl=1.0,
+                 precision=LETKF_FP32, chunk_bytes=0, stream=None, device=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device if device is not None else "cuda")
+        self.nx, self.ny, self.k, self.n_aux = int(nx), int(ny), int(k), int(n_aux)
+        self.nmem = self.k + self.n_aux
+        self._obs_xy = np.ascontiguousarray(np.asarray(obs_xy, dtype=np.int32).reshape(-1, 2))
+        self._obs_var = _f32(obs_err_var).reshape(-1)
+        self._force = None if force is None else _f32(force).reshape(2, ny, nx)
+        self.V = bin(int(obs_vars) & 7).count("1")
+        self.L = self._obs_xy.shape[0]
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        cfg = letkf_config()
+        cfg.nx, cfg.ny, cfg.k, cfg.n_aux = self.nx, self.ny, self.k, self.n_aux
+        cfg.tau = float(tau)
+        cfg.force = (self._force.ctypes.data_as(C.POINTER(C.c_float)) if self._force is not None
+                     else C.POINTER(C.c_float)())
+        cfg.n_obs = self.L
+        cfg.obs_xy = self._obs_xy.ctypes.data_as(C.POINTER(C.c_int32))
+        cfg.obs_vars = int(obs_vars)
+        cfg.obs_err_var = self._obs_var.ctypes.data_as(C.POINTER(C.c_float))
+        if loc_radius is None:
+            cfg.loc_kind, cfg.loc_radius = LETKF_LOC_NONE, 0.0
+        else:
+            cfg.loc_kind, cfg.loc_radius = LETKF_LOC_GAUSS, float(loc_radius)
+        cfg.loc_cutoff2 = float(loc_cutoff2)
+        cfg.infl = float(infl)
+        cfg.precision = int(precision)
+        cfg.chunk_bytes = int(chunk_bytes)
+        cfg.stream = self.stream.cuda_stream
+        self.cfg = cfg
+        self.workspace_bytes = letkf_workspace_size(cfg)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=self.device)
+            self.h = letkf_init(cfg, self.workspace.data_ptr(), self.workspace_bytes)
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "h", None):
+            letkf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self) -> int:
+        return letkf_sync(self.h)
+
+    def stats(self) -> letkf_stats:
+        return letkf_get_stats(self.h)
+
+    def enable_timing(self, on=True):
+        letkf_enable_timing(self.h, on)
+
+    def timings(self) -> dict:
+        return letkf_get_timings(self.h).as_dict()
+
+    # -- state
+    def set_state(self, f, m0=0):
+        f = _f32(f) if isinstance(f, np.ndarray) else f
+        ptr, where = _ptr_where(f)
+        count = int(np.prod(f.shape)) // (9 * self.nx * self.ny)
+        letkf_set_state(self.h, ptr, m0, count, where)
+
+    def get_state(self, m0=0, count=None):
+        count = self.nmem - m0 if count is None else count
+        out = np.empty((count, 9, self.ny, self.nx), dtype=np.float32)
+        letkf_get_state(self.h, out.ctypes.data, m0, count, LETKF_HOST)
+        return out
+
+    def get_deviation(self, m0=0, count=None):
+        """Device state g = f - w_q (FP32 weights), [count, 9, ny, nx] float32."""
+        count = self.nmem - m0 if count is None else count
+        out = np.empty((count, 9, self.ny, self.nx), dtype=np.float32)
+        letkf_get_deviation(self.h, out.ctypes.data, m0, count, LETKF_HOST)
+        return out
+
+    def set_deviation(self, g, m0=0):
+        g = _f32(g) if isinstance(g, np.ndarray) else g
+        ptr, where = _ptr_where(g)
+        count = int(np.prod(g.shape)) // (9 * self.nx * self.ny)
+        letkf_set_deviation(self.h, ptr, m0, count, where)
+
+    def set_macro(self, rho, ux, uy, m0=0):
+        arrs = [_f32(a) for a in (rho, ux, uy)]
+        count = arrs[0].size // (self.nx * self.ny)
+        letkf_set_macro(self.h, arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data,
+                        m0, count, LETKF_HOST)
+
+    # -- hot path
+    def forecast(self, nsteps):
+        lbm_forecast(self.h, nsteps)
+
+    def get_obs(self):
+        out = np.empty((self.nmem, self.L * self.V), dtype=np.float32)
+        letkf_get_obs(self.h, out.ctypes.data, LETKF_HOST)
+        return out
+
+    def analyze(self, yo):
+        yo = _f32(yo) if isinstance(yo, np.ndarray) else yo
+        ptr, where = _ptr_where(yo)
+        letkf_analyze(self.h, ptr, where)
+
+    def analyze_probe(self, yo, points, want=("nloc", "gram", "cvec", "eigval", "xf")):
+        yo = _f32(yo) if isinstance(yo, np.ndarray) else yo
+        ptr, where = _ptr_where(yo)
+        pts = np.ascontiguousarray(np.asarray(points, dtype=np.int32).reshape(-1))
+        n, k = pts.size, self.k
+        out = {"nloc": np.zeros(n, np.int32), "gram": np.zeros((n, k, k), np.float32),
+               "cvec": np.zeros((n, k), np.float32), "eigval": np.zeros((n, k), np.float32),
+               "xf": np.zeros((n, 9, k), np.float32)}
+        pr = letkf_probe()
+        pr.n_points = n
+        pr.points = pts.ctypes.data_as(C.POINTER(C.c_int32))
+        for name in ("nloc", "gram", "cvec", "eigval", "xf"):
+            typ = C.c_int32 if name == "nloc" else C.c_float
+            setattr(pr, name, out[name].ctypes.data_as(C.POINTER(typ)) if name in want
+                    else C.POINTER(typ)())
+        letkf_analyze_probe(self.h, ptr, where, pr)
+        return {name: out[name] for name in want}
+
+    def cycle(self, nsteps, yo):
+        yo = _f32(yo) if isinstance(yo, np.ndarray) else yo
+        ptr, where = _ptr_where(yo)
+        letkf_cycle(self.h, nsteps, ptr, where)

@@ -1,0 +1,102 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol that
+include/letkf.h declares, and its host-side validation rejects bad problems."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2308_03310_gb300 import _build, letkf as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return L.load()
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "letkf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\([^;{]*\)\s*;", src, flags=re.M)
+    return [n for n in names if n != "if"]
+
+
+def test_header_declarations_match_binding():
+    declared = _declared_functions()
+    assert len(declared) >= 14
+    assert sorted(declared) == sorted(L.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_strerror_names_every_code(lib):
+    for code in range(0, -8, -1):
+        assert L.strerror(code) and L.strerror(code) != "unknown status code"
+    assert L.strerror(-99) == "unknown status code"
+
+
+def _cfg(nx=32, ny=32, k=8, **kw):
+    obs = np.array([[0, 0], [4, 4]], dtype=np.int32)
+    var = np.full(4, 1e-4, dtype=np.float32)
+    cfg = L.letkf_config()
+    cfg.nx, cfg.ny, cfg.k, cfg.n_aux = nx, ny, k, 0
+    cfg.tau = 0.6
+    cfg.n_obs = 2
+    cfg.obs_xy = obs.ctypes.data_as(C.POINTER(C.c_int32))
+    cfg.obs_vars = L.LETKF_OBS_U | L.LETKF_OBS_V
+    cfg.obs_err_var = var.ctypes.data_as(C.POINTER(C.c_float))
+    cfg.loc_kind = L.LETKF_LOC_GAUSS
+    cfg.loc_radius = 3.0
+    cfg.infl = 1.0
+    for key, val in kw.items():
+        setattr(cfg, key, val)
+    cfg._keep = (obs, var)
+    return cfg
+
+
+def test_workspace_size_is_host_only_and_scales(lib):
+    small = L.letkf_workspace_size(_cfg())
+    big = L.letkf_workspace_size(_cfg(nx=64, ny=64))
+    assert small > 0 and big > 3 * small
+    # state double buffer + grid-point-major copy at least
+    assert small >= (2 * 8 * 9 + 9 * 8) * 32 * 32 * 4
+
+
+@pytest.mark.parametrize("field,value", [
+    ("k", 1), ("k", 129), ("nx", 0), ("tau", 0.5), ("obs_vars", 0), ("obs_vars", 8),
+    ("loc_radius", 0.0), ("infl", 0.0), ("n_aux", 5), ("precision", 7), ("loc_kind", 3),
+    ("chunk_bytes", -1)])
+def test_invalid_configurations_are_rejected(lib, field, value):
+    with pytest.raises(L.LetkfError) as e:
+        L.letkf_workspace_size(_cfg(**{field: value}))
+    assert e.value.code == L.LETKF_EINVAL
+
+
+def test_observation_outside_grid_is_rejected(lib):
+    cfg = _cfg()
+    bad = np.array([[0, 0], [32, 4]], dtype=np.int32)
+    cfg.obs_xy = bad.ctypes.data_as(C.POINTER(C.c_int32))
+    with pytest.raises(L.LetkfError):
+        L.letkf_workspace_size(cfg)
+
+
+def test_nonpositive_error_variance_is_rejected(lib):
+    cfg = _cfg()
+    var = np.array([1e-4, 0.0, 1e-4, 1e-4], dtype=np.float32)
+    cfg.obs_err_var = var.ctypes.data_as(C.POINTER(C.c_float))
+    with pytest.raises(L.LetkfError):
+        L.letkf_workspace_size(cfg)
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    assert lib.letkf_sync(None) == L.LETKF_EINVAL
+    assert lib.letkf_destroy(None) == L.LETKF_OK
+    assert lib.lbm_forecast(None, 1) == L.LETKF_EINVAL
+    assert lib.letkf_analyze(None, None, 0) == L.LETKF_EINVAL

@@ -1,0 +1,87 @@
+"""Host-side logic of bench.py, on CPU: clock parsing, roofline arithmetic, the
+multi-rank reductions (world size 2 over gloo) and the reference (oracle) arm."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_parse_clock_csv_reads_median_max_and_reasons():
+    text = ("0, 1900, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Active\n"
+            "0, 1950, 2070, 1000.0, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+            "0, 2000, 2070, 1100.0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+    c = bench.parse_clock_csv(text)
+    assert c["sm_mhz"] == 1950 and c["sm_max_mhz"] == 2070 and c["samples"] == 3
+    assert c["reasons"] == ["sw_power_cap"]
+    assert c["power_w_max"] == 1100.0
+
+
+def test_fp32_peak_from_unit_counts():
+    # 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
+    assert bench.fp32_peak_tflops(2070.0) == pytest.approx(80.55, rel=1e-3)
+
+
+def test_roofline_table_fractions_and_shares():
+    work = {"a": ("GB", 6.8, 100), "b": ("TFLOP", 0.8, 2)}
+    t = bench.roofline_table(work, {"a": 1.0, "b": 3.0}, {"hbm_gbs": 6800.0}, 2070.0)
+    assert t["a"]["achieved"] == pytest.approx(6800.0)
+    assert t["a"]["frac"] == pytest.approx(1.0)
+    assert t["a"]["ms_per_launch"] == pytest.approx(0.01)
+    assert t["b"]["bound"] == "alu" and t["b"]["achieved"] == pytest.approx(800 / 3)
+    assert t["a"]["share"] + t["b"]["share"] == pytest.approx(1.0)
+
+
+def test_whole_job_rate_is_weak_scaling_sum():
+    assert bench.whole_job_rate(1000, 2.0, 4) == 2000.0
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def test_reductions_over_two_gloo_ranks():
+    port = _free_port()
+    code = ("import os, sys, json; sys.path.insert(0, %r); import bench; "
+            "r, w = bench.dist_init('gloo'); "
+            "print(json.dumps([bench.reduce_max(1.0 + r), bench.reduce_sum(10.0 * (r + 1))]))" % ROOT)
+    procs = []
+    for r in range(2):
+        env = dict(os.environ, RANK=str(r), WORLD_SIZE="2", LOCAL_RANK=str(r),
+                   MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), CUDA_VISIBLE_DEVICES="")
+        procs.append(subprocess.Popen([sys.executable, "-c", code], env=env,
+                                      stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
+    outs = [p.communicate(timeout=120) for p in procs]
+    for p, (out, err) in zip(procs, outs):
+        assert p.returncode == 0, err
+        assert json.loads(out.strip().splitlines()[-1]) == [2.0, 30.0]
+
+
+def test_reference_arm_prints_one_oracle_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", "tgv32_k8", "--steps", "1", "--warmup", "0",
+                        "--cpu-sample-seconds", "1"], capture_output=True, text=True, timeout=300,
+                       env=dict(os.environ, CUDA_VISIBLE_DEVICES=""))
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == bench.UNIT
+    assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
+    assert line["config"]["workload"] == "tgv32_k8"
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1", CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference"],
+                       capture_output=True, text=True, timeout=60, env=env)
+    assert r.returncode == 0 and r.stdout.strip() == ""

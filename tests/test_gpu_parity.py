@@ -1,0 +1,351 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, row by row.
+
+Tolerances (relative L2 unless stated):
+  LBM state after 10 steps                1e-6 (FP32 state; the bar the method states)
+  observation operator h(x)               1e-6
+  transposed block, local counts          bit exact (copies and integer decisions)
+  Gram matrix, c vector, eigenvalues      1e-5
+  analysis mean, mean increment,
+  analysis perturbations                  1e-5 (the bar the method states)
+The FP32 path's own error budget: the FP32 eigensolve/transform of a k x k
+problem reproduces the FP64 result to ~1e-6 relative (measured on CPU emulation
+for k = 8..128), an order of magnitude inside the bar.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import lbm, obs as oobs, letkf as oletkf
+from paper_2308_03310_gb300 import _build, letkf as L
+from tests import _cases as C
+
+pytestmark = pytest.mark.gpu
+
+UV = L.LETKF_OBS_U | L.LETKF_OBS_V
+W32 = lbm.W.astype(np.float32)
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _built():
+    _build.build()
+
+
+def make(nx, ny, k, tau=0.6, stride=4, radius=3.0, obs_vars=UV, force=None, n_aux=0, infl=1.0,
+         chunk_bytes=0, obs_xy=None, sigma=0.01):
+    obs_xy = synth.regular_obs_network(nx, ny, stride) if obs_xy is None else obs_xy
+    V = bin(obs_vars).count("1")
+    var = np.full(len(obs_xy) * V, sigma * sigma, dtype=np.float32)
+    exp = L.Experiment(nx, ny, k, tau, obs_xy, var, obs_vars=obs_vars, loc_radius=radius,
+                       force=force, n_aux=n_aux, infl=infl, chunk_bytes=chunk_bytes)
+    return exp, obs_xy, var
+
+
+def forcing(nx, ny, seed=5):
+    fx, fy = synth.kolmogorov_force(nx, ny, 1e-5, 4)
+    rx, ry = synth.band_limited_force(nx, ny, 4.0, 6.0, 1e-5, seed)
+    return np.stack([fx + rx, fy + ry]).astype(np.float32)
+
+
+# ------------------------------------------------------------------ a1: D2Q9 forecast
+
+@pytest.mark.parametrize("nx,ny,k,tau,forced,n_aux", [
+    (32, 32, 8, 0.6, False, 0),     # the Taylor-Green case of the single-cycle workload
+    (37, 29, 5, 0.52, True, 1),     # ragged grid, forced, auxiliary member
+    (256, 64, 4, 0.52, True, 0),    # several 128-wide blocks per row
+])
+def test_lbm_matches_oracle_after_10_steps(nx, ny, k, tau, forced, n_aux):
+    f0 = C.perturb_nonequilibrium(C.ensemble_state(k + n_aux, nx, ny, seed=11), 2e-4, 12)
+    F = forcing(nx, ny) if forced else None
+    exp, _, _ = make(nx, ny, k, tau=tau, force=F, n_aux=n_aux)
+    exp.set_state(f0)
+    exp.forecast(10)
+    got = exp.get_state()
+    assert exp.sync() == 0
+    ref = lbm.run(f0.astype(np.float64), tau, 10,
+                  None if F is None else F[0].astype(np.float64),
+                  None if F is None else F[1].astype(np.float64))
+    err = C.rel_l2(got, ref)
+    assert err < 1e-6, err
+    for m in range(k + n_aux):
+        assert C.rel_l2(got[m], ref[m]) < 1e-6
+    # the deviation from rest, where the dynamics live, read as the device stores it
+    dev_err = C.rel_l2(C.dev64(exp.get_deviation()), ref - lbm.W[:, None, None])
+    assert dev_err < 1e-5, dev_err
+
+
+def test_set_macro_is_the_equilibrium():
+    nx, ny, k = 40, 24, 3
+    ux = synth.gaussian((k, ny, nx), 0.02, 1).astype(np.float32)
+    uy = synth.gaussian((k, ny, nx), 0.02, 2).astype(np.float32)
+    rho = (1.0 + synth.gaussian((k, ny, nx), 1e-3, 3)).astype(np.float32)
+    exp, _, _ = make(nx, ny, k)
+    exp.set_macro(rho, ux, uy)
+    got = exp.get_state()
+    ref = lbm.equilibrium(rho.astype(np.float64), ux.astype(np.float64), uy.astype(np.float64))
+    assert C.rel_l2(got, ref) < 1e-7
+
+
+def test_lbm_conserves_mass_and_gains_the_total_force():
+    nx, ny, k, steps = 256, 256, 2, 100
+    F = forcing(nx, ny)
+    F[0] += 1e-6  # non-zero mean so that the momentum budget is not trivially zero
+    f0 = C.ensemble_state(k, nx, ny, seed=21)
+    exp, _, _ = make(nx, ny, k, tau=0.52, force=F)
+    exp.set_state(f0)
+    exp.forecast(steps)
+    got = exp.get_state().astype(np.float64)
+    for m in range(k):
+        m0, m1 = f0[m].astype(np.float64).sum(), got[m].sum()
+        assert abs(m1 - m0) / m0 < 1e-6
+        p0 = (lbm.CX[:, None, None] * f0[m]).sum()
+        p1 = (lbm.CX[:, None, None] * got[m]).sum()
+        expect = steps * F[0].astype(np.float64).sum()
+        assert abs((p1 - p0) - expect) < 1e-3 * abs(expect) + 1e-6
+
+
+# ------------------------------------------------------------------ a2: observation operator
+
+@pytest.mark.parametrize("obs_vars", [UV, L.LETKF_OBS_RHO | UV, L.LETKF_OBS_V])
+def test_observation_operator_matches_oracle(obs_vars):
+    nx, ny, k = 48, 40, 6
+    f0 = C.ensemble_state(k + 1, nx, ny, seed=31)
+    exp, net, _ = make(nx, ny, k, stride=3, obs_vars=obs_vars, n_aux=1)
+    exp.set_state(f0)
+    got = exp.get_obs()
+    ref = oobs.observe(f0.astype(np.float64), net, obs_vars)
+    assert got.shape == ref.shape
+    assert C.rel_l2(got, ref) < 1e-6
+    # perturbations about the ensemble mean carry their digits too (rho as rho - 1)
+    ybar, dY = oobs.ensemble_obs(ref[:k])
+    gbar = got[:k].astype(np.float64).mean(0)
+    assert C.rel_l2(got[:k] - gbar, dY) < 1e-5
+
+
+# ------------------------------------------------------------------ a3..a8: analysis pieces
+
+def _cfg1_case(seed=41, k=8, nx=32, ny=32, stride=4, radius=3.0, obs_vars=UV, infl=1.0,
+               chunk_bytes=0, force=None):
+    f0 = C.perturb_nonequilibrium(C.ensemble_state(k, nx, ny, seed=seed), 1e-4, seed + 1)
+    truth = C.ensemble_state(1, nx, ny, seed=seed + 7)
+    exp, net, var = make(nx, ny, k, stride=stride, radius=radius, obs_vars=obs_vars, infl=infl,
+                         chunk_bytes=chunk_bytes, force=force)
+    yo = C.observations(truth, net, obs_vars, 0.01, seed + 9)[0]
+    exp.set_state(f0)
+    return exp, f0, yo, net, var
+
+
+def test_transposed_block_and_local_counts_are_exact():
+    exp, f0, yo, net, var = _cfg1_case()
+    pts = np.arange(32 * 32)
+    pr = exp.analyze_probe(yo, pts, want=("nloc", "xf"))
+    assert exp.sync() == 0
+    c2 = synth.loc_cutoff2(3.0)
+    for p in pts:
+        x, y = p % 32, p // 32
+        sel, _ = oletkf.local_obs(x, y, net, 32, 32, c2)
+        assert pr["nloc"][p] == len(sel)
+        expect = C.to_deviation32(f0[:, :, y, x][:, :, None, None])[:, :, 0, 0].T
+        assert np.array_equal(pr["xf"][p], expect)     # the device's g = f - w, moved exactly
+    st = exp.stats()
+    counts = [len(oletkf.local_obs(p % 32, p // 32, net, 32, 32, c2)[0]) for p in pts]
+    assert st.max_local_obs == max(counts) and st.n_zero_obs == counts.count(0)
+    assert st.mean_local_obs == pytest.approx(np.mean(counts))
+
+
+def test_gram_cvec_eigenvalues_match_oracle():
+    exp, f0, yo, net, var = _cfg1_case(seed=51)
+    pts = np.array([0, 1, 31, 32, 33, 500, 777, 1023])
+    pr = exp.analyze_probe(yo, pts, want=("nloc", "gram", "cvec", "eigval"))
+    assert exp.sync() == 0
+    ref = C.oracle_analysis(f0, yo, net, var, 3.0, UV, points=[(p % 32, p // 32) for p in pts])[1]
+    for i, p in enumerate(pts):
+        r = ref[(p % 32, p // 32)]
+        assert pr["nloc"][i] == r["nloc"]
+        assert C.rel_l2(pr["gram"][i], r["A"]) < 1e-5
+        assert C.rel_l2(pr["cvec"][i], r["c"]) < 1e-5
+        assert np.abs(pr["eigval"][i] - r["lam"]).max() < 1e-5 * r["lam"].max()
+
+
+def _flat(a):
+    return np.asarray(a).transpose(0, 2, 3, 1).reshape(a.shape[0], -1)
+
+
+def _full_parity(exp, f0, yo, net, var, radius=3.0, obs_vars=UV, infl=1.0, tol=1e-5):
+    """Analysis of the whole grid against the oracle, compared as deviations from rest
+    (f - w): the FP32 f itself cannot carry the perturbations' digits."""
+    exp.analyze(yo)
+    got = exp.get_state()
+    dev = C.dev64(exp.get_deviation())
+    assert exp.sync() == 0
+    Xa_ref, _ = C.oracle_analysis(f0, yo, net, var, radius, obs_vars, infl=infl)
+    Wb = lbm.W[None, :, None, None]
+    errs = C.point_parity(_flat(dev), _flat(Xa_ref - Wb), _flat(f0.astype(np.float64) - Wb))
+    assert max(errs) < tol, errs
+    assert C.rel_l2(got, Xa_ref) < tol          # the state itself, in f
+    return got, Xa_ref
+
+
+def test_single_cycle_analysis_matches_oracle():
+    exp, f0, yo, net, var = _cfg1_case(seed=61)
+    _full_parity(exp, f0, yo, net, var)
+
+
+def test_single_cycle_forecast_and_analysis_matches_oracle():
+    # the single-cycle workload end to end: 50 steps of the ensemble, then one analysis
+    nx = ny = 32
+    k = 8
+    f0 = C.ensemble_state(k, nx, ny, seed=71)
+    truth = C.ensemble_state(1, nx, ny, seed=72)
+    exp, net, var = make(nx, ny, k)
+    exp.set_state(f0)
+    yo = C.observations(lbm.run(truth.astype(np.float64), 0.6, 50), net, UV, 0.01, 73)[0]
+    exp.cycle(50, yo)
+    dev = C.dev64(exp.get_deviation())
+    assert exp.sync() == 0
+    ff = lbm.run(f0.astype(np.float64), 0.6, 50)
+    Xa_ref, _ = C.oracle_analysis(ff, yo, net, var, 3.0, UV)  # oracle forecast in FP64
+    Wb = lbm.W[None, :, None, None]
+    mean_err, inc_err, pert_err = C.point_parity(_flat(dev), _flat(Xa_ref - Wb), _flat(ff - Wb))
+    assert mean_err < 1e-5 and pert_err < 1e-5, (mean_err, pert_err)
+    # The increment here is measured from the FP64 forecast, so it also carries the FP32
+    # forecast's 50-step rounding (~1e-6 of the mean deviation, which is ~60x the increment);
+    # the analysis-only tests check the increment from identical inputs at 1e-5.
+    assert inc_err < 1e-4, inc_err
+
+
+@pytest.mark.parametrize("k,nx,ny,stride,radius,obs_vars,infl", [
+    (2, 16, 16, 4, 3.0, UV, 1.0),                        # smallest ensemble
+    (5, 21, 19, 3, 2.5, UV, 1.0),                        # k off the 8-grid, ragged grid
+    (24, 20, 20, 4, 3.0, L.LETKF_OBS_RHO | UV, 1.1),     # rho observed, inflation
+    (32, 24, 24, 4, 4.0, UV, 1.0),                       # one warp per matrix exactly
+    (64, 16, 16, 4, 3.0, UV, 1.0),                       # two columns per lane
+    (128, 12, 12, 3, 2.0, UV, 1.0),                      # largest ensemble
+])
+def test_analysis_edge_cases_match_oracle(k, nx, ny, stride, radius, obs_vars, infl):
+    exp, f0, yo, net, var = _cfg1_case(seed=80 + k, k=k, nx=nx, ny=ny, stride=stride,
+                                        radius=radius, obs_vars=obs_vars, infl=infl)
+    _full_parity(exp, f0, yo, net, var, radius=radius, obs_vars=obs_vars, infl=infl)
+
+
+def test_points_without_local_observations_are_unchanged():
+    nx = ny = 32
+    k = 8
+    net = np.array([[3, 3], [20, 5]], dtype=np.int32)
+    f0 = C.ensemble_state(k, nx, ny, seed=91)
+    exp, _, var = make(nx, ny, k, obs_xy=net, radius=2.0)
+    exp.set_state(f0)
+    yo = np.array([0.01, -0.01, 0.0, 0.02], dtype=np.float32)
+    st = exp.stats()
+    assert st.n_zero_obs > 0.5 * nx * ny
+    g0 = exp.get_deviation()
+    _full_parity(exp, f0, yo, net, var, radius=2.0)
+    g1 = exp.get_deviation()
+    c2 = synth.loc_cutoff2(2.0)
+    n_far = 0
+    for y in range(ny):
+        for x in range(nx):
+            if len(oletkf.local_obs(x, y, net, nx, ny, c2)[0]) == 0:   # includes periodic images
+                assert np.array_equal(g1[:, :, y, x], g0[:, :, y, x])
+                n_far += 1
+    assert n_far == st.n_zero_obs
+
+
+def test_no_observations_at_all_is_identity():
+    nx = ny = 16
+    k = 8
+    f0 = C.ensemble_state(k, nx, ny, seed=95)
+    exp, _, _ = make(nx, ny, k, obs_xy=np.zeros((0, 2), np.int32))
+    exp.set_state(f0)
+    exp.analyze(np.zeros(0, np.float32))
+    assert exp.sync() == 0
+    assert np.array_equal(exp.get_state(), f0)
+
+
+def test_infinite_localization_matches_global_etkf():
+    nx, ny, k = 12, 10, 8
+    f0 = C.perturb_nonequilibrium(C.ensemble_state(k, nx, ny, seed=101), 1e-4, 102)
+    net = synth.regular_obs_network(nx, ny, 3)
+    var = np.full(len(net) * 2, 1e-4, dtype=np.float32)
+    exp = L.Experiment(nx, ny, k, 0.6, net, var, loc_radius=None)
+    exp.set_state(f0)
+    truth = C.ensemble_state(1, nx, ny, seed=103)
+    yo = C.observations(truth, net, UV, 0.01, 104)[0]
+    _full_parity(exp, f0, yo, net, var, radius=math.inf)
+    dev = C.dev64(exp.get_deviation())
+    # every point used the same (global) transform: compare with one global ETKF
+    Yf = oobs.observe(f0.astype(np.float64), net, UV)
+    ybar, dY = oobs.ensemble_obs(Yf)
+    g = oletkf.local_analysis(f0.astype(np.float64).reshape(k, -1).T, dY.T, yo - ybar,
+                              1.0 / var.astype(np.float64))
+    ga = g["Xa"] - np.repeat(lbm.W, nx * ny)[:, None]
+    assert C.rel_l2(dev.reshape(k, -1).T - ga.mean(1, keepdims=True),
+                    ga - ga.mean(1, keepdims=True)) < 1e-5
+
+
+# ------------------------------------------------------------------ orchestration
+
+def test_chunked_analysis_is_bitwise_identical():
+    outs = []
+    for chunk in (0, 8 * 32 * 8 * 8 * 4):   # whole grid vs chunks of a few tile rows
+        exp, f0, yo, net, var = _cfg1_case(seed=111, chunk_bytes=chunk)
+        exp.analyze(yo)
+        outs.append(exp.get_state())
+        assert exp.sync() == 0
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_graph_cycle_equals_forecast_then_analyze_and_is_reproducible():
+    F = forcing(32, 32)
+    res = []
+    for mode in ("eager", "graph", "graph"):
+        exp, f0, yo, net, var = _cfg1_case(seed=121, force=F)
+        for c in range(3):   # odd step count flips the ping-pong buffer between cycles
+            if mode == "eager":
+                exp.forecast(7)
+                exp.analyze(yo)
+            else:
+                exp.cycle(7, yo)
+        res.append(exp.get_state())
+        assert exp.sync() == 0
+    assert np.array_equal(res[0], res[1])
+    assert np.array_equal(res[1], res[2])
+
+
+# ------------------------------------------------------------------ full-size workloads, sampled
+
+def _sampled_points(nx, ny, n, seed):
+    rng = synth.generator(seed)
+    pts = {(0, 0), (nx - 1, ny - 1), (0, ny - 1), (nx - 1, 0), (nx // 2, ny // 2)}
+    while len(pts) < n:
+        pts.add((int(rng.integers(nx)), int(rng.integers(ny))))
+    return sorted(pts)
+
+
+@pytest.mark.parametrize("name", ["turb256_k32", "turb1024_k64"])
+def test_full_size_workload_sampled_points_match_oracle(name):
+    w = synth.WORKLOADS[name]
+    nx, ny, k = w.nx, w.ny, w.k
+    f0 = C.big_ensemble_state(k, nx, ny, seed=131)
+    net = w.obs_network()
+    var = w.obs_error_var(len(net) * 2).astype(np.float32)
+    exp = L.Experiment(nx, ny, k, w.tau, net, var, loc_radius=w.loc_radius)
+    exp.set_state(f0)
+    Yf = C.observe_at_points(f0, net, UV)
+    yo = (Yf.mean(0) + synth.gaussian(Yf.shape[1], 0.01, 132)).astype(np.float32)
+    pts = _sampled_points(nx, ny, 40, 133)
+    lin = np.array([y * nx + x for (x, y) in pts])
+    pr = exp.analyze_probe(yo, lin, want=("nloc", "eigval"))
+    got = exp.get_deviation()
+    assert exp.sync() == 0
+    ref = C.oracle_points(f0, Yf, yo, net, var, w.loc_radius, UV, pts)
+    worst = [0.0, 0.0, 0.0]
+    for i, (x, y) in enumerate(pts):
+        r = ref[(x, y)]
+        assert pr["nloc"][i] == r["nloc"]
+        assert np.abs(pr["eigval"][i] - r["lam"]).max() < 1e-5 * r["lam"].max()
+        errs = C.point_parity(C.dev64(got[:, :, y, x][:, :, None, None])[:, :, 0, 0],
+                              r["Xa"].T - lbm.W[None, :], f0[:, :, y, x] - lbm.W[None, :])
+        worst = [max(a, b) for a, b in zip(worst, errs)]
+    assert max(worst) < 1e-5, worst
