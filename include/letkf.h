@@ -203,6 +203,40 @@ int letkf_analyze_probe(letkf_handle *h, const float *yo, int32_t where, letkf_p
  * once per nsteps into a CUDA graph and replayed. */
 int letkf_cycle(letkf_handle *h, int32_t nsteps, const float *yo, int32_t where);
 
+/* ---- local analysis without any device allocation -------------------------------
+ * The paper has no counterpart of this entry point; it serves callers that cannot call
+ * cudaMalloc and therefore cannot create a handle (whose workspace must be allocated by
+ * someone): plugin code that a host framework hands only its input/output device buffers,
+ * processes whose device memory is all reserved by another allocator, or loops in which an
+ * allocation, and the device synchronisation it can imply, is not allowed.
+ *
+ * It runs the analysis steps of Algorithm 1 for npts independent local problems given in the
+ * paper's padded local layout, and allocates nothing: its only scratch (the k x k Gram
+ * matrices, the c vectors, the local counts and a status word) sits in one static device array
+ * of LETKF_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until exit.
+ *   npts       number of grid points (local problems), >= 0
+ *   k          ensemble size, 2..128
+ *   lmaxv      padded local observed scalars per point (l_max V), >= 0
+ *   dy_loc     device [npts][lmaxv][k] obs-space perturbations of the local observations
+ *   d_loc      device [npts][lmaxv]    innovations yo - ybar
+ *   rinv_loc   device [npts][lmaxv]    localized inverse error variances G / sigma^2; 0 marks a
+ *                                      padding row (its dy_loc/d_loc entries are ignored)
+ *   infl       multiplicative inflation (1 = none): Q = (k-1)/infl I + dY^T R_loc^-1 dY
+ *   x          device [npts][9][k] forecast blocks (grid-point-major, any fixed reference such
+ *              as f or f - w), overwritten with the analysis blocks
+ *   stream     cudaStream_t (NULL = legacy default stream)
+ * Returns after the work has finished, with LETKF_OK, LETKF_ENOTCONV or LETKF_ENONFINITE from
+ * the device status; LETKF_EINVAL when npts * (k*k + k + 1) + 64 floats exceed the scratch
+ * (e.g. at most 15,858 points for k = 32, 4,033 for k = 64) or an argument is invalid.
+ * Every call shares the one scratch array: calls that overlap on the GPU (different streams
+ * or threads) race; calls ordered on one stream do not.  Each call clears the status word and
+ * overwrites the scratch of the points it processes.  The first call on a device looks up the
+ * array's device address and prepares the kernels; make it before any stream capture. */
+#define LETKF_NOALLOC_SCRATCH_BYTES (64u << 20)
+int letkf_local_analysis_noalloc(int32_t npts, int32_t k, int32_t lmaxv, const float *dy_loc,
+                                 const float *d_loc, const float *rinv_loc, float infl, float *x,
+                                 void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -42,7 +42,10 @@ EXPORTED = (
     "letkf_get_stats", "letkf_enable_timing", "letkf_get_timings", "letkf_set_state", "letkf_get_state", "letkf_set_deviation",
     "letkf_get_deviation", "letkf_set_macro", "lbm_forecast",
     "letkf_get_obs", "letkf_analyze", "letkf_analyze_probe", "letkf_cycle",
+    "letkf_local_analysis_noalloc",
 )
+
+LETKF_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
 class letkf_config(C.Structure):
@@ -116,6 +119,8 @@ def load(path: str = LIB):
         "letkf_analyze": (C.c_int, [P, P, C.c_int32]),
         "letkf_analyze_probe": (C.c_int, [P, P, C.c_int32, C.POINTER(letkf_probe)]),
         "letkf_cycle": (C.c_int, [P, C.c_int32, P, C.c_int32]),
+        "letkf_local_analysis_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, P, P,
+                                                   C.c_float, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -215,6 +220,14 @@ def letkf_analyze_probe(h, yo_ptr, where, probe: letkf_probe):
 
 def letkf_cycle(h, nsteps, yo_ptr, where):
     _check(load().letkf_cycle(C.c_void_p(h), int(nsteps), C.c_void_p(yo_ptr), where), "letkf_cycle")
+
+
+def letkf_local_analysis_noalloc(npts, k, lmaxv, dy_ptr, d_ptr, rinv_ptr, infl, x_ptr, stream):
+    """Local analyses of npts padded local problems with no device allocation (device pointers).
+    Returns the status code (LETKF_OK, LETKF_EINVAL, LETKF_ENOTCONV, ...) without raising."""
+    return load().letkf_local_analysis_noalloc(int(npts), int(k), int(lmaxv), C.c_void_p(dy_ptr),
+                                               C.c_void_p(d_ptr), C.c_void_p(rinv_ptr),
+                                               float(infl), C.c_void_p(x_ptr), C.c_void_p(stream))
 
 
 # ---------------------------------------------------------------- marshalling helpers
