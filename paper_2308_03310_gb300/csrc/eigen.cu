@@ -8,18 +8,17 @@
 // populations share one transform, Sec. II-B) and c = dY^T R_loc^-1 (yo - ybar).
 //
 // The eigensolver follows the batched-EVD route the paper gives (Sec. III):
-// Householder tridiagonalization Q = H T H^T, then implicit-shift QL on T = Z L Z^T.
-// It runs as one warp per matrix -- the paper's warp-per-batch mapping -- with the
-// matrix in shared memory.  Unlike a plain EVD it never forms V = H Z: the
-// reflectors and the QL rotations are applied to the 10-row right-hand side
-// [dX; c^T] instead (10 k^2 flops instead of 2 k^3 for the back-transform):
-//     C = [dX; c^T] H Z          (rows 0..8: dX V, row 9: (V^T c)^T)
+// Householder tridiagonalization Q = H T H^T, then implicit-shift QL on T = Z L Z^T,
+// then the back-transform V = H Z.  It runs as one warp per matrix -- the paper's
+// warp-per-batch mapping -- with the matrix in shared memory.  W is never formed:
+//     C = [dX; c^T] V            (rows 0..8: dX V, row 9: (V^T c)^T)
 //     mean increment = C[0..8] L^-1 C[9]^T
-//     perturbations  = (sqrt(k-1) C[0..8] L^-1/2) Z^T H^T
-// The tridiagonal (d, e) of the QL phase lives in registers, one element per lane
-// and read through warp shuffles, so the sequential bulge chase needs no shared
-// memory traffic and no intra-warp synchronisation; only the rotation of the
-// lane-owned columns of Z touches shared memory.
+//     perturbations  = (sqrt(k-1) C[0..8] L^-1/2) V^T
+// (two 10 x k x k products instead of the k^3 product that forms W and the 9 k^2 one
+// that applies it).
+// In the QL phase every lane runs the same scalar recurrence on (d, e) in shared
+// memory, and each lane rotates its own columns of Z, carrying one row in registers
+// so that a rotation costs one shared load and one store per lane.
 #include <float.h>
 
 #include "common.cuh"
@@ -34,63 +33,13 @@ constexpr int kRows = 10;      // right-hand-side rows: 9 populations + c
 
 __host__ __device__ inline int smem_floats(int k) {
     const int ld = k + 1;
-    return 2 * k * ld + kRows * ld + 3 * k;
+    const int n = 2 * k * ld + kRows * ld + 5 * k;
+    return (n + 3) & ~3;  // keep every warp's slice 16-byte aligned
 }
 
-template <int NC>
-__device__ __forceinline__ float lane_get(const float (&r)[NC], int idx) {
-    float v = 0.0f;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        const float t = __shfl_sync(kFull, r[c], idx & 31);
-        if ((idx >> 5) == c) v = t;
-    }
-    return v;
-}
-
-template <int NC>
-__device__ __forceinline__ void lane_set(float (&r)[NC], int idx, float v, int lane) {
-#pragma unroll
-    for (int c = 0; c < NC; ++c)
-        if (lane + 32 * c == idx) r[c] = v;
-}
-
-// b <- b H_j for rows 0..nrows-1 of B, H_j = I - tau v v^T acting on indices j+1..k-1.
-template <int NC>
-__device__ __forceinline__ void apply_reflector(float *B, int ld, int nrows, const float *v,
-                                                float tau, int j, int k, int lane) {
-    const int m = k - 1 - j;
-    float part[kRows];
-#pragma unroll
-    for (int r = 0; r < kRows; ++r) part[r] = 0.0f;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        const int t = lane + 32 * c;
-        if (t < m) {
-            const float vt = v[t];
-#pragma unroll
-            for (int r = 0; r < kRows; ++r)
-                if (r < nrows) part[r] = fmaf(B[r * ld + j + 1 + t], vt, part[r]);
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < kRows; ++r)
-        if (r < nrows) part[r] = warp_sum(part[r]) * tau;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        const int t = lane + 32 * c;
-        if (t < m) {
-            const float vt = v[t];
-#pragma unroll
-            for (int r = 0; r < kRows; ++r)
-                if (r < nrows) B[r * ld + j + 1 + t] -= part[r] * vt;
-        }
-    }
-    __syncwarp();
-}
-
-template <int NC>
-__global__ void __launch_bounds__(128) eigen_update_kernel(EigArgs a) {
+// NC = columns per lane (k <= 32 NC); MINB = resident blocks the register budget aims for.
+template <int NC, int MINB>
+__global__ void __launch_bounds__(128, MINB) eigen_update_kernel(EigArgs a) {
     extern __shared__ float smem[];
     const int k = a.k;
     const int ld = k + 1;
@@ -99,9 +48,9 @@ __global__ void __launch_bounds__(128) eigen_update_kernel(EigArgs a) {
     float *S = smem + (size_t)wib * smem_floats(k);
     float *Z = S + k * ld;
     float *B = Z + k * ld;
-    float *wv = B + kRows * ld;   // w = p - K v of the current reflection
-    float *es = wv + k;           // subdiagonal from the reflections
-    float *taus = es + k;         // reflector scalars
+    float2 *vw = reinterpret_cast<float2 *>(B + kRows * ld);  // (v_t, w_t) of the reflection
+    float2 *de = vw + k;                    // tridiagonal (d_t, e_t), e_t couples t and t+1
+    float *taus = reinterpret_cast<float *>(de + k);  // reflector scalars
 
     const int warps_per_block = blockDim.x >> 5;
     const int nw = gridDim.x * warps_per_block;
@@ -114,36 +63,59 @@ __global__ void __launch_bounds__(128) eigen_update_kernel(EigArgs a) {
                 for (int t = lane; t < k; t += 32) a.eigval[(size_t)lp * k + t] = a.diag;
             continue;
         }
-        // ---- Q = diag + A, symmetrised from the upper triangle
-        const float *Ag = a.gram + (size_t)lp * k * k;
-        for (int i = 0; i < k; ++i)
-            for (int j = i + lane; j < k; j += 32) {
-                const float v = Ag[i * k + j];
-                S[i * ld + j] = v;
-                S[j * ld + i] = v;
-            }
+        // ---- Q = diag + A, symmetrised from the upper triangle.  Rows are fetched eight at a
+        // time with every load of a batch issued before its shared stores.
+        const float *__restrict__ Ag = a.gram + (size_t)lp * k * k;
+        for (int i0 = 0; i0 < k; i0 += 8) {
+            float v[8][NC];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const int i = i0 + u, j = lane + 32 * c;
+                    v[u][c] = (i < k && j < k) ? __ldg(Ag + i * k + j) : 0.0f;
+                }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const int i = i0 + u, j = lane + 32 * c;
+                    if (i < k && j < k && j >= i) {
+                        S[i * ld + j] = v[u][c];
+                        S[j * ld + i] = v[u][c];
+                    }
+                }
+        }
         __syncwarp();
         for (int i = lane; i < k; i += 32) S[i * ld + i] += a.diag;
 
         // ---- forecast block: mean and perturbations of the 9 populations, and c
         float *X = a.x + (size_t)(a.pt0 + lp) * NV * k;
+        float xv[NV][NC], cv[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int t = lane + 32 * c;
+#pragma unroll
+            for (int q = 0; q < NV; ++q) xv[q][c] = t < k ? X[q * k + t] : 0.0f;
+            cv[c] = t < k ? __ldg(a.cvec + (size_t)lp * k + t) : 0.0f;
+        }
         float xbar[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
-            float s = 0.0f;
+            float sum = 0.0f;
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const int t = lane + 32 * c;
-                if (t < k) s += X[q * k + t];
-            }
-            xbar[q] = warp_sum(s) / (float)k;
+            for (int c = 0; c < NC; ++c) sum += xv[q][c];
+            xbar[q] = warp_sum(sum) / (float)k;
+        }
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const int t = lane + 32 * c;
-                if (t < k) B[q * ld + t] = X[q * k + t] - xbar[q];
+        for (int c = 0; c < NC; ++c) {
+            const int t = lane + 32 * c;
+            if (t < k) {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) B[q * ld + t] = xv[q][c] - xbar[q];
+                B[9 * ld + t] = cv[c];
             }
         }
-        for (int t = lane; t < k; t += 32) B[9 * ld + t] = a.cvec[(size_t)lp * k + t];
         __syncwarp();
 
         // ---- Householder tridiagonalization, reflector j stored in row j of S
@@ -160,41 +132,65 @@ __global__ void __launch_bounds__(128) eigen_update_kernel(EigArgs a) {
             }
             tail = warp_sum(tail);
             const float alpha = __shfl_sync(kFull, x[0], 0);
+            // H x = beta e_0 with beta = -sign(alpha) ||x||, tau = 1 + |alpha| / ||x||,
+            // v = x / (alpha - beta), v_0 = 1 (one rsqrt, one reciprocal, no division)
             float tau = 0.0f, beta = alpha, scale = 0.0f;
             if (tail > 0.0f) {
-                beta = -copysignf(sqrtf(fmaf(alpha, alpha, tail)), alpha);
-                tau = (beta - alpha) / beta;
-                scale = 1.0f / (alpha - beta);
+                const float n2 = fmaf(alpha, alpha, tail);
+                float rn = rsqrtf(n2);
+                rn = rn * fmaf(-0.5f * n2, rn * rn, 1.5f);
+                const float nrm = n2 * rn;
+                beta = -copysignf(nrm, alpha);
+                tau = fmaf(fabsf(alpha), rn, 1.0f);
+                scale = copysignf(__frcp_rn(fabsf(alpha) + nrm), alpha);
+            }
+            float vt[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int t = lane + 32 * c;
+                vt[c] = t < m ? (t == 0 ? 1.0f : x[c] * scale) : 0.0f;
             }
             __syncwarp();
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 const int t = lane + 32 * c;
-                if (t < m) vj[t] = t == 0 ? 1.0f : x[c] * scale;
+                if (t < m) vj[t] = vt[c];
             }
             if (lane == 0) {
                 taus[j] = tau;
-                es[j] = beta;
+                de[j].y = beta;
             }
             __syncwarp();
             if (tau != 0.0f) {
-                // p = tau S' v, with S' the trailing block (its column t is read by lane t)
-                float pv[NC], vt[NC];
+                // p = tau S' v, with S' the trailing block (its column t is read by lane t);
+                // two accumulators halve the dependent FMA chain
+                float pv[NC], pw[NC];
 #pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    pv[c] = 0.0f;
-                    const int t = lane + 32 * c;
-                    vt[c] = t < m ? vj[t] : 0.0f;
-                }
-                for (int s = 0; s < m; ++s) {
-                    const float vs = vj[s];
-                    const float *rowS = S + (j + 1 + s) * ld + j + 1;
+                for (int c = 0; c < NC; ++c) pv[c] = pw[c] = 0.0f;
+                int s = 0;
+                for (; s + 2 <= m; s += 2) {
+                    const float vs0 = vj[s], vs1 = vj[s + 1];
+                    const float *r0 = S + (j + 1 + s) * ld + j + 1;
 #pragma unroll
                     for (int c = 0; c < NC; ++c) {
                         const int t = lane + 32 * c;
-                        if (t < m) pv[c] = fmaf(rowS[t], vs, pv[c]);
+                        if (t < m) {
+                            pv[c] = fmaf(r0[t], vs0, pv[c]);
+                            pw[c] = fmaf(r0[ld + t], vs1, pw[c]);
+                        }
                     }
                 }
+                if (s < m) {
+                    const float vs0 = vj[s];
+                    const float *r0 = S + (j + 1 + s) * ld + j + 1;
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        const int t = lane + 32 * c;
+                        if (t < m) pv[c] = fmaf(r0[t], vs0, pv[c]);
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < NC; ++c) pv[c] += pw[c];
                 float kk = 0.0f;
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
@@ -207,37 +203,29 @@ __global__ void __launch_bounds__(128) eigen_update_kernel(EigArgs a) {
                 for (int c = 0; c < NC; ++c) {
                     const int t = lane + 32 * c;
                     wvl[c] = pv[c] - K * vt[c];
-                    if (t < m) wv[t] = wvl[c];
+                    if (t < m) vw[t] = make_float2(vt[c], wvl[c]);
                 }
                 __syncwarp();
-                // S' -= v w^T + w v^T
+                // S' -= v w^T + w v^T  (one 8-byte broadcast load of (v_s, w_s) per row)
+#pragma unroll 4
                 for (int s = 0; s < m; ++s) {
-                    const float vs = vj[s];
-                    const float ws = wv[s];
+                    const float2 p2 = vw[s];
                     float *rowS = S + (j + 1 + s) * ld + j + 1;
 #pragma unroll
                     for (int c = 0; c < NC; ++c) {
                         const int t = lane + 32 * c;
-                        if (t < m) rowS[t] -= fmaf(vs, wvl[c], ws * vt[c]);
+                        if (t < m) rowS[t] -= fmaf(p2.x, wvl[c], p2.y * vt[c]);
                     }
                 }
                 __syncwarp();
             }
         }
-        // ---- tridiagonal into lane registers: lane t holds d_t, e_t (e_t couples t, t+1)
-        float dr[NC], er[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            const int t = lane + 32 * c;
-            dr[c] = t < k ? S[t * ld + t] : 0.0f;
-            er[c] = t < k - 2 ? es[t] : (t == k - 2 ? S[t * ld + t + 1] : 0.0f);
+        // ---- tridiagonal (d, e) into shared memory, e_t couples t and t+1; Z = I
+        for (int t = lane; t < k; t += 32) {
+            de[t].x = S[t * ld + t];
+            if (t == k - 2) de[t].y = S[t * ld + t + 1];
+            if (t == k - 1) de[t].y = 0.0f;
         }
-        // ---- reflectors applied to the right-hand side [dX; c^T]
-        for (int j = 0; j < k - 2; ++j) {
-            const float tau = taus[j];
-            if (tau != 0.0f) apply_reflector<NC>(B, ld, kRows, S + j * ld + j + 1, tau, j, k, lane);
-        }
-        // ---- Z = I
         for (int i = 0; i < k; ++i)
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
@@ -246,7 +234,13 @@ __global__ void __launch_bounds__(128) eigen_update_kernel(EigArgs a) {
             }
         __syncwarp();
 
-        // ---- implicit-shift QL on (d, e); Z accumulates the rotations (Z[i][:] = column i)
+        // ---- implicit-shift QL on (d, e); Z accumulates the rotations (Z[i][:] = column i).
+        // Every lane runs the same scalar recurrence; d and e are read from shared memory
+        // (the next index is fetched one rotation ahead, off the dependency chain) and each
+        // rotation's results are written by all lanes with identical values, ordered by one
+        // __syncwarp per rotation.  The rotation needs 1/sqrt(f^2 + g^2): MUFU rsqrt refined
+        // by one Newton step; there is no branch on the hot path other than the underflow
+        // exit of the classical algorithm.
         bool notconv = false;
         for (int l = 0; l < k; ++l) {
             int iter = 0;
@@ -256,11 +250,11 @@ __global__ void __launch_bounds__(128) eigen_update_kernel(EigArgs a) {
 #pragma unroll
                 for (int c = NC - 1; c >= 0; --c) {
                     const int t = lane + 32 * c;
-                    const float dn0 = __shfl_down_sync(kFull, dr[c], 1);
-                    const float dn1 = (c + 1 < NC) ? __shfl_sync(kFull, dr[c + 1 < NC ? c + 1 : c], 0) : 0.0f;
-                    const float dnext = lane == 31 ? dn1 : dn0;
-                    const bool small = t >= l && t < k - 1 &&
-                                       fabsf(er[c]) <= eps * (fabsf(dr[c]) + fabsf(dnext));
+                    bool small = false;
+                    if (t >= l && t < k - 1) {
+                        const float2 a0 = de[t];
+                        small = fabsf(a0.y) <= eps * (fabsf(a0.x) + fabsf(de[t + 1].x));
+                    }
                     const unsigned bal = __ballot_sync(kFull, small);
                     if (bal) msplit = 32 * c + __ffs(bal) - 1;
                 }
@@ -271,55 +265,112 @@ __global__ void __launch_bounds__(128) eigen_update_kernel(EigArgs a) {
                     break;
                 }
                 // shift: eigenvalue of the leading 2 x 2 block nearer to d_l
-                const float dl = lane_get<NC>(dr, l);
-                const float el = lane_get<NC>(er, l);
-                const float dl1 = lane_get<NC>(dr, l + 1);
+                const float2 del = de[l];
+                const float dl = del.x, el = del.y, dl1 = de[l + 1].x;
                 const float th = (dl1 - dl) / (2.0f * el);
                 const float rt = hypotf(th, 1.0f);
-                float g = lane_get<NC>(dr, m) - dl + el / (th + copysignf(rt, th));
+                float di1 = de[m].x;
+                float g = di1 - dl + el / (th + copysignf(rt, th));
                 float s = 1.0f, co = 1.0f, pacc = 0.0f;
-                float di1 = lane_get<NC>(dr, m);
+                float zc[NC];  // carried column entries of row i+1 of Z
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const int t = lane + 32 * c;
+                    zc[c] = t < k ? Z[m * ld + t] : 0.0f;
+                }
+                float ei = de[m - 1].y, di = de[m - 1].x;
                 bool underflow = false;
-                for (int i = m - 1; i >= l; --i) {
-                    const float ei = lane_get<NC>(er, i);
-                    const float di = lane_get<NC>(dr, i);
+                int i = m - 1;
+                float *zp = Z + i * ld + lane;  // row i of Z at this lane's first column
+                for (; i >= l; --i) {
+                    // next index fetched ahead; at i == l == 0 this reads the pair before de,
+                    // which lies inside this warp's slice and is never used
+                    const float2 dnext = de[i - 1];
                     const float f = s * ei, b = co * ei;
-                    float r = hypotf(f, g);
-                    lane_set<NC>(er, i + 1, r, lane);
-                    if (r == 0.0f) {
-                        lane_set<NC>(dr, i + 1, di1 - pacc, lane);
-                        lane_set<NC>(er, m, 0.0f, lane);
+                    const float ff = fmaf(f, f, g * g);
+                    __syncwarp();   // every lane has read index i+1 before it is rewritten
+                    if (ff < 1e-30f) {  // f and g vanish: the coupling has underflowed
+                        de[i + 1] = make_float2(di1 - pacc, 0.0f);
+                        de[m].y = 0.0f;
                         underflow = true;
                         break;
                     }
-                    const float rinv = 1.0f / r;
+                    float rinv = rsqrtf(ff);
+                    rinv = rinv * fmaf(-0.5f * ff, rinv * rinv, 1.5f);
+                    const float enew = ff * rinv;
                     s = f * rinv;
                     co = g * rinv;
                     g = di1 - pacc;
-                    r = (di - g) * s + 2.0f * co * b;
+                    const float r = (di - g) * s + 2.0f * co * b;
                     pacc = s * r;
-                    lane_set<NC>(dr, i + 1, g + pacc, lane);
+                    de[i + 1] = make_float2(g + pacc, enew);
                     g = co * r - b;
-                    // Z <- Z G_i on columns i, i+1 (rows i, i+1 of the stored transpose)
+                    // Z <- Z G_i on columns i, i+1: row i+1 is final, row i is carried on
 #pragma unroll
                     for (int c = 0; c < NC; ++c) {
-                        const int t = lane + 32 * c;
-                        if (t < k) {
-                            float *zi = Z + i * ld + t;
-                            const float za = zi[0], zb = zi[ld];
-                            zi[ld] = s * za + co * zb;
-                            zi[0] = co * za - s * zb;
+                        if (lane + 32 * c < k) {
+                            const float za = zp[32 * c];
+                            zp[ld + 32 * c] = s * za + co * zc[c];
+                            zc[c] = co * za - s * zc[c];
                         }
                     }
+                    zp -= ld;
                     di1 = di;
+                    ei = dnext.y;
+                    di = dnext.x;
                 }
-                if (underflow) continue;
-                lane_set<NC>(dr, l, di1 - pacc, lane);
-                lane_set<NC>(er, l, g, lane);
-                lane_set<NC>(er, m, 0.0f, lane);
+                // the carried row: row i+1 after an underflow break, row l after a full sweep
+                const int last = underflow ? i + 1 : l;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const int t = lane + 32 * c;
+                    if (t < k) Z[last * ld + t] = zc[c];
+                }
+                __syncwarp();
+                if (!underflow) {
+                    de[l] = make_float2(di1 - pacc, g);
+                    de[m].y = 0.0f;
+                }
+                __syncwarp();
             }
         }
         if (notconv && lane == 0) atomicOr(a.status, ST_NOTCONV);
+        __syncwarp();
+        float dr[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int t = lane + 32 * c;
+            dr[c] = t < k ? de[t].x : 1.0f;
+        }
+
+        // ---- V = H Z: the reflectors applied from the left, innermost first.  Lane owns
+        // column col of Z (a stored row, odd stride: no bank conflicts); every lane is busy
+        // and no cross-lane reduction is needed.
+        for (int j = k - 3; j >= 0; --j) {
+            const float tau = taus[j];
+            if (tau == 0.0f) continue;
+            const int m = k - 1 - j;
+            const float *v = S + j * ld + j + 1;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int col = lane + 32 * c;
+                if (col < k) {
+                    float *zc_ = Z + col * ld + j + 1;
+                    float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, d3 = 0.0f;
+                    int t = 0;
+                    for (; t + 4 <= m; t += 4) {
+                        d0 = fmaf(v[t], zc_[t], d0);
+                        d1 = fmaf(v[t + 1], zc_[t + 1], d1);
+                        d2 = fmaf(v[t + 2], zc_[t + 2], d2);
+                        d3 = fmaf(v[t + 3], zc_[t + 3], d3);
+                    }
+                    for (; t < m; ++t) d0 = fmaf(v[t], zc_[t], d0);
+                    const float beta = ((d0 + d1) + (d2 + d3)) * tau;
+#pragma unroll 4
+                    for (t = 0; t < m; ++t) zc_[t] = fmaf(-beta, v[t], zc_[t]);
+                }
+            }
+        }
         __syncwarp();
 
         if (a.eigval)
@@ -329,7 +380,7 @@ __global__ void __launch_bounds__(128) eigen_update_kernel(EigArgs a) {
                 if (t < k) a.eigval[(size_t)lp * k + t] = dr[c];
             }
 
-        // ---- C = B Z^T-stored (C[r][j] = sum_i B[r][i] Z[j][i]); lane owns columns j
+        // ---- C = B V (C[r][j] = sum_i B[r][i] V[i][j], V[i][j] stored at Z[j][i]); lane owns j
         float C[NC][kRows];
 #pragma unroll
         for (int c = 0; c < NC; ++c)
@@ -376,7 +427,7 @@ __global__ void __launch_bounds__(128) eigen_update_kernel(EigArgs a) {
                 for (int q = 0; q < NV; ++q) B[q * ld + t] = C[c][q];
         }
         __syncwarp();
-        // ---- E = D Z^T: E[q][i] = sum_j D[q][j] Z[j][i]; lane owns columns i
+        // ---- F = D V^T: F[q][i] = sum_j D[q][j] V[i][j]; lane owns columns i
         float E[NC][NV];
 #pragma unroll
         for (int c = 0; c < NC; ++c)
@@ -403,11 +454,6 @@ __global__ void __launch_bounds__(128) eigen_update_kernel(EigArgs a) {
                 for (int q = 0; q < NV; ++q) B[q * ld + t] = E[c][q];
         }
         __syncwarp();
-        // ---- F = E H^T: reflectors in reverse order on the 9 population rows
-        for (int j = k - 3; j >= 0; --j) {
-            const float tau = taus[j];
-            if (tau != 0.0f) apply_reflector<NC>(B, ld, NV, S + j * ld + j + 1, tau, j, k, lane);
-        }
         // ---- X^a = xbar + increment + perturbation, in place
         bool bad = false;
 #pragma unroll
@@ -428,26 +474,40 @@ __global__ void __launch_bounds__(128) eigen_update_kernel(EigArgs a) {
     }
 }
 
+constexpr int kSmemPerSm = 227 * 1024;
+
 template <int NC>
+constexpr int min_blocks() { return NC == 1 ? 5 : 1; }
+
+// Warps per block (1..4) that let the most warps share an SM's shared memory.
 int warps_per_block(int k) {
-    const size_t per_warp = (size_t)smem_floats(k) * sizeof(float);
-    int warps = (int)((200 * 1024) / per_warp);
-    return warps < 1 ? 1 : (warps > 4 ? 4 : warps);
+    const int per_warp = smem_floats(k) * (int)sizeof(float);
+    const int max_warps = kSmemPerSm / per_warp;
+    int best = 1, best_total = 0;
+    for (int w = 4; w >= 1; --w) {
+        const int total = (kSmemPerSm / (w * per_warp)) * w;
+        if (total > best_total) {
+            best = w;
+            best_total = total;
+        }
+        if (total == max_warps) break;
+    }
+    return best;
 }
 
 template <int NC>
 cudaError_t prepare_nc(int k, int *max_blocks) {
-    const int warps = warps_per_block<NC>(k);
+    const int warps = warps_per_block(k);
     const size_t smem = (size_t)smem_floats(k) * sizeof(float) * warps;
-    cudaError_t e = cudaFuncSetAttribute(eigen_update_kernel<NC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = eigen_update_kernel<NC, min_blocks<NC>()>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eigen_update_kernel<NC>, 32 * warps,
-                                                      smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     *max_blocks = sms * per_sm;
@@ -456,12 +516,12 @@ cudaError_t prepare_nc(int k, int *max_blocks) {
 
 template <int NC>
 cudaError_t launch_nc(const EigArgs &a, cudaStream_t s) {
-    const int warps = warps_per_block<NC>(a.k);
+    const int warps = warps_per_block(a.k);
     const size_t smem = (size_t)smem_floats(a.k) * sizeof(float) * warps;
     long long need = ((long long)a.npts + warps - 1) / warps;
     long long blocks = a.max_blocks > 0 ? a.max_blocks : 1;
     if (blocks > need) blocks = need;
-    eigen_update_kernel<NC><<<(unsigned)blocks, 32 * warps, smem, s>>>(a);
+    eigen_update_kernel<NC, min_blocks<NC>()><<<(unsigned)blocks, 32 * warps, smem, s>>>(a);
     return cudaGetLastError();
 }
 
