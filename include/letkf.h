@@ -52,8 +52,10 @@ extern "C" {
 #define LETKF_LOC_NONE  0      /* G = 1 for every observation ("infinite")    */
 #define LETKF_LOC_GAUSS 1      /* G = exp(-d^2/(2 r^2)) for d^2 < cutoff^2    */
 
-#define LETKF_FP32  0          /* plain FP32 CUDA-core analysis               */
-#define LETKF_MIXED 1          /* reserved for the split-precision form       */
+#define LETKF_FP32  0          /* plain FP32 CUDA-core analysis                                */
+#define LETKF_MIXED 1          /* split-precision: for 33 <= k <= 128 the localized Gram runs on
+                                  the tensor cores (tcgen05, FP16 hi+lo operands, FP32
+                                  accumulation); for k <= 32 it stays on CUDA cores         */
 
 /* ---- problem statement --------------------------------------------------
  * Follows the paper's statement of the problem (Sec. II-B): the grid, the
@@ -78,9 +80,9 @@ typedef struct letkf_config {
                                   i.e. cutoff 2 sqrt(10/3) r                            */
     float   infl;              /* multiplicative inflation rho: Q = (k-1)/rho I + ...;
                                   1 = none (the paper's Eq. letkf_q)                    */
-    int32_t precision;         /* LETKF_FP32 (LETKF_MIXED is rejected for now)          */
+    int32_t precision;         /* LETKF_FP32 or LETKF_MIXED                             */
     int64_t chunk_bytes;       /* device bytes for the per-point k x k Gram buffer;
-                                  0 = default (64 MiB)                                  */
+                                  0 = default (256 MiB)                                 */
     void   *stream;            /* cudaStream_t to run on; NULL = a stream the handle
                                   creates and owns                                       */
 } letkf_config;

@@ -23,7 +23,7 @@
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int64_t kDefaultChunkBytes = 64ll << 20;
+constexpr int64_t kDefaultChunkBytes = 256ll << 20;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -36,6 +36,7 @@ struct Plan {
     size_t npts = 0;
     int nmem = 0, V = 0, LV = 0, kp = 0;
     int tile_w = 1, tile_h = 1;
+    bool tensor_gram = false;  // mixed precision with k in 33..128: tcgen05 split-FP16 Gram
     int chunk_rows = 0;
     size_t chunk_pts = 0;
     int cs = 8, ncx = 1, ncy = 1;
@@ -58,7 +59,7 @@ int validate(const letkf_config *c) {
     if (c->loc_kind == LETKF_LOC_GAUSS && !(c->loc_radius > 0.0f && isfinite(c->loc_radius)))
         return LETKF_EINVAL;
     if (!(c->infl > 0.0f) || !isfinite(c->infl)) return LETKF_EINVAL;
-    if (c->precision != LETKF_FP32) return LETKF_EINVAL;
+    if (c->precision != LETKF_FP32 && c->precision != LETKF_MIXED) return LETKF_EINVAL;
     if (c->chunk_bytes < 0) return LETKF_EINVAL;
     const int V = popcount3(c->obs_vars);
     for (int l = 0; l < c->n_obs; ++l) {
@@ -82,6 +83,11 @@ int make_plan(const letkf_config *c, Plan *p) {
     p->kp = kp_of(c->k);
     p->tile_w = lk::gram_tile_width(p->kp);
     p->tile_h = lk::gram_tile_height(p->kp);
+    p->tensor_gram = c->precision == LETKF_MIXED && p->kp >= 64;
+    if (p->tensor_gram) {  // the bins must fit either kernel's tile patch
+        p->tile_w = std::max(p->tile_w, lk::gram_tc_tile_width(p->kp));
+        p->tile_h = std::max(p->tile_h, lk::gram_tc_tile_height(p->kp));
+    }
     // localization: integer threshold of the strict cutoff d^2 < c^2 (Sec. II-B)
     if (c->loc_kind == LETKF_LOC_GAUSS) {
         const double r = c->loc_radius;
@@ -170,6 +176,7 @@ struct letkf_handle {
     lk::ObsNet net;
     float yref[3] = {0, 0, 0};
     int eig_blocks = 0;
+    int tc_ctas = 0;
     letkf_stats stats;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int graph_nsteps[2] = {-1, -1};
@@ -305,7 +312,10 @@ int enqueue_analysis(letkf_handle *h, letkf_probe *probe) {
         g.gram = h->gram;
         g.cvec = h->cvec;
         g.nloc = h->nloc;
-        CK(lk::launch_gram(g, h->stream));
+        if (p.tensor_gram)
+            CK(lk::launch_gram_tc(g, h->status, h->tc_ctas, h->stream));
+        else
+            CK(lk::launch_gram(g, h->stream));
         if ((rc = mark(h, 5 + 2 * chunk))) return rc;
         const long long pt0 = (long long)y0 * c.nx;
         const int npts = (y1 - y0) * c.nx;
@@ -512,6 +522,13 @@ int letkf_init(const letkf_config *cfg, void *workspace, size_t workspace_bytes,
     if (lk::gram_prepare(plan.kp) != cudaSuccess ||
         lk::eigen_prepare(cfg->k, &h->eig_blocks) != cudaSuccess)
         return fail(LETKF_ECUDA);
+    if (plan.tensor_gram) {
+        int sms = 0;
+        if (lk::gram_tc_prepare(plan.kp) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess)
+            return fail(LETKF_ECUDA);
+        h->tc_ctas = sms;  // one CTA per SM: each holds all 512 tensor-memory columns
+    }
     // rest state, clean status, zero Gram buffers
     if (cudaMemsetAsync(h->state[0], 0, (size_t)plan.nmem * 9 * npts * sizeof(float), h->stream) ||
         cudaMemsetAsync(h->status, 0, kAlign, h->stream) ||

@@ -43,9 +43,13 @@ __device__ __forceinline__ int posmod(int a, int n) {  // n > 0
     return r < 0 ? r + n : r;
 }
 
-// Periodic minimum-image displacement on a ring of n cells, in [-n/2, n - n/2).
+// Periodic minimum-image displacement on a ring of n cells, in [-n/2, n - n/2), for
+// -n < d < n (a difference of two coordinates on the ring): two compares, no division.
 __device__ __forceinline__ int min_image(int d, int n) {
-    return posmod(d + n / 2, n) - n / 2;
+    const int h = n >> 1;
+    d -= d >= n - h ? n : 0;
+    d += d < -h ? n : 0;
+    return d;
 }
 
 // The coordinate interval [c0, c1] of a periodic axis of n cells, as at most two ranges of

@@ -33,24 +33,36 @@ constexpr int kRows = 10;      // right-hand-side rows: 9 populations + c
 
 __host__ __device__ inline int smem_floats(int k) {
     const int ld = k + 1;
-    const int n = 2 * k * ld + kRows * ld + 5 * k;
+    const int n = k * ld + kRows * ld + 6 * k;
     return (n + 3) & ~3;  // keep every warp's slice 16-byte aligned
 }
 
-// NC = columns per lane (k <= 32 NC); MINB = resident blocks the register budget aims for.
-template <int NC, int MINB>
-__global__ void __launch_bounds__(128, MINB) eigen_update_kernel(EigArgs a) {
+// Block shape per NC (columns per lane): warps per block and the resident blocks per SM that
+// the register budget targets, chosen with the shared memory per matrix (k x (k+1) + 10 (k+1)
+// + 6k floats) so that registers and shared memory allow the same number of matrices in flight.
+template <int NC>
+struct EigCfg {
+    static constexpr int WARPS = NC == 1 ? 4 : (NC == 2 ? 2 : 1);
+    static constexpr int MINB = NC == 1 ? 5 : (NC == 2 ? 5 : 3);
+};
+
+template <int NC>
+__global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB)
+    eigen_update_kernel(EigArgs a) {
     extern __shared__ float smem[];
     const int k = a.k;
     const int ld = k + 1;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
+    // S holds Q during the tridiagonalization; its reflectors are then kept in the point's
+    // (already consumed) Gram slot in global memory, and Z reuses S's shared memory.
     float *S = smem + (size_t)wib * smem_floats(k);
-    float *Z = S + k * ld;
-    float *B = Z + k * ld;
+    float *Z = S;
+    float *B = S + k * ld;
     float2 *vw = reinterpret_cast<float2 *>(B + kRows * ld);  // (v_t, w_t) of the reflection
     float2 *de = vw + k;                    // tridiagonal (d_t, e_t), e_t couples t and t+1
     float *taus = reinterpret_cast<float *>(de + k);  // reflector scalars
+    float *vtmp = taus + k;                 // one reflector, back in shared memory
 
     const int warps_per_block = blockDim.x >> 5;
     const int nw = gridDim.x * warps_per_block;
@@ -65,7 +77,7 @@ __global__ void __launch_bounds__(128, MINB) eigen_update_kernel(EigArgs a) {
         }
         // ---- Q = diag + A, symmetrised from the upper triangle.  Rows are fetched eight at a
         // time with every load of a batch issued before its shared stores.
-        const float *__restrict__ Ag = a.gram + (size_t)lp * k * k;
+        float *Ag = a.gram + (size_t)lp * k * k;
         for (int i0 = 0; i0 < k; i0 += 8) {
             float v[8][NC];
 #pragma unroll
@@ -73,7 +85,7 @@ __global__ void __launch_bounds__(128, MINB) eigen_update_kernel(EigArgs a) {
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
                     const int i = i0 + u, j = lane + 32 * c;
-                    v[u][c] = (i < k && j < k) ? __ldg(Ag + i * k + j) : 0.0f;
+                    v[u][c] = (i < k && j < k) ? __ldcg(Ag + i * k + j) : 0.0f;
                 }
 #pragma unroll
             for (int u = 0; u < 8; ++u)
@@ -154,7 +166,10 @@ __global__ void __launch_bounds__(128, MINB) eigen_update_kernel(EigArgs a) {
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 const int t = lane + 32 * c;
-                if (t < m) vj[t] = vt[c];
+                if (t < m) {
+                    vj[t] = vt[c];
+                    Ag[j * k + j + 1 + t] = vt[c];  // reflector j kept in row j of the slot
+                }
             }
             if (lane == 0) {
                 taus[j] = tau;
@@ -220,12 +235,13 @@ __global__ void __launch_bounds__(128, MINB) eigen_update_kernel(EigArgs a) {
                 __syncwarp();
             }
         }
-        // ---- tridiagonal (d, e) into shared memory, e_t couples t and t+1; Z = I
+        // ---- tridiagonal (d, e) into shared memory, e_t couples t and t+1; Z = I over S
         for (int t = lane; t < k; t += 32) {
             de[t].x = S[t * ld + t];
             if (t == k - 2) de[t].y = S[t * ld + t + 1];
             if (t == k - 1) de[t].y = 0.0f;
         }
+        __syncwarp();
         for (int i = 0; i < k; ++i)
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
@@ -345,33 +361,53 @@ __global__ void __launch_bounds__(128, MINB) eigen_update_kernel(EigArgs a) {
 
         // ---- V = H Z: the reflectors applied from the left, innermost first.  Lane owns
         // column col of Z (a stored row, odd stride: no bank conflicts); every lane is busy
-        // and no cross-lane reduction is needed.
+        // and no cross-lane reduction is needed.  Reflector j comes back from row j of the
+        // point's Gram slot (L2), fetched one reflector ahead.
+        float vnext[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int t = lane + 32 * c, m0 = 2;  // reflector k-3 has m = 2
+            vnext[c] = (k >= 3 && t < m0) ? __ldcg(Ag + (k - 3) * k + (k - 2) + t) : 0.0f;
+        }
         for (int j = k - 3; j >= 0; --j) {
-            const float tau = taus[j];
-            if (tau == 0.0f) continue;
             const int m = k - 1 - j;
-            const float *v = S + j * ld + j + 1;
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                const int col = lane + 32 * c;
-                if (col < k) {
-                    float *zc_ = Z + col * ld + j + 1;
-                    float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, d3 = 0.0f;
-                    int t = 0;
-                    for (; t + 4 <= m; t += 4) {
-                        d0 = fmaf(v[t], zc_[t], d0);
-                        d1 = fmaf(v[t + 1], zc_[t + 1], d1);
-                        d2 = fmaf(v[t + 2], zc_[t + 2], d2);
-                        d3 = fmaf(v[t + 3], zc_[t + 3], d3);
-                    }
-                    for (; t < m; ++t) d0 = fmaf(v[t], zc_[t], d0);
-                    const float beta = ((d0 + d1) + (d2 + d3)) * tau;
+                const int t = lane + 32 * c;
+                if (t < m) vtmp[t] = vnext[c];
+            }
+            __syncwarp();
+            if (j > 0)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const int t = lane + 32 * c;
+                    vnext[c] = t < m + 1 ? __ldcg(Ag + (j - 1) * k + j + t) : 0.0f;
+                }
+            const float tau = taus[j];
+            const float *v = vtmp;
+            if (tau != 0.0f) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const int col = lane + 32 * c;
+                    if (col < k) {
+                        float *zc_ = Z + col * ld + j + 1;
+                        float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, d3 = 0.0f;
+                        int t = 0;
+                        for (; t + 4 <= m; t += 4) {
+                            d0 = fmaf(v[t], zc_[t], d0);
+                            d1 = fmaf(v[t + 1], zc_[t + 1], d1);
+                            d2 = fmaf(v[t + 2], zc_[t + 2], d2);
+                            d3 = fmaf(v[t + 3], zc_[t + 3], d3);
+                        }
+                        for (; t < m; ++t) d0 = fmaf(v[t], zc_[t], d0);
+                        const float beta = ((d0 + d1) + (d2 + d3)) * tau;
 #pragma unroll 4
-                    for (t = 0; t < m; ++t) zc_[t] = fmaf(-beta, v[t], zc_[t]);
+                        for (t = 0; t < m; ++t) zc_[t] = fmaf(-beta, v[t], zc_[t]);
+                    }
                 }
             }
+            __syncwarp();
         }
-        __syncwarp();
 
         if (a.eigval)
 #pragma unroll
@@ -474,32 +510,11 @@ __global__ void __launch_bounds__(128, MINB) eigen_update_kernel(EigArgs a) {
     }
 }
 
-constexpr int kSmemPerSm = 227 * 1024;
-
-template <int NC>
-constexpr int min_blocks() { return NC == 1 ? 5 : 1; }
-
-// Warps per block (1..4) that let the most warps share an SM's shared memory.
-int warps_per_block(int k) {
-    const int per_warp = smem_floats(k) * (int)sizeof(float);
-    const int max_warps = kSmemPerSm / per_warp;
-    int best = 1, best_total = 0;
-    for (int w = 4; w >= 1; --w) {
-        const int total = (kSmemPerSm / (w * per_warp)) * w;
-        if (total > best_total) {
-            best = w;
-            best_total = total;
-        }
-        if (total == max_warps) break;
-    }
-    return best;
-}
-
 template <int NC>
 cudaError_t prepare_nc(int k, int *max_blocks) {
-    const int warps = warps_per_block(k);
+    const int warps = EigCfg<NC>::WARPS;
     const size_t smem = (size_t)smem_floats(k) * sizeof(float) * warps;
-    auto kern = eigen_update_kernel<NC, min_blocks<NC>()>;
+    auto kern = eigen_update_kernel<NC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -516,12 +531,12 @@ cudaError_t prepare_nc(int k, int *max_blocks) {
 
 template <int NC>
 cudaError_t launch_nc(const EigArgs &a, cudaStream_t s) {
-    const int warps = warps_per_block(a.k);
+    const int warps = EigCfg<NC>::WARPS;
     const size_t smem = (size_t)smem_floats(a.k) * sizeof(float) * warps;
     long long need = ((long long)a.npts + warps - 1) / warps;
     long long blocks = a.max_blocks > 0 ? a.max_blocks : 1;
     if (blocks > need) blocks = need;
-    eigen_update_kernel<NC, min_blocks<NC>()><<<(unsigned)blocks, 32 * warps, smem, s>>>(a);
+    eigen_update_kernel<NC><<<(unsigned)blocks, 32 * warps, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -18,13 +18,13 @@
 // Summation order is fixed by the bin order, so results are bitwise reproducible.
 #include "common.cuh"
 #include "kernels.h"
+#include "patch.cuh"
 
 namespace lk {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kChunk = 32;     // observation points per staged chunk
-constexpr int kMaxCells = 1024;  // bins in one tile's patch (the host sizes bins to fit)
+constexpr int kChunk = 32;  // observation points per staged chunk
 
 template <int KP>
 struct GramShape {
@@ -35,62 +35,13 @@ struct GramShape {
     static constexpr int TH = P / TW;
 };
 
-// Exclusive prefix sum in place over s[0..n], n <= 4 * kThreads; s[n] receives the total.
-__device__ void block_exclusive_scan(int *s, int n, int *warp_tot) {
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    int v[4], local = 0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int idx = tid * 4 + i;
-        v[i] = idx < n ? s[idx] : 0;
-        local += v[i];
-    }
-    int incl = local;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) warp_tot[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-        int t = lane < kThreads / 32 ? warp_tot[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += u;
-        }
-        if (lane < kThreads / 32) warp_tot[lane] = t;  // inclusive warp totals
-    }
-    __syncthreads();
-    int run = incl - local + (wid > 0 ? warp_tot[wid - 1] : 0);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int idx = tid * 4 + i;
-        if (idx < n) s[idx] = run;
-        run += v[i];
-    }
-    if (tid == kThreads - 1) s[n] = run;
-    __syncthreads();
-}
-
-__device__ __forceinline__ int range_len(const BinRanges &r) {
-    int n = 0;
-    for (int i = 0; i < r.n; ++i) n += r.hi[i] - r.lo[i] + 1;
-    return n;
-}
-__device__ __forceinline__ int range_at(const BinRanges &r, int i) {
-    const int l0 = r.hi[0] - r.lo[0] + 1;
-    return i < l0 ? r.lo[0] + i : r.lo[1] + (i - l0);
-}
-
 template <int KP>
 __global__ void __launch_bounds__(kThreads) gram_kernel(GramArgs a) {
     using S = GramShape<KP>;
     constexpr int KB = S::KB, T = S::T, P = S::P, TW = S::TW, TH = S::TH;
 
-    __shared__ int cell_base[kMaxCells];
-    __shared__ int cell_pre[kMaxCells + 1];
+    __shared__ int cell_base[kMaxPatchCells];
+    __shared__ int cell_pre[kMaxPatchCells + 1];
     __shared__ int warp_tot[kThreads / 32];
     __shared__ int2 opos[kChunk];
     __shared__ int oidx[kChunk];
@@ -107,26 +58,8 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(GramArgs a) {
     const int ty0 = a.y_begin + blockIdx.y * TH;
 
     // ---- the tile's observation patch: bins touched by any cutoff disk of the tile
-    BinRanges rx, ry;
-    if (net.loc_none) {
-        rx.n = ry.n = 1;
-        rx.lo[0] = ry.lo[0] = 0;
-        rx.hi[0] = net.ncx - 1;
-        ry.hi[0] = net.ncy - 1;
-    } else {
-        rx = bin_ranges(tx0 - net.cr, tx0 + TW - 1 + net.cr, a.nx, net.cs);
-        ry = bin_ranges(ty0 - net.cr, ty0 + TH - 1 + net.cr, a.ny, net.cs);
-    }
-    const int ncx_p = range_len(rx);
-    const int nc = ncx_p * range_len(ry);  // <= kMaxCells by construction of the bin size
-    for (int c = tid; c < nc; c += kThreads) {
-        const int cell = range_at(ry, c / ncx_p) * net.ncx + range_at(rx, c % ncx_p);
-        const int b0 = net.cell_start[cell];
-        cell_base[c] = b0;
-        cell_pre[c] = net.cell_start[cell + 1] - b0;
-    }
-    __syncthreads();
-    block_exclusive_scan(cell_pre, nc, warp_tot);
+    const int nc = build_patch<kThreads>(net, a.nx, a.ny, tx0, ty0, TW, TH, cell_base, cell_pre,
+                                         warp_tot);
     const int total = cell_pre[nc];
 
     // ---- this thread's role: point p of the tile, 8 x 8 block (ti, tj) of A_p
@@ -147,13 +80,7 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(GramArgs a) {
     for (int base = 0; base < total; base += kChunk) {
         const int nch = min(kChunk, total - base);
         if (tid < nch) {
-            const int j = base + tid;
-            int lo = 0, hi = nc - 1;  // last bin whose prefix is <= j
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (cell_pre[mid] <= j) lo = mid; else hi = mid - 1;
-            }
-            const int o = net.cell_obs[cell_base[lo] + (j - cell_pre[lo])];
+            const int o = patch_obs(net, cell_base, cell_pre, nc, base + tid);
             oidx[tid] = o;
             opos[tid] = net.xy[o];
             for (int v = 0; v < V; ++v) {
@@ -175,17 +102,8 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(GramArgs a) {
         for (int e = tid; e < P * nch; e += kThreads) {
             const int pp = e / nch, t = e % nch;
             const int qx = tx0 + pp % TW, qy = ty0 + pp / TW;
-            float w = 0.0f;
-            if (qx < a.nx && qy < a.y_end) {
-                if (net.loc_none) {
-                    w = 1.0f;
-                } else {
-                    const int dx = min_image(opos[t].x - qx, a.nx);
-                    const int dy = min_image(opos[t].y - qy, a.ny);
-                    const int d2 = dx * dx + dy * dy;
-                    if (d2 <= net.d2max) w = expf(-(float)d2 * net.inv2r2);
-                }
-            }
+            const float w = (qx < a.nx && qy < a.y_end) ? loc_weight(net, opos[t], qx, qy, a.nx, a.ny)
+                                                        : 0.0f;
             wts[pp * kChunk + t] = w;
         }
         __syncthreads();
@@ -276,7 +194,7 @@ int gram_tile_width(int kp) {
         default: return GramShape<128>::TW;
     }
 }
-int gram_max_cells() { return kMaxCells; }
+int gram_max_cells() { return kMaxPatchCells; }
 
 cudaError_t gram_prepare(int kp) {
     switch (kp) {

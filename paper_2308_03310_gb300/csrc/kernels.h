@@ -70,6 +70,11 @@ struct GramArgs {
     int *nloc;              // [(y_end-y_begin)*nx]
 };
 cudaError_t gram_prepare(int kp);            // once per process and kp
+// tensor-core (tcgen05) split-FP16 form for kp = 64 or 128; persistent, <= max_ctas CTAs
+cudaError_t gram_tc_prepare(int kp);
+cudaError_t launch_gram_tc(const GramArgs &a, int *status, int max_ctas, cudaStream_t s);
+int gram_tc_tile_width(int kp);
+int gram_tc_tile_height(int kp);
 cudaError_t launch_gram(const GramArgs &a, cudaStream_t s);
 int gram_tile_width(int kp);
 int gram_tile_height(int kp);
@@ -79,7 +84,7 @@ int gram_max_cells();
 struct EigArgs {
     int k;
     float diag;             // (k - 1) / rho_infl
-    const float *gram;      // [npts][k][k]
+    float *gram;            // [npts][k][k]; consumed, then reused for the Householder vectors
     const float *cvec;      // [npts][k]
     const int *nloc;        // [npts]
     float *x;               // grid-point-major ensemble [N][9][k], updated in place

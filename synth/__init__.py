@@ -220,6 +220,12 @@ WORKLOADS = {
         name="turb256_k32", nx=256, ny=256, k=32, tau=0.52, obs_stride=8, obs_sigma=0.01,
         loc_radius=8.0, steps_per_cycle=100, cycles=50, init="turbulence", truth_noise=1e-3,
         kolmogorov_amp=1e-5, kolmogorov_n=4, random_rms=1e-5, spinup=20000),
+    # The analysis shape of the 1024^2 case (k = 64, obs every 4th point, r = 12) on a 256^2
+    # grid: a small stand-in for profiling its kernels.
+    "turb256_k64": Workload(
+        name="turb256_k64", nx=256, ny=256, k=64, tau=0.52, obs_stride=4, obs_sigma=0.01,
+        loc_radius=12.0, steps_per_cycle=100, cycles=50, init="turbulence", truth_noise=1e-3,
+        kolmogorov_amp=1e-5, kolmogorov_n=4, random_rms=1e-5, spinup=20000),
     # Same turbulence at scale (FP32 and mixed forms).
     "turb1024_k64": Workload(
         name="turb1024_k64", nx=1024, ny=1024, k=64, tau=0.52, obs_stride=4, obs_sigma=0.01,
