@@ -44,8 +44,8 @@ struct Plan {
     float inv2r2 = 0.0f;
     // byte offsets inside the workspace
     size_t off_state[2], off_force, off_xg, off_obs_xy, off_cell_start, off_cell_obs, off_rinv,
-        off_yf, off_yb, off_ybar, off_yo, off_gram, off_cvec, off_nloc, off_nloc_all, off_eigval,
-        off_status, total;
+        off_yf, off_yb, off_ybar, off_yo, off_orec, off_gram, off_cvec, off_nloc, off_nloc_all,
+        off_eigval, off_status, total;
 };
 
 int validate(const letkf_config *c) {
@@ -83,7 +83,8 @@ int make_plan(const letkf_config *c, Plan *p) {
     p->kp = kp_of(c->k);
     p->tile_w = lk::gram_tile_width(p->kp);
     p->tile_h = lk::gram_tile_height(p->kp);
-    p->tensor_gram = c->precision == LETKF_MIXED && p->kp >= 64;
+    // (observation points are packed as x | y << 16 in the tensor-core kernel's records)
+    p->tensor_gram = c->precision == LETKF_MIXED && p->kp >= 64 && c->nx < 65536 && c->ny < 65536;
     if (p->tensor_gram) {  // the bins must fit either kernel's tile patch
         p->tile_w = std::max(p->tile_w, lk::gram_tc_tile_width(p->kp));
         p->tile_h = std::max(p->tile_h, lk::gram_tc_tile_height(p->kp));
@@ -145,6 +146,7 @@ int make_plan(const letkf_config *c, Plan *p) {
     p->off_yb = take((size_t)p->LV * p->kp * sizeof(float));
     p->off_ybar = take((size_t)p->LV * sizeof(float));
     p->off_yo = take((size_t)p->LV * sizeof(float));
+    p->off_orec = take(p->tensor_gram ? (size_t)p->LV * sizeof(float4) : 0);
     p->off_gram = take(p->chunk_pts * c->k * c->k * sizeof(float));
     p->off_cvec = take(p->chunk_pts * c->k * sizeof(float));
     p->off_nloc = take(p->chunk_pts * sizeof(int));
@@ -170,6 +172,7 @@ struct letkf_handle {
     float2 *force = nullptr;
     float *xg = nullptr, *rinv = nullptr, *yf = nullptr, *yb = nullptr, *ybar = nullptr,
           *yo = nullptr, *gram = nullptr, *cvec = nullptr, *eigval = nullptr;
+    float4 *orec = nullptr;
     int2 *obs_xy = nullptr;
     int *cell_start = nullptr, *cell_obs = nullptr, *nloc = nullptr, *nloc_all = nullptr,
         *status = nullptr;
@@ -312,6 +315,8 @@ int enqueue_analysis(letkf_handle *h, letkf_probe *probe) {
         g.gram = h->gram;
         g.cvec = h->cvec;
         g.nloc = h->nloc;
+        g.orec = h->orec;
+        if (p.tensor_gram && chunk == 0) CK(lk::launch_obs_records(g, h->orec, h->stream));
         if (p.tensor_gram)
             CK(lk::launch_gram_tc(g, h->status, h->tc_ctas, h->stream));
         else
@@ -464,6 +469,7 @@ int letkf_init(const letkf_config *cfg, void *workspace, size_t workspace_bytes,
     h->yb = (float *)(w + plan.off_yb);
     h->ybar = (float *)(w + plan.off_ybar);
     h->yo = (float *)(w + plan.off_yo);
+    h->orec = plan.tensor_gram ? (float4 *)(w + plan.off_orec) : nullptr;
     h->gram = (float *)(w + plan.off_gram);
     h->cvec = (float *)(w + plan.off_cvec);
     h->nloc = (int *)(w + plan.off_nloc);

@@ -1,53 +1,75 @@
-// Localized Gram matrices on the 5th-generation tensor cores (tcgen05), split FP16, FP32
+// Localized Gram matrices on the 5th-generation tensor cores (tcgen05), split FP16 with FP32
 // accumulation: the mixed-precision form of
 //     A_p = sum_o G_po / sigma_o^2  dy_o dy_o^T ,   c_p = sum_o G_po / sigma_o^2  dy_o (yo_o - ybar_o)
 // (the k x k term of Eq. letkf_q and the vector of Eq. letkf_wa, R-localization of Sec. II-B).
 //
-// With y_o = dy_o / sigma_o (O(1) values) a tile of P grid points that share one observation
-// patch computes, per point, A_p = Y^T (diag(G_p) Y) with Y the patch's scaled perturbations.
-// Both operands are split into FP16 hi + lo parts and all four products are accumulated in
-// FP32 in tensor memory, so the result carries ~22 significant bits, like FP32:
-//     k = 64:  one M = 128 MMA per K-step stacks [Y_hi; Y_lo] as rows, and the N dimension
-//              holds [B_hi | B_lo] of every point (B = diag(G_p) Y), P = 4 points, N = 512;
-//     k = 128: two M = 128 MMAs (Y_hi, Y_lo) per point and K-step, P = 2 points, N = 512.
-// The tile's accumulators fill all 512 TMEM columns.  CUDA cores build the next 64-scalar
-// K-chunk of both operands (scaling, localization weights, hi/lo split, c) into the second
-// shared-memory stage while the tensor cores consume the current one; a single thread issues
-// the MMAs and commits them to the stage's mbarrier.  The chunk's perturbation rows are staged
-// in shared memory by 1-D TMA bulk copies (cp.async.bulk, completion counted in bytes on an
-// mbarrier) one chunk ahead of their use.  Operands are K-major without swizzle (8 x 16-byte
-// core matrices).  Every wait on an mbarrier is bounded: on expiry the status
-// word gets ST_TIMEOUT, the CTA stops issuing work, waits (bounded) for its MMAs and frees
-// its tensor memory.  Candidate order is fixed, so results are bitwise reproducible.
+// Symmetric form.  With x_po = sqrt(G_po) dy_o / sigma_o the Gram matrix of point p is
+// A_p = X_p^T X_p, so one operand tile per point serves as both MMA operands.  X_p is split
+// into FP16 parts X = Xh + Xl (Xl carries the rounding residual, ~22 significant bits in all)
+// and A_p = Xh Xh^T + Xl Xh^T + (Xl Xh^T)^T; the Xl Xl^T term (relative size 2^-22) is dropped.
+// The tile [Xl; Xh] (2 kp rows, K-major) gives with one M = 128 MMA per K-step
+//     kp = 64:  D = [Xl; Xh] Xh^T  (128 x 64): rows 0..63 Xl Xh^T, rows 64..127 Xh Xh^T;
+//     kp = 128: two MMAs, D_lh = Xl Xh^T and D_hh = Xh Xh^T (128 x 128 each).
+// The epilogue forms A = D_hh + (D_lh + D_lh^T) through a shared-memory transpose.
+// c_p = sum_o x_po (sqrt(G_po) (yo_o - ybar_o) / sigma_o) is accumulated in FP32 on the CUDA
+// cores by the threads that build the operands.
+//
+// Warp roles of one persistent CTA per SM, linked by mbarrier rings (no block-wide barrier in
+// the steady state):
+//   warp 0      candidates: walks the tile's observation patch (bins of the cs x cs cell
+//               grid, contiguous runs of the observation records per bin row), computes the
+//               square-root localization weights of the tile's points, drops candidates that
+//               no point of the tile sees, and publishes segments of slots;
+//   warp 1      bulk copies (cp.async.bulk, 1-D TMA) of the slots' dy rows into a staging ring;
+//   warp 2      MMA issue: one thread issues the tile's MMAs and commits them to mbarriers;
+//   warps 3..6  epilogue: tensor memory (double-buffered across tiles) -> A_p in global memory;
+//   warps 7..14 operands: weights x dy rows, hi/lo split, core-matrix layout, and c_p.
+// Every wait is bounded in time: on expiry the status word gets ST_TIMEOUT, all roles leave
+// their loops, the CTA waits (bounded) for its MMAs and copies and frees its tensor memory.
+// Candidate order and every summation order are fixed, so results are bitwise reproducible.
 #include <cuda_fp16.h>
 
 #include "common.cuh"
 #include "kernels.h"
-#include "patch.cuh"
 
 namespace lk {
 namespace {
 
-constexpr int kTcThreads = 256;      // 8 warps: operand production; warps w, w+4 share a TMEM quadrant
-constexpr int kMetaCap = 1024;       // candidate scalars whose metadata one segment keeps
+constexpr int kWarpMeta = 0, kWarpTma = 1, kWarpMma = 2, kWarpEpi = 3, kWarpProd = 7;
+constexpr int kEpiWarps = 4, kProdWarps = 8;
+constexpr int kTcThreads = 32 * (kWarpProd + kProdWarps);  // 480
+constexpr int kProdThreads = 32 * kProdWarps, kEpiThreads = 32 * kEpiWarps;
 constexpr uint32_t kTmemCols = 512;
-constexpr long long kWaitSpins = 1ll << 24;
+static_assert(kWarpEpi + kEpiWarps == kWarpProd, "warp roles");
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 
 template <int KP>
 struct TcShape {
-    static constexpr int P = 512 / (2 * KP);                       // points per tile
-    static constexpr int TW = 2, TH = P / 2;                       // 2x2 (k=64), 2x1 (k=128)
-    static constexpr int KC = KP == 64 ? 64 : 32;                  // scalars per K-chunk
-    static constexpr int SBO = (KC / 8) * 128;                     // bytes between row blocks
-    static constexpr int AROWS = 2 * KP;                           // Y_hi rows then Y_lo rows
-    static constexpr int BROWS = P * 2 * KP;                       // per point B_hi then B_lo
-    static constexpr int A_BYTES = AROWS * KC * 2;
-    static constexpr int B_BYTES = BROWS * KC * 2;
-    static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int YLD = KP + 4;                             // padded FP32 staging row
-    static constexpr int Y_BYTES = KC * YLD * 4;
-    static constexpr int NM = KP / 64;                             // member slots per thread
-    static constexpr int SMEM = 2 * STAGE + 2 * Y_BYTES;
+    static constexpr int P = KP == 64 ? 4 : 1;              // points per tile
+    static constexpr int TW = KP == 64 ? 2 : 1, TH = KP == 64 ? 2 : 1;
+    static constexpr int KC = KP == 64 ? 64 : 32;           // slots per chunk (MMA K)
+    static constexpr int NOP = KP == 64 ? 2 : 4;            // operand stages
+    static constexpr int NY = KP == 64 ? 2 : 4;             // dy staging stages
+    static constexpr int SEG = KP == 64 ? 256 : 512;        // slots per candidate segment
+    static constexpr int SBO = (KC / 8) * 128;              // bytes between 8-row core blocks
+    static constexpr int OPB = 2 * KP * KC * 2;             // operand bytes per point and stage
+    static constexpr int STAGE = P * OPB;
+    static constexpr int YROW = KP * 4;                     // bytes of one staged dy row
+    static constexpr int YSTAGE = KC * YROW;
+    static constexpr int MQ = KP / 32;                      // member quarters of the producers
+    static constexpr int KQ = kProdWarps / MQ;              // producer warps per member quarter
+    static constexpr int NG = KC / 8, GPW = NG / KQ;        // 8-slot groups: per chunk, per warp
+    static constexpr int ELD = KP + 1;                      // padded row of the transpose buffer
+    static constexpr int OFF_OP = 0;
+    static constexpr int OFF_Y = OFF_OP + NOP * STAGE;
+    static constexpr int OFF_GIDX = OFF_Y + NY * YSTAGE;    // int   [2][SEG]
+    static constexpr int OFF_SW = OFF_GIDX + 2 * SEG * 4;   // float [2][P][SEG]
+    static constexpr int OFF_SU = OFF_SW + 2 * P * SEG * 4; // float [2][P][SEG]
+    static constexpr int OFF_E = OFF_SU + 2 * P * SEG * 4;  // float [KP][ELD]
+    static constexpr int OFF_CRED = OFF_E + KP * ELD * 4;   // float [2][KQ][P][KP]
+    static constexpr int SMEM = OFF_CRED + 2 * KQ * P * KP * 4;
+    static_assert(SEG % KC == 0 && NG % KQ == 0, "chunking");
+    static_assert(SMEM <= 227 * 1024 - 1024, "shared memory");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -66,10 +88,10 @@ __host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
     return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// Half offset of element (row, kk) of a K-major tile with KC columns (core-matrix layout).
+// Byte offset of the 16-byte run (row, k8..k8+7) of a K-major tile with KC columns.
 template <int KC>
-__device__ __forceinline__ int core_off(int row, int kk) {
-    return ((row >> 3) * (KC / 8) + (kk >> 3)) * 64 + (row & 7) * 8 + (kk & 7);
+__device__ __forceinline__ uint32_t core_off_b(int row, int k8) {
+    return (uint32_t)((((row >> 3) * (KC / 8) + (k8 >> 3)) * 64 + (row & 7) * 8) * 2);
 }
 
 __device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
@@ -80,18 +102,51 @@ __device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint
         "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t done = 0;
-    for (long long it = 0; it < kWaitSpins && !done; ++it)
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(smem_u32(bar)), "r"(parity));
-    return done != 0;
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar)));
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+__device__ __forceinline__ void bar_init(uint64_t *bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void bar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool bar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for the completion of the phase with the given parity; gives up after kWaitNs
+// or once another role has raised the abort flag.  The outcome is made uniform over the warp
+// (every lane of the calling warp waits on the same phase).
+__device__ bool wait_bar(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    bool ok = bar_try(bar, parity);
+    if (!ok) {
+        const unsigned long long t0 = global_ns();
+        for (;;) {
+#pragma unroll 1
+            for (int i = 0; i < 32 && !ok; ++i) ok = bar_try(bar, parity);
+            if (ok || *abort_flag || global_ns() - t0 > kWaitNs) break;
+        }
+    }
+    return __all_sync(0xffffffffu, ok);
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     uint32_t r[32];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
@@ -108,24 +163,45 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Square root of the Gaussian localization weight, exp(-d^2 / (4 r^2)), of an observation at
+// (ox, oy) seen from grid point (qx, qy); 0 beyond the cutoff.
+__device__ __forceinline__ float loc_weight_sqrt(const ObsNet &net, int ox, int oy, int qx,
+                                                 int qy, int nx, int ny) {
+    if (net.loc_none) return 1.0f;
+    const int dx = min_image(ox - qx, nx), dy = min_image(oy - qy, ny);
+    const int d2 = dx * dx + dy * dy;
+    return d2 <= net.d2max ? expf(-0.5f * (float)d2 * net.inv2r2) : 0.0f;
+}
+
+// A_p row `row` (accumulator values v[0..31] for columns c0..c0+31) to global memory.
+__device__ __forceinline__ void store_row32(float *dst, const float *v, int c0, int k) {
+    if ((k & 3) == 0) {
+#pragma unroll
+        for (int i = 0; i < 32; i += 4)
+            if (c0 + i < k)
+                *reinterpret_cast<float4 *>(dst + c0 + i) =
+                    make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            if (c0 + i < k) dst[c0 + i] = v[i];
+    }
+}
+
 template <int KP>
 __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int *status) {
     using S = TcShape<KP>;
-    constexpr int P = S::P, TW = S::TW, TH = S::TH, NM = S::NM, KC = S::KC, YLD = S::YLD;
+    constexpr int P = S::P, TW = S::TW, TH = S::TH, KC = S::KC, SEG = S::SEG;
+    constexpr int NOP = S::NOP, NY = S::NY;
     extern __shared__ __align__(1024) unsigned char dyn[];
-    __shared__ int cell_base[kMaxPatchCells];
-    __shared__ int cell_pre[kMaxPatchCells + 1];
-    __shared__ int warp_tot[kTcThreads / 32];
-    __shared__ int gidx[kMetaCap];       // global scalar index of each candidate slot (-1: pad)
-    __shared__ float sr[kMetaCap];       // sqrt(R^-1) of the slot
-    __shared__ float cm[kMetaCap];       // sqrt(R^-1) (yo - ybar) of the slot
-    __shared__ int2 opos[kMetaCap];      // observation point of the slot
-    __shared__ float wts[2][P][KC];      // localization weights of the current / next chunk
-    __shared__ int nloc_s[P];
-    __shared__ __align__(8) uint64_t mbar[2];   // MMAs of an operand stage done
-    __shared__ __align__(8) uint64_t ybar[2];   // bulk copies of a staging buffer landed
+    __shared__ __align__(8) uint64_t meta_full[2], meta_empty[2];
+    __shared__ __align__(8) uint64_t y_full[NY], y_empty[NY];
+    __shared__ __align__(8) uint64_t op_full[NOP], op_empty[NOP];
+    __shared__ __align__(8) uint64_t tm_full[2], tm_empty[2];
+    __shared__ __align__(8) uint64_t prod_sync, epi_sync, mma_done;
+    __shared__ int4 mdesc[2];  // segment: tile, slots, flags (1: first of tile, 2: last)
     __shared__ uint32_t tmem_base;
-    __shared__ int abort_flag;
+    __shared__ volatile int abort_flag;
 
     const ObsNet &net = a.net;
     const int V = net.V;
@@ -133,325 +209,480 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int 
     const int rows = a.y_end - a.y_begin;
     const int ntx = (a.nx + TW - 1) / TW, nty = (rows + TH - 1) / TH;
     const int ntiles = ntx * nty;
-    float *ystage = reinterpret_cast<float *>(dyn + 2 * S::STAGE);
+    int *gidx_s = reinterpret_cast<int *>(dyn + S::OFF_GIDX);
+    float *sw_s = reinterpret_cast<float *>(dyn + S::OFF_SW);
+    float *su_s = reinterpret_cast<float *>(dyn + S::OFF_SU);
+    float *ystage = reinterpret_cast<float *>(dyn + S::OFF_Y);
+    float *E = reinterpret_cast<float *>(dyn + S::OFF_E);
+    float *cred = reinterpret_cast<float *>(dyn + S::OFF_CRED);
 
+    // ---- set-up: barriers, tensor memory, finite contents for every staged value
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[i])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&ybar[i])));
+            bar_init(&meta_full[i], 32);
+            bar_init(&meta_empty[i], 32 + 32 + kProdThreads);
+            bar_init(&tm_full[i], 1);
+            bar_init(&tm_empty[i], kEpiThreads);
         }
+        for (int i = 0; i < NY; ++i) {
+            bar_init(&y_full[i], 1);
+            bar_init(&y_empty[i], kProdThreads);
+        }
+        for (int i = 0; i < NOP; ++i) {
+            bar_init(&op_full[i], kProdThreads);
+            bar_init(&op_empty[i], 1);
+        }
+        bar_init(&prod_sync, kProdThreads);
+        bar_init(&epi_sync, kEpiThreads);
+        bar_init(&mma_done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;");
         abort_flag = 0;
     }
-    if (warp == 0) {
+    for (int i = tid; i < (S::OFF_E - S::OFF_Y) / 4; i += kTcThreads)
+        reinterpret_cast<float *>(dyn + S::OFF_Y)[i] = 0.0f;
+    if (warp == kWarpMma) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_base)),
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
 
-    // barrier bookkeeping (identical in every thread): each completion is waited exactly once
-    bool mpend[2] = {false, false}, ypend[2] = {false, false};
-    uint32_t mph[2] = {0u, 0u}, yph[2] = {0u, 0u};
-    auto wait_mma = [&](int b) -> bool {
-        if (!mpend[b]) return true;
-        const bool ok = mbar_wait(&mbar[b], mph[b]);
-        mph[b] ^= 1u;
-        mpend[b] = false;
-        return ok;
+    auto fail = [&]() {
+        abort_flag = 1;
+        if (lane == 0) atomicOr(status, ST_TIMEOUT);
     };
-    auto wait_y = [&](int b) -> bool {
-        if (!ypend[b]) return true;
-        const bool ok = mbar_wait(&ybar[b], yph[b]);
-        yph[b] ^= 1u;
-        ypend[b] = false;
-        return ok;
-    };
-    // warp 1: bulk-copy the dY rows of the KC slots starting at segment slot `first` (n of
-    // them real) into staging buffer yb.  Lane 0 announces the byte count on the buffer's
-    // mbarrier, then every lane issues the copies of its own slots.  All threads mark the
-    // buffer pending.
-    auto prefetch = [&](int yb, int first, int n) {
-        if (warp == 1) {
-            float *dst = ystage + yb * KC * YLD;
-            int mine[KC / 32];
-            int cnt = 0;
-#pragma unroll
-            for (int r = 0; r < KC / 32; ++r) {
-                const int kk = lane + 32 * r;
-                mine[r] = kk < n ? gidx[first + kk] : -1;
-                cnt += __popc(__ballot_sync(0xffffffffu, mine[r] >= 0));
-            }
-            if (lane == 0)
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
-                                 smem_u32(&ybar[yb])),
-                             "r"((uint32_t)(cnt * KP * 4)));
-            __syncwarp();
-#pragma unroll
-            for (int r = 0; r < KC / 32; ++r) {
-                if (mine[r] < 0) continue;
-                asm volatile(
-                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], "
-                    "%2, [%3];" ::"r"(smem_u32(dst + (lane + 32 * r) * YLD)),
-                    "l"(a.yb + (size_t)mine[r] * KP), "r"(KP * 4), "r"(smem_u32(&ybar[yb]))
-                    : "memory");
-            }
-        }
-        ypend[yb] = true;
-    };
-    // localization weights of the KC slots starting at `first` for every point of the tile
-    auto weights = [&](int wb, int seg, int first, int n, int tx0, int ty0) {
-        for (int e = tid; e < P * KC; e += kTcThreads) {
-            const int p = e / KC, kk = e % KC;
-            const int qx = tx0 + (p % TW), qy = ty0 + (p / TW);
-            float w = 0.0f;
-            if (kk < n && gidx[first + kk] >= 0 && qx < a.nx && qy < a.y_end) {
-                w = loc_weight(net, opos[first + kk], qx, qy, a.nx, a.ny);
-                if (w != 0.0f && (seg + first + kk) % V == 0) atomicAdd(&nloc_s[p], 1);
-            }
-            wts[wb][p][kk] = w;
-        }
+    auto tile_origin = [&](int tile, int &tx0, int &ty0) {
+        tx0 = (tile % ntx) * TW;
+        ty0 = a.y_begin + (tile / ntx) * TH;
     };
 
-    int gch = 0;  // chunks issued by this CTA (selects operand stage and staging buffer)
-    for (int tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x) {
-        const int tx0 = (tile % ntx) * TW;
-        const int ty0 = a.y_begin + (tile / ntx) * TH;
-        const int nc = build_patch<kTcThreads>(net, a.nx, a.ny, tx0, ty0, TW, TH, cell_base,
-                                               cell_pre, warp_tot);
-        const int total_slots = cell_pre[nc] * V;
-        if (tid < P) nloc_s[tid] = 0;
-        float cacc[P][NM];
-#pragma unroll
-        for (int p = 0; p < P; ++p)
-#pragma unroll
-            for (int i = 0; i < NM; ++i) cacc[p][i] = 0.0f;
-        int tile_chunks = 0;
-
-        for (int seg = 0; seg < total_slots && !abort_flag; seg += kMetaCap) {
-            const int nseg = min(kMetaCap, total_slots - seg);
-            __syncthreads();  // previous segment's metadata no longer in use
-            // ---- segment metadata: every candidate scalar slot at once
-            for (int e = tid; e < kMetaCap; e += kTcThreads) {
-                int sidx = -1;
-                float r = 0.0f, c = 0.0f;
-                int2 xy = make_int2(0, 0);
-                if (e < nseg) {
-                    const int j = seg + e, v = j % V;
-                    const int o = patch_obs(net, cell_base, cell_pre, nc, j / V);
-                    sidx = o * V + v;
-                    xy = net.xy[o];
-                    r = sqrtf(a.rinv[sidx]);
-                    c = r * ((a.yo[sidx] - a.yref[v]) - a.ybar[sidx]);
-                }
-                gidx[e] = sidx;
-                sr[e] = r;
-                cm[e] = c;
-                opos[e] = xy;
+    if (warp == kWarpMeta) {
+        // ===================== candidates and weights =====================
+        int segc = 0;
+        const unsigned lt_mask = (1u << lane) - 1u;
+        for (int tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x) {
+            int tx0, ty0;
+            tile_origin(tile, tx0, ty0);
+            BinRanges rx, ry;
+            if (net.loc_none) {
+                rx.n = ry.n = 1;
+                rx.lo[0] = ry.lo[0] = 0;
+                rx.hi[0] = net.ncx - 1;
+                ry.hi[0] = net.ncy - 1;
+            } else {
+                rx = bin_ranges(tx0 - net.cr, tx0 + TW - 1 + net.cr, a.nx, net.cs);
+                ry = bin_ranges(ty0 - net.cr, ty0 + TH - 1 + net.cr, a.ny, net.cs);
             }
-            __syncthreads();
-            const int nchunks = (nseg + KC - 1) / KC;
-            prefetch(gch & 1, 0, min(KC, nseg));
-            weights(0, seg, 0, min(KC, nseg), tx0, ty0);
-            __syncthreads();
-            for (int ch = 0; ch < nchunks; ++ch, ++gch) {
-                const int b = gch & 1, wb = ch & 1;
-                const int first = ch * KC, n = min(KC, nseg - first);
-                const bool okm = wait_mma(b);   // operand stage b free again
-                const bool oky = wait_y(b);     // this chunk's dY rows landed
-                // a wait that gave up is reported through the shared flag; every thread reads
-                // it after the chunk's barrier, so all of them leave the loop together
-                if (!okm || !oky) abort_flag = 1;
-                // next chunk's rows into the other staging buffer (its last reader, the
-                // previous chunk's production, finished before the last barrier)
-                if (ch + 1 < nchunks) prefetch(b ^ 1, first + KC, min(KC, nseg - first - KC));
-                unsigned char *stage = dyn + b * S::STAGE;
-                __half *sA = reinterpret_cast<__half *>(stage);
-                __half *sB = reinterpret_cast<__half *>(stage + S::A_BYTES);
-                const float *ys = ystage + b * KC * YLD;
-                // ---- operands: (member, slot pair) items, 8 members x 4 pairs per instruction
+            int cnt_p[P];
 #pragma unroll
-                for (int im = 0; im < NM; ++im) {
-                    const int m = 8 * (warp + 8 * im) + (lane >> 2);
-#pragma unroll 2
-                    for (int kb = 0; kb < KC / 8; ++kb) {
-                        const int kk = 8 * kb + 2 * (lane & 3);
-                        const bool v0 = kk < n && gidx[first + kk] >= 0;
-                        const bool v1 = kk + 1 < n && gidx[first + kk + 1] >= 0;
-                        const float y0 = v0 ? ys[kk * YLD + m] * sr[first + kk] : 0.0f;
-                        const float y1 = v1 ? ys[(kk + 1) * YLD + m] * sr[first + kk + 1] : 0.0f;
-                        const __half h0 = __float2half_rn(y0), h1 = __float2half_rn(y1);
-                        const __half l0 = __float2half_rn(y0 - __half2float(h0));
-                        const __half l1 = __float2half_rn(y1 - __half2float(h1));
-                        *reinterpret_cast<__half2 *>(sA + core_off<KC>(m, kk)) =
-                            __halves2half2(h0, h1);
-                        *reinterpret_cast<__half2 *>(sA + core_off<KC>(KP + m, kk)) =
-                            __halves2half2(l0, l1);
-                        const float c0 = v0 ? cm[first + kk] * y0 : 0.0f;
-                        const float c1 = v1 ? cm[first + kk + 1] * y1 : 0.0f;
+            for (int p = 0; p < P; ++p) cnt_p[p] = 0;
+            int mb = segc & 1, nfill = 0, first = 1;
+            bool ok = wait_bar(&meta_empty[mb], ((segc >> 1) & 1) ^ 1, &abort_flag);
+            // close the current segment (pad its last chunk with zero weights) and publish it
+            auto publish = [&](int last) {
+                const int pad_end = min(SEG, max(KC, (nfill + KC - 1) / KC * KC));
+                for (int e = nfill + lane; e < pad_end; e += 32) {
+                    gidx_s[mb * SEG + e] = -1;
 #pragma unroll
-                        for (int p = 0; p < P; ++p) {
-                            const float w0 = wts[wb][p][kk], w1 = wts[wb][p][kk + 1];
-                            const float b0 = w0 * y0, b1 = w1 * y1;
-                            const __half bh0 = __float2half_rn(b0), bh1 = __float2half_rn(b1);
-                            const __half bl0 = __float2half_rn(b0 - __half2float(bh0));
-                            const __half bl1 = __float2half_rn(b1 - __half2float(bh1));
-                            const int rb = p * 2 * KP + m;
-                            *reinterpret_cast<__half2 *>(sB + core_off<KC>(rb, kk)) =
-                                __halves2half2(bh0, bh1);
-                            *reinterpret_cast<__half2 *>(sB + core_off<KC>(rb + KP, kk)) =
-                                __halves2half2(bl0, bl1);
-                            cacc[p][im] = fmaf(w0, c0, fmaf(w1, c1, cacc[p][im]));
-                        }
+                    for (int p = 0; p < P; ++p) {
+                        sw_s[(mb * P + p) * SEG + e] = 0.0f;
+                        su_s[(mb * P + p) * SEG + e] = 0.0f;
                     }
                 }
-                // the next chunk's weights, for use after the barrier
-                if (ch + 1 < nchunks)
-                    weights(wb ^ 1, seg, first + KC, min(KC, nseg - first - KC), tx0, ty0);
-                asm volatile("fence.proxy.async.shared::cta;");
-                __syncthreads();
-                if (abort_flag) break;
-                // ---- tensor cores: the chunk's K-steps of 16, committed to the stage barrier
-                if (tid == 0) {
-                    asm volatile("tcgen05.fence::after_thread_sync;");
-                    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-#pragma unroll
-                    for (int ks = 0; ks < KC / 16; ++ks) {
-                        const uint32_t acc = (tile_chunks > 0 || ks > 0) ? 1u : 0u;
-                        if (KP == 64) {
-                            const uint64_t da = sdesc(a0 + ks * 256, S::SBO);
-#pragma unroll
-                            for (int h = 0; h < 2; ++h)
-                                mma_f16(tmem + h * 256, da,
-                                        sdesc(b0 + h * (256 / 8) * S::SBO + ks * 256, S::SBO),
-                                        idesc_f16(128, 256), acc);
-                        } else {
+                if (lane == 0) mdesc[mb] = make_int4(tile, nfill, first | (last ? 2 : 0), 0);
+                __syncwarp();
+                bar_arrive(&meta_full[mb]);
+                ++segc;
+                first = 0;
+            };
+            for (int yr = 0; yr < ry.n && ok; ++yr)
+                for (int by = ry.lo[yr]; by <= ry.hi[yr] && ok; ++by)
+                    for (int xr = 0; xr < rx.n && ok; ++xr) {
+                        const int c0 = by * net.ncx + rx.lo[xr];
+                        const int j0 = __ldg(net.cell_start + c0) * V;
+                        const int j1 =
+                            __ldg(net.cell_start + c0 + (rx.hi[xr] - rx.lo[xr]) + 1) * V;
+                        float4 rn = j0 + lane < j1 ? __ldg(a.orec + j0 + lane)
+                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+                        for (int jb = j0; jb < j1; jb += 32) {
+                            const float4 r = rn;
+                            const bool in = jb + lane < j1;
+                            if (jb + 32 + lane < j1) rn = __ldg(a.orec + jb + 32 + lane);
+                            const int s = __float_as_int(r.x), pk = __float_as_int(r.y);
+                            const int ox = pk & 0xffff, oy = (int)((unsigned)pk >> 16);
+                            const float sr = sqrtf(r.z);
+                            float sw[P];
+                            bool keep = false;
 #pragma unroll
                             for (int p = 0; p < P; ++p) {
-                                const uint64_t db =
-                                    sdesc(b0 + p * (256 / 8) * S::SBO + ks * 256, S::SBO);
-                                mma_f16(tmem + p * 256, sdesc(a0 + ks * 256, S::SBO), db,
-                                        idesc_f16(128, 256), acc);
-                                mma_f16(tmem + p * 256,
-                                        sdesc(a0 + (128 / 8) * S::SBO + ks * 256, S::SBO), db,
-                                        idesc_f16(128, 256), 1u);
+                                const int qx = tx0 + p % TW, qy = ty0 + p / TW;
+                                float w = 0.0f;
+                                if (in && qx < a.nx && qy < a.y_end)
+                                    w = loc_weight_sqrt(net, ox, oy, qx, qy, a.nx, a.ny);
+                                keep |= w != 0.0f;
+                                if (w != 0.0f && s % V == 0) ++cnt_p[p];
+                                sw[p] = w * sr;
                             }
+                            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                            const int n = __popc(bal);
+                            if (n == 0) continue;
+                            if (nfill + n > SEG) {
+                                publish(0);
+                                mb = segc & 1;
+                                nfill = 0;
+                                ok = wait_bar(&meta_empty[mb], ((segc >> 1) & 1) ^ 1, &abort_flag);
+                                if (!ok) break;
+                            }
+                            if (keep) {
+                                const int e = nfill + __popc(bal & lt_mask);
+                                gidx_s[mb * SEG + e] = s;
+#pragma unroll
+                                for (int p = 0; p < P; ++p) {
+                                    sw_s[(mb * P + p) * SEG + e] = sw[p];
+                                    su_s[(mb * P + p) * SEG + e] = sw[p] * r.w;
+                                }
+                            }
+                            nfill += n;
                         }
                     }
-                    asm volatile(
-                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                            smem_u32(&mbar[b])));
-                }
-                mpend[b] = true;
-                ++tile_chunks;
+            if (!ok) {
+                fail();
+                break;
+            }
+            publish(1);
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                int c = cnt_p[p];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+                const int qx = tx0 + p % TW, qy = ty0 + p / TW;
+                if (lane == 0 && qx < a.nx && qy < a.y_end)
+                    a.nloc[(size_t)(qy - a.y_begin) * a.nx + qx] = c;
             }
         }
-        // ---- all MMAs and copies of the tile done
-        const bool ok = wait_mma(0) & wait_mma(1) & wait_y(0) & wait_y(1);
-        if (!ok && tid == 0) abort_flag = 1;
-        __syncthreads();
-        if (abort_flag) break;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-
-        // ---- epilogue: A_p = sum of the hi/lo blocks; warps w and w+4 share TMEM lanes
-        const int quad = warp & 3, half = warp >> 2;
-        const int trow = 32 * quad + lane;                      // D row of this thread
-        const uint32_t tl = tmem + ((uint32_t)(32 * quad) << 16);
-        float *red = reinterpret_cast<float *>(dyn);            // [P][64][65] (k = 64)
-        if (KP == 64 && tile_chunks > 0 && quad >= 2) {         // rows 64..127: Y_lo part
-            const int m = trow - 64, c0 = 32 * half;
-#pragma unroll 1
-            for (int p = 0; p < P; ++p) {
-                float vh[32], vl[32];
-                tmem_ld32(tl + p * 128 + c0, vh);
-                tmem_ld32(tl + p * 128 + 64 + c0, vl);
+    } else if (warp == kWarpTma) {
+        // ===================== dy rows into the staging ring =====================
+        int segc = 0;
+        uint32_t g = 0;
+        for (int tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x) {
+            bool last = false, ok = true;
+            while (!last && ok) {
+                const int mb = segc & 1;
+                if (!(ok = wait_bar(&meta_full[mb], (segc >> 1) & 1, &abort_flag))) break;
+                const int4 d = mdesc[mb];
+                last = (d.z & 2) != 0;
+                const int nch = max(1, (d.y + KC - 1) / KC);
+                for (int ch = 0; ch < nch; ++ch, ++g) {
+                    const int s = g % NY;
+                    if (!(ok = wait_bar(&y_empty[s], ((g / NY) & 1) ^ 1, &abort_flag))) break;
+                    const int cnt = min(KC, d.y - ch * KC);
+                    if (lane == 0)
+                        asm volatile(
+                            "mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                                smem_u32(&y_full[s])),
+                            "r"((uint32_t)(max(cnt, 0) * S::YROW))
+                            : "memory");
+                    __syncwarp();
+                    float *dst = ystage + (size_t)s * (S::YSTAGE / 4);
 #pragma unroll
-                for (int i = 0; i < 32; ++i) red[(p * 64 + m) * 65 + c0 + i] = vh[i] + vl[i];
-            }
-        }
-        __syncthreads();
-        if (tile_chunks > 0 && (KP == 128 || quad < 2)) {
-            const int m = trow;
-#pragma unroll 1
-            for (int p = 0; p < P; ++p) {
-                const int qx = tx0 + (p % TW), qy = ty0 + (p / TW);
-                const bool valid = qx < a.nx && qy < a.y_end && m < a.k;
-                const size_t lp = valid ? (size_t)(qy - a.y_begin) * a.nx + qx : 0;
-#pragma unroll 1
-                for (int cc = 0; cc < KP / 64; ++cc) {
-                    const int c0 = (KP / 2) * half + 32 * cc;
-                    float vh[32], vl[32];
-                    tmem_ld32(tl + p * 2 * KP + c0, vh);
-                    tmem_ld32(tl + p * 2 * KP + KP + c0, vl);
-                    if (!valid) continue;
-                    float *dst = a.gram + lp * a.k * a.k + (size_t)m * a.k;
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        vh[i] += vl[i];
-                        if (KP == 64) vh[i] += red[(p * 64 + m) * 65 + c0 + i];
+                    for (int r = 0; r < KC / 32; ++r) {
+                        const int kk = lane + 32 * r;
+                        if (kk < cnt) {
+                            const int row = gidx_s[mb * SEG + ch * KC + kk];
+                            asm volatile(
+                                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+                                "[%0], [%1], %2, [%3];" ::"r"(smem_u32(dst + kk * KP)),
+                                "l"(a.yb + (size_t)row * KP), "r"((uint32_t)S::YROW),
+                                "r"(smem_u32(&y_full[s]))
+                                : "memory");
+                        }
                     }
-                    if ((a.k & 3) == 0) {  // rows start 16-byte aligned: vector stores
+                }
+                if (!ok) break;
+                bar_arrive(&meta_empty[mb]);
+                ++segc;
+            }
+            if (!ok) {
+                fail();
+                break;
+            }
+        }
+        // every issued copy has landed before the CTA may exit (bounded)
+        volatile int no_abort = 0;
+        for (int s = 0; s < NY; ++s) {
+            if (g <= (uint32_t)s) continue;
+            const uint32_t last_use = (g - 1 - s) / NY * NY + s;  // last chunk on stage s
+            if (!wait_bar(&y_full[s], (last_use / NY) & 1, &no_abort)) fail();
+        }
+    } else if (warp == kWarpMma) {
+        // ===================== tensor-core issue =====================
+        int segc = 0, tcount = 0;
+        uint32_t g = 0;
+        const uint32_t op0 = smem_u32(dyn + S::OFF_OP);
+        for (int tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x, ++tcount) {
+            const int tb = tcount & 1;
+            bool last = false, ok = true, firstc = true;
+            while (!last && ok) {
+                const int mb = segc & 1;
+                if (!(ok = wait_bar(&meta_full[mb], (segc >> 1) & 1, &abort_flag))) break;
+                const int4 d = mdesc[mb];
+                last = (d.z & 2) != 0;
+                const int nch = max(1, (d.y + KC - 1) / KC);
+                for (int ch = 0; ch < nch; ++ch, ++g) {
+                    const int so = g % NOP;
+                    if (!(ok = wait_bar(&op_full[so], (g / NOP) & 1, &abort_flag))) break;
+                    if (firstc &&
+                        !(ok = wait_bar(&tm_empty[tb], ((tcount >> 1) & 1) ^ 1, &abort_flag)))
+                        break;
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    if (lane == 0) {
+                        const uint32_t st = op0 + so * S::STAGE;
 #pragma unroll
-                        for (int i = 0; i < 32; i += 4)
-                            if (c0 + i < a.k)
-                                *reinterpret_cast<float4 *>(dst + c0 + i) =
-                                    make_float4(vh[i], vh[i + 1], vh[i + 2], vh[i + 3]);
-                    } else {
+                        for (int ks = 0; ks < KC / 16; ++ks) {
+                            const uint32_t acc = (firstc && ks == 0) ? 0u : 1u;
+#pragma unroll
+                            for (int p = 0; p < P; ++p) {
+                                const uint32_t tp = st + p * S::OPB + ks * 256;
+                                const uint64_t dl = sdesc(tp, S::SBO);
+                                const uint64_t dh = sdesc(tp + (KP / 8) * S::SBO, S::SBO);
+                                if (KP == 64) {
+                                    mma_f16(tmem + tb * 256 + p * 64, dl, dh, idesc_f16(128, 64),
+                                            acc);
+                                } else {
+                                    mma_f16(tmem + tb * 256, dl, dh, idesc_f16(128, 128), acc);
+                                    mma_f16(tmem + tb * 256 + 128, dh, dh, idesc_f16(128, 128),
+                                            acc);
+                                }
+                            }
+                        }
+                        mma_commit(&op_empty[so]);
+                        if (last && ch == nch - 1) mma_commit(&tm_full[tb]);
+                    }
+                    __syncwarp();
+                    firstc = false;
+                }
+                if (!ok) break;
+                bar_arrive(&meta_empty[mb]);
+                ++segc;
+            }
+            if (!ok) {
+                fail();
+                break;
+            }
+        }
+        // all MMAs issued by this CTA complete before its tensor memory is freed (bounded)
+        if (lane == 0) mma_commit(&mma_done);
+        __syncwarp();
+        volatile int no_abort = 0;
+        if (!wait_bar(&mma_done, 0, &no_abort)) fail();
+    } else if (warp < kWarpEpi + kEpiWarps) {
+        // ===================== epilogue: tensor memory -> A_p =====================
+        const int eq = warp & 3;           // tensor-memory lane quadrant of this warp
+        const int r = 32 * eq + lane;      // accumulator row of this thread
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * eq) << 16);
+        int tcount = 0;
+        uint32_t esync = 0;
+        bool ok = true;
+        auto epi_barrier = [&]() {
+            bar_arrive(&epi_sync);
+            ok = wait_bar(&epi_sync, esync & 1, &abort_flag);
+            ++esync;
+        };
+        for (int tile = blockIdx.x; tile < ntiles && !abort_flag && ok;
+             tile += gridDim.x, ++tcount) {
+            const int tb = tcount & 1;
+            if (!(ok = wait_bar(&tm_full[tb], (tcount >> 1) & 1, &abort_flag))) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            int tx0, ty0;
+            tile_origin(tile, tx0, ty0);
+            for (int p = 0; p < P && ok; ++p) {
+                const int qx = tx0 + p % TW, qy = ty0 + p / TW;
+                const bool valid = qx < a.nx && qy < a.y_end;
+                const size_t lp = valid ? (size_t)(qy - a.y_begin) * a.nx + qx : 0;
+                float v[32];
+                if (KP == 64) {
+                    const uint32_t col = tb * 256 + p * 64;
+                    if (eq < 2) {  // rows of Xl Xh^T
+#pragma unroll
+                        for (int c0 = 0; c0 < 64; c0 += 32) {
+                            tmem_ld32(lane_base + col + c0, v);
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) E[r * S::ELD + c0 + i] = v[i];
+                        }
+                    }
+                    epi_barrier();
+                    if (!ok) break;
+                    if (eq >= 2) {  // rows of Xh Xh^T
+                        const int m = r - 64;
+                        float *dst = a.gram + lp * a.k * a.k + (size_t)m * a.k;
+#pragma unroll
+                        for (int c0 = 0; c0 < 64; c0 += 32) {
+                            tmem_ld32(lane_base + col + c0, v);
+#pragma unroll
+                            for (int i = 0; i < 32; ++i)
+                                v[i] += E[m * S::ELD + c0 + i] + E[(c0 + i) * S::ELD + m];
+                            if (valid && m < a.k) store_row32(dst, v, c0, a.k);
+                        }
+                    }
+                    epi_barrier();
+                } else {
+                    const uint32_t col = tb * 256;
+#pragma unroll 1
+                    for (int c0 = 0; c0 < 128; c0 += 32) {  // D_lh row r
+                        tmem_ld32(lane_base + col + c0, v);
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) E[r * S::ELD + c0 + i] = v[i];
+                    }
+                    epi_barrier();
+                    if (!ok) break;
+                    float *dst = a.gram + lp * a.k * a.k + (size_t)r * a.k;
+#pragma unroll 1
+                    for (int c0 = 0; c0 < 128; c0 += 32) {  // D_hh row r
+                        tmem_ld32(lane_base + col + 128 + c0, v);
 #pragma unroll
                         for (int i = 0; i < 32; ++i)
-                            if (c0 + i < a.k) dst[c0 + i] = vh[i];
+                            v[i] += E[r * S::ELD + c0 + i] + E[(c0 + i) * S::ELD + r];
+                        if (valid && r < a.k) store_row32(dst, v, c0, a.k);
                     }
+                    epi_barrier();
                 }
             }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            bar_arrive(&tm_empty[tb]);
         }
-        // ---- c_p: the 4 lanes sharing a member hold partial sums; nloc from the counters
+        if (!ok) fail();
+    } else {
+        // ===================== operands and c_p =====================
+        const int pw = warp - kWarpProd;
+        const int mq = pw % S::MQ, kq = pw / S::MQ;
+        const int m = 32 * mq + lane;
+        unsigned char *op = dyn + S::OFF_OP;
+        int segc = 0, par = 0;
+        uint32_t g = 0, psync = 0;
+        float cacc[P];
 #pragma unroll
-        for (int p = 0; p < P; ++p)
+        for (int p = 0; p < P; ++p) cacc[p] = 0.0f;
+        for (int tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x) {
+            bool last = false, ok = true;
+            while (!last && ok) {
+                const int mb = segc & 1;
+                if (!(ok = wait_bar(&meta_full[mb], (segc >> 1) & 1, &abort_flag))) break;
+                const int4 d = mdesc[mb];
+                last = (d.z & 2) != 0;
+                if (d.z & 1) {
 #pragma unroll
-            for (int im = 0; im < NM; ++im) {
-                float v = cacc[p][im];
-                v += __shfl_xor_sync(0xffffffffu, v, 1);
-                v += __shfl_xor_sync(0xffffffffu, v, 2);
-                const int m = 8 * (warp + 8 * im) + (lane >> 2);
-                const int qx = tx0 + (p % TW), qy = ty0 + (p / TW);
-                if ((lane & 3) == 0 && m < a.k && qx < a.nx && qy < a.y_end) {
-                    const size_t lp = (size_t)(qy - a.y_begin) * a.nx + qx;
-                    a.cvec[lp * a.k + m] = v;
+                    for (int p = 0; p < P; ++p) cacc[p] = 0.0f;
+                }
+                const int nch = max(1, (d.y + KC - 1) / KC);
+                for (int ch = 0; ch < nch; ++ch, ++g) {
+                    const int s = g % NY, so = g % NOP;
+                    if (!(ok = wait_bar(&y_full[s], (g / NY) & 1, &abort_flag))) break;
+                    if (!(ok = wait_bar(&op_empty[so], ((g / NOP) & 1) ^ 1, &abort_flag))) break;
+                    const int first = ch * KC, cnt = min(KC, d.y - first);
+                    const float *ys = ystage + (size_t)s * (S::YSTAGE / 4);
+                    unsigned char *st = op + so * S::STAGE;
+#pragma unroll
+                    for (int gi = 0; gi < S::GPW; ++gi) {
+                        const int k8 = 8 * (kq + S::KQ * gi);
+                        float yv[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            yv[i] = k8 + i < cnt ? ys[(k8 + i) * KP + m] : 0.0f;
+#pragma unroll
+                        for (int p = 0; p < P; ++p) {
+                            const float *wp = sw_s + (mb * P + p) * SEG + first + k8;
+                            const float *up = su_s + (mb * P + p) * SEG + first + k8;
+                            const float4 w0 = *reinterpret_cast<const float4 *>(wp);
+                            const float4 w1 = *reinterpret_cast<const float4 *>(wp + 4);
+                            const float4 u0 = *reinterpret_cast<const float4 *>(up);
+                            const float4 u1 = *reinterpret_cast<const float4 *>(up + 4);
+                            const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+                            const float u[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+                            uint32_t hw[4], lw[4];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const float x0 = yv[2 * i] * w[2 * i];
+                                const float x1 = yv[2 * i + 1] * w[2 * i + 1];
+                                const __half2 h = __floats2half2_rn(x0, x1);
+                                const float2 hf = __half22float2(h);
+                                const __half2 l = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+                                hw[i] = *reinterpret_cast<const uint32_t *>(&h);
+                                lw[i] = *reinterpret_cast<const uint32_t *>(&l);
+                                cacc[p] = fmaf(x0, u[2 * i], cacc[p]);
+                                cacc[p] = fmaf(x1, u[2 * i + 1], cacc[p]);
+                            }
+                            unsigned char *tp = st + p * S::OPB;
+                            *reinterpret_cast<uint4 *>(tp + core_off_b<KC>(KP + m, k8)) =
+                                make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                            *reinterpret_cast<uint4 *>(tp + core_off_b<KC>(m, k8)) =
+                                make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                        }
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    bar_arrive(&op_full[so]);
+                    bar_arrive(&y_empty[s]);
+                }
+                if (!ok) break;
+                bar_arrive(&meta_empty[mb]);
+                ++segc;
+            }
+            if (!ok) {
+                fail();
+                break;
+            }
+            // ---- c_p: partial sums of the KQ warps sharing a member quarter
+#pragma unroll
+            for (int p = 0; p < P; ++p) cred[((par * S::KQ + kq) * P + p) * KP + m] = cacc[p];
+            bar_arrive(&prod_sync);
+            if (!wait_bar(&prod_sync, psync & 1, &abort_flag)) {
+                fail();
+                break;
+            }
+            ++psync;
+            if (kq == 0) {
+                int tx0, ty0;
+                tile_origin(tile, tx0, ty0);
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    float c = 0.0f;
+#pragma unroll
+                    for (int q = 0; q < S::KQ; ++q)
+                        c += cred[((par * S::KQ + q) * P + p) * KP + m];
+                    const int qx = tx0 + p % TW, qy = ty0 + p / TW;
+                    if (m < a.k && qx < a.nx && qy < a.y_end)
+                        a.cvec[((size_t)(qy - a.y_begin) * a.nx + qx) * a.k + m] = c;
                 }
             }
-        if (tid < P) {
-            const int qx = tx0 + (tid % TW), qy = ty0 + (tid / TW);
-            if (qx < a.nx && qy < a.y_end) {
-                const size_t lp = (size_t)(qy - a.y_begin) * a.nx + qx;
-                a.nloc[lp] = nloc_s[tid];
-                if (tile_chunks == 0)  // no candidate at all: the Gram matrix is zero
-                    for (int e = 0; e < a.k * a.k; ++e) a.gram[lp * a.k * a.k + e] = 0.0f;
-            }
+            par ^= 1;
         }
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
     }
-    // ---- stop: outstanding MMAs and copies (bounded), then free the tensor memory
-    wait_mma(0);
-    wait_mma(1);
-    wait_y(0);
-    wait_y(1);
-    if (abort_flag && tid == 0) atomicOr(status, ST_TIMEOUT);
+
+    // ---- stop: every role has left its loop; free the tensor memory
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (warp == 0)
+    if (warp == kWarpMma)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(kTmemCols));
 }
 
-template <int KP>
-size_t tc_smem() {
-    return (size_t)TcShape<KP>::SMEM;
+// Observation records in bin order: slot j = V * (position in cell_obs) + v holds the row of
+// the scalar in dy, the packed point (x | y << 16), 1 / sigma^2 and yo - reference - ybar.
+__global__ void obs_records_kernel(ObsNet net, const float *rinv, const float *yo,
+                                   const float *ybar, float r0, float r1, float r2,
+                                   float4 *rec) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= net.L * net.V) return;
+    const int o = net.cell_obs[j / net.V], v = j % net.V, s = o * net.V + v;
+    const int2 xy = net.xy[o];
+    const float ref = v == 0 ? r0 : (v == 1 ? r1 : r2);
+    rec[j] = make_float4(__int_as_float(s), __int_as_float(xy.x | (xy.y << 16)), rinv[s],
+                         (yo[s] - ref) - ybar[s]);
 }
 
 }  // namespace
@@ -462,25 +693,34 @@ int gram_tc_tile_height(int kp) { return kp == 64 ? TcShape<64>::TH : TcShape<12
 cudaError_t gram_tc_prepare(int kp) {
     if (kp == 64)
         return cudaFuncSetAttribute(gram_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)tc_smem<64>());
+                                    TcShape<64>::SMEM);
     if (kp == 128)
         return cudaFuncSetAttribute(gram_tc_kernel<128>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)tc_smem<128>());
+                                    TcShape<128>::SMEM);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_obs_records(const GramArgs &a, float4 *rec, cudaStream_t s) {
+    const int n = a.net.L * a.net.V;
+    if (n == 0) return cudaSuccess;
+    obs_records_kernel<<<(n + 255) / 256, 256, 0, s>>>(a.net, a.rinv, a.yo, a.ybar, a.yref[0],
+                                                        a.yref[1], a.yref[2], rec);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_gram_tc(const GramArgs &a, int *status, int max_ctas, cudaStream_t s) {
     if (a.y_end <= a.y_begin) return cudaSuccess;
     if (a.kp != 64 && a.kp != 128) return cudaErrorInvalidValue;
+    if (a.orec == nullptr) return cudaErrorInvalidValue;
     const int TW = gram_tc_tile_width(a.kp), TH = gram_tc_tile_height(a.kp);
     const long long tiles =
         (long long)((a.nx + TW - 1) / TW) * ((a.y_end - a.y_begin + TH - 1) / TH);
     const unsigned grid = (unsigned)(tiles < max_ctas ? tiles : max_ctas);
     if (a.kp == 64)
-        gram_tc_kernel<64><<<grid, kTcThreads, tc_smem<64>(), s>>>(a, status);
+        gram_tc_kernel<64><<<grid, kTcThreads, TcShape<64>::SMEM, s>>>(a, status);
     else
-        gram_tc_kernel<128><<<grid, kTcThreads, tc_smem<128>(), s>>>(a, status);
+        gram_tc_kernel<128><<<grid, kTcThreads, TcShape<128>::SMEM, s>>>(a, status);
     return cudaGetLastError();
 }
 

@@ -65,6 +65,7 @@ struct GramArgs {
     const float *rinv;      // [L*V] 1 / sigma^2
     float yref[3];          // reference of each observed variable (1 for rho, else 0)
     int y_begin, y_end;     // grid rows of this chunk
+    const float4 *orec;     // tensor-core form: observation records in bin order [L*V]
     float *gram;            // [(y_end-y_begin)*nx][k][k]
     float *cvec;            // [(y_end-y_begin)*nx][k]
     int *nloc;              // [(y_end-y_begin)*nx]
@@ -73,6 +74,8 @@ cudaError_t gram_prepare(int kp);            // once per process and kp
 // tensor-core (tcgen05) split-FP16 form for kp = 64 or 128; persistent, <= max_ctas CTAs
 cudaError_t gram_tc_prepare(int kp);
 cudaError_t launch_gram_tc(const GramArgs &a, int *status, int max_ctas, cudaStream_t s);
+// records for launch_gram_tc, rebuilt whenever yo or ybar change
+cudaError_t launch_obs_records(const GramArgs &a, float4 *rec, cudaStream_t s);
 int gram_tc_tile_width(int kp);
 int gram_tc_tile_height(int kp);
 cudaError_t launch_gram(const GramArgs &a, cudaStream_t s);
