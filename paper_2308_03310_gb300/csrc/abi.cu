@@ -83,8 +83,10 @@ int make_plan(const letkf_config *c, Plan *p) {
     p->kp = kp_of(c->k);
     p->tile_w = lk::gram_tile_width(p->kp);
     p->tile_h = lk::gram_tile_height(p->kp);
-    // (observation points are packed as x | y << 16 in the tensor-core kernel's records)
-    p->tensor_gram = c->precision == LETKF_MIXED && p->kp >= 64 && c->nx < 65536 && c->ny < 65536;
+    // (the tensor-core kernel's records pack a point as x | y << 16 and a scalar's row with
+    // its variable in bits 28..29)
+    p->tensor_gram = c->precision == LETKF_MIXED && p->kp >= 64 && c->nx < 65536 &&
+                     c->ny < 65536 && p->LV < (1 << 28);
     if (p->tensor_gram) {  // the bins must fit either kernel's tile patch
         p->tile_w = std::max(p->tile_w, lk::gram_tc_tile_width(p->kp));
         p->tile_h = std::max(p->tile_h, lk::gram_tc_tile_height(p->kp));

@@ -16,14 +16,15 @@
 //
 // Warp roles of one persistent CTA per SM, linked by mbarrier rings (no block-wide barrier in
 // the steady state):
-//   warp 0      candidates: walks the tile's observation patch (bins of the cs x cs cell
-//               grid, contiguous runs of the observation records per bin row), computes the
-//               square-root localization weights of the tile's points, drops candidates that
-//               no point of the tile sees, and publishes segments of slots;
-//   warp 1      bulk copies (cp.async.bulk, 1-D TMA) of the slots' dy rows into a staging ring;
+//   warps 0, 1  candidates, alternating tiles, each through its own ring: walk the tile's
+//               observation patch (bins of the cs x cs cell grid, contiguous runs of the
+//               observation records per bin row), compute the square-root localization
+//               weights of the tile's points, drop candidates that no point of the tile sees,
+//               and publish segments of slots;
 //   warp 2      MMA issue: one thread issues the tile's MMAs and commits them to mbarriers;
-//   warps 3..6  epilogue: tensor memory (double-buffered across tiles) -> A_p in global memory;
-//   warps 7..14 operands: weights x dy rows, hi/lo split, core-matrix layout, and c_p.
+//   warp 3      loads: the slots' dy rows into a staging ring, 16-byte cp.async per lane;
+//   warps 4..7  epilogue: tensor memory (double-buffered across tiles) -> A_p in global memory;
+//   warps 8..15 operands: weights x dy rows, hi/lo split, core-matrix layout, and c_p.
 // Every wait is bounded in time: on expiry the status word gets ST_TIMEOUT, all roles leave
 // their loops, the CTA waits (bounded) for its MMAs and copies and frees its tensor memory.
 // Candidate order and every summation order are fixed, so results are bitwise reproducible.
@@ -35,21 +36,22 @@
 namespace lk {
 namespace {
 
-constexpr int kWarpMeta = 0, kWarpTma = 1, kWarpMma = 2, kWarpEpi = 3, kWarpProd = 7;
+constexpr int kMetaWarps = 2, kWarpMma = 2, kWarpLoad = 3, kWarpEpi = 4, kWarpProd = 8;
 constexpr int kEpiWarps = 4, kProdWarps = 8;
-constexpr int kTcThreads = 32 * (kWarpProd + kProdWarps);  // 480
+constexpr int kTcThreads = 32 * (kWarpProd + kProdWarps);  // 512
 constexpr int kProdThreads = 32 * kProdWarps, kEpiThreads = 32 * kEpiWarps;
 constexpr uint32_t kTmemCols = 512;
 static_assert(kWarpEpi + kEpiWarps == kWarpProd, "warp roles");
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
+constexpr uint32_t kSuspendNs = 20000;  // a waiting thread sleeps until the phase completes
 
 template <int KP>
 struct TcShape {
     static constexpr int P = KP == 64 ? 4 : 1;              // points per tile
     static constexpr int TW = KP == 64 ? 2 : 1, TH = KP == 64 ? 2 : 1;
-    static constexpr int KC = KP == 64 ? 64 : 32;           // slots per chunk (MMA K)
+    static constexpr int KC = 32;                           // slots per chunk (MMA K)
     static constexpr int NOP = KP == 64 ? 2 : 4;            // operand stages
-    static constexpr int NY = KP == 64 ? 2 : 4;             // dy staging stages
+    static constexpr int NY = KP == 64 ? 8 : 4;             // dy staging stages
     static constexpr int SEG = KP == 64 ? 256 : 512;        // slots per candidate segment
     static constexpr int SBO = (KC / 8) * 128;              // bytes between 8-row core blocks
     static constexpr int OPB = 2 * KP * KC * 2;             // operand bytes per point and stage
@@ -62,10 +64,11 @@ struct TcShape {
     static constexpr int ELD = KP + 1;                      // padded row of the transpose buffer
     static constexpr int OFF_OP = 0;
     static constexpr int OFF_Y = OFF_OP + NOP * STAGE;
-    static constexpr int OFF_GIDX = OFF_Y + NY * YSTAGE;    // int   [2][SEG]
-    static constexpr int OFF_SW = OFF_GIDX + 2 * SEG * 4;   // float [2][P][SEG]
-    static constexpr int OFF_SU = OFF_SW + 2 * P * SEG * 4; // float [2][P][SEG]
-    static constexpr int OFF_E = OFF_SU + 2 * P * SEG * 4;  // float [KP][ELD]
+    static constexpr int NMB = 2 * kMetaWarps;              // candidate buffers: 2 per ring
+    static constexpr int OFF_GIDX = OFF_Y + NY * YSTAGE;    // int   [NMB][SEG]
+    static constexpr int OFF_SW = OFF_GIDX + NMB * SEG * 4; // float [NMB][P][SEG]
+    static constexpr int OFF_SU = OFF_SW + NMB * P * SEG * 4;  // float [NMB][P][SEG]
+    static constexpr int OFF_E = OFF_SU + NMB * P * SEG * 4;   // float [KP][ELD]
     static constexpr int OFF_CRED = OFF_E + KP * ELD * 4;   // float [2][KQ][P][KP]
     static constexpr int SMEM = OFF_CRED + 2 * KQ * P * KP * 4;
     static_assert(SEG % KC == 0 && NG % KQ == 0, "chunking");
@@ -117,10 +120,10 @@ __device__ __forceinline__ void bar_arrive(uint64_t *bar) {
 __device__ __forceinline__ bool bar_try(uint64_t *bar, uint32_t parity) {
     uint32_t done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return done != 0;
 }
@@ -139,7 +142,7 @@ __device__ bool wait_bar(uint64_t *bar, uint32_t parity, volatile int *abort_fla
         const unsigned long long t0 = global_ns();
         for (;;) {
 #pragma unroll 1
-            for (int i = 0; i < 32 && !ok; ++i) ok = bar_try(bar, parity);
+            for (int i = 0; i < 4 && !ok; ++i) ok = bar_try(bar, parity);
             if (ok || *abort_flag || global_ns() - t0 > kWaitNs) break;
         }
     }
@@ -170,7 +173,7 @@ __device__ __forceinline__ float loc_weight_sqrt(const ObsNet &net, int ox, int 
     if (net.loc_none) return 1.0f;
     const int dx = min_image(ox - qx, nx), dy = min_image(oy - qy, ny);
     const int d2 = dx * dx + dy * dy;
-    return d2 <= net.d2max ? expf(-0.5f * (float)d2 * net.inv2r2) : 0.0f;
+    return d2 <= net.d2max ? __expf(-0.5f * (float)d2 * net.inv2r2) : 0.0f;
 }
 
 // A_p row `row` (accumulator values v[0..31] for columns c0..c0+31) to global memory.
@@ -194,12 +197,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int 
     constexpr int P = S::P, TW = S::TW, TH = S::TH, KC = S::KC, SEG = S::SEG;
     constexpr int NOP = S::NOP, NY = S::NY;
     extern __shared__ __align__(1024) unsigned char dyn[];
-    __shared__ __align__(8) uint64_t meta_full[2], meta_empty[2];
+    __shared__ __align__(8) uint64_t meta_full[S::NMB], meta_empty[S::NMB];
     __shared__ __align__(8) uint64_t y_full[NY], y_empty[NY];
     __shared__ __align__(8) uint64_t op_full[NOP], op_empty[NOP];
     __shared__ __align__(8) uint64_t tm_full[2], tm_empty[2];
     __shared__ __align__(8) uint64_t prod_sync, epi_sync, mma_done;
-    __shared__ int4 mdesc[2];  // segment: tile, slots, flags (1: first of tile, 2: last)
+    __shared__ int4 mdesc[S::NMB];  // segment: tile, slots, flags (1: first of tile, 2: last)
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
 
@@ -218,14 +221,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int 
 
     // ---- set-up: barriers, tensor memory, finite contents for every staged value
     if (tid == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < S::NMB; ++i) {
             bar_init(&meta_full[i], 32);
-            bar_init(&meta_empty[i], 32 + 32 + kProdThreads);
+            bar_init(&meta_empty[i], 32 + 32 + kProdThreads);  // loader, MMA, producers
+        }
+        for (int i = 0; i < 2; ++i) {
             bar_init(&tm_full[i], 1);
             bar_init(&tm_empty[i], kEpiThreads);
         }
         for (int i = 0; i < NY; ++i) {
-            bar_init(&y_full[i], 1);
+            bar_init(&y_full[i], 32);  // one arrival per loader lane, when its copies land
             bar_init(&y_empty[i], kProdThreads);
         }
         for (int i = 0; i < NOP; ++i) {
@@ -261,11 +266,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int 
         ty0 = a.y_begin + (tile / ntx) * TH;
     };
 
-    if (warp == kWarpMeta) {
+    if (warp < kMetaWarps) {
         // ===================== candidates and weights =====================
+        // warp w serves the CTA's tiles w, w + 2, ... through its own ring of two buffers
         int segc = 0;
         const unsigned lt_mask = (1u << lane) - 1u;
-        for (int tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x) {
+        for (int tile = blockIdx.x + warp * gridDim.x; tile < ntiles && !abort_flag;
+             tile += kMetaWarps * gridDim.x) {
             int tx0, ty0;
             tile_origin(tile, tx0, ty0);
             BinRanges rx, ry;
@@ -281,7 +288,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int 
             int cnt_p[P];
 #pragma unroll
             for (int p = 0; p < P; ++p) cnt_p[p] = 0;
-            int mb = segc & 1, nfill = 0, first = 1;
+            int mb = 2 * warp + (segc & 1), nfill = 0, first = 1;
             bool ok = wait_bar(&meta_empty[mb], ((segc >> 1) & 1) ^ 1, &abort_flag);
             // close the current segment (pad its last chunk with zero weights) and publish it
             auto publish = [&](int last) {
@@ -300,56 +307,92 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int 
                 ++segc;
                 first = 0;
             };
-            for (int yr = 0; yr < ry.n && ok; ++yr)
-                for (int by = ry.lo[yr]; by <= ry.hi[yr] && ok; ++by)
-                    for (int xr = 0; xr < rx.n && ok; ++xr) {
-                        const int c0 = by * net.ncx + rx.lo[xr];
-                        const int j0 = __ldg(net.cell_start + c0) * V;
-                        const int j1 =
-                            __ldg(net.cell_start + c0 + (rx.hi[xr] - rx.lo[xr]) + 1) * V;
-                        float4 rn = j0 + lane < j1 ? __ldg(a.orec + j0 + lane)
-                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
-                        for (int jb = j0; jb < j1; jb += 32) {
-                            const float4 r = rn;
-                            const bool in = jb + lane < j1;
-                            if (jb + 32 + lane < j1) rn = __ldg(a.orec + jb + 32 + lane);
-                            const int s = __float_as_int(r.x), pk = __float_as_int(r.y);
-                            const int ox = pk & 0xffff, oy = (int)((unsigned)pk >> 16);
-                            const float sr = sqrtf(r.z);
-                            float sw[P];
-                            bool keep = false;
+            // Ranges of records: one per (bin row, x range) of the patch, in that order.  32
+            // ranges at a time, every lane fetches one range's bounds; the slots of the batch
+            // are then walked as one flat list, 32 per step, with the next step's record
+            // fetched ahead.
+            const int ly0 = ry.hi[0] - ry.lo[0] + 1;
+            const int nyb = ly0 + (ry.n > 1 ? ry.hi[1] - ry.lo[1] + 1 : 0);
+            const int nr = nyb * rx.n;
+            for (int rb = 0; rb < nr && ok; rb += 32) {
+                int j0 = 0, cnt = 0;
+                if (rb + lane < nr) {
+                    const int yi = (rb + lane) / rx.n, xr = (rb + lane) - yi * rx.n;
+                    const int by = yi < ly0 ? ry.lo[0] + yi : ry.lo[1] + (yi - ly0);
+                    const int c0 = by * net.ncx + rx.lo[xr];
+                    j0 = __ldg(net.cell_start + c0) * V;
+                    cnt = __ldg(net.cell_start + c0 + (rx.hi[xr] - rx.lo[xr]) + 1) * V - j0;
+                }
+                int incl = cnt;
 #pragma unroll
-                            for (int p = 0; p < P; ++p) {
-                                const int qx = tx0 + p % TW, qy = ty0 + p / TW;
-                                float w = 0.0f;
-                                if (in && qx < a.nx && qy < a.y_end)
-                                    w = loc_weight_sqrt(net, ox, oy, qx, qy, a.nx, a.ny);
-                                keep |= w != 0.0f;
-                                if (w != 0.0f && s % V == 0) ++cnt_p[p];
-                                sw[p] = w * sr;
-                            }
-                            const unsigned bal = __ballot_sync(0xffffffffu, keep);
-                            const int n = __popc(bal);
-                            if (n == 0) continue;
-                            if (nfill + n > SEG) {
-                                publish(0);
-                                mb = segc & 1;
-                                nfill = 0;
-                                ok = wait_bar(&meta_empty[mb], ((segc >> 1) & 1) ^ 1, &abort_flag);
-                                if (!ok) break;
-                            }
-                            if (keep) {
-                                const int e = nfill + __popc(bal & lt_mask);
-                                gidx_s[mb * SEG + e] = s;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                const int tot = __shfl_sync(0xffffffffu, incl, 31);
+                // record index of flat slot f of this batch (f < tot)
+                auto record_of = [&](int f) -> int {
+                    int lo = 0;  // first range whose inclusive end exceeds f
 #pragma unroll
-                                for (int p = 0; p < P; ++p) {
-                                    sw_s[(mb * P + p) * SEG + e] = sw[p];
-                                    su_s[(mb * P + p) * SEG + e] = sw[p] * r.w;
-                                }
-                            }
-                            nfill += n;
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const int e = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+                        if (e <= f) lo += step;
+                    }
+                    const int e_lo = __shfl_sync(0xffffffffu, incl, lo);
+                    const int c_lo = __shfl_sync(0xffffffffu, cnt, lo);
+                    const int b_lo = __shfl_sync(0xffffffffu, j0, lo);
+                    return b_lo + (f - (e_lo - c_lo));
+                };
+                float4 rn = make_float4(0.f, 0.f, 0.f, 0.f);
+                {
+                    const int jn = record_of(min(lane, max(tot - 1, 0)));
+                    if (lane < tot) rn = __ldg(a.orec + jn);
+                }
+                for (int fb = 0; fb < tot; fb += 32) {
+                    const float4 r = rn;
+                    const bool in = fb + lane < tot;
+                    if (fb + 32 < tot) {
+                        const int jn = record_of(min(fb + 32 + lane, tot - 1));
+                        if (fb + 32 + lane < tot) rn = __ldg(a.orec + jn);
+                    }
+                    const int sv = __float_as_int(r.x), pk = __float_as_int(r.y);
+                    const int s = sv & 0x0FFFFFFF;
+                    const bool first_var = (sv >> 28) == 0;
+                    const int ox = pk & 0xffff, oy = (int)((unsigned)pk >> 16);
+                    float sw[P];
+                    bool keep = false;
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        const int qx = tx0 + p % TW, qy = ty0 + p / TW;
+                        float w = 0.0f;
+                        if (in && qx < a.nx && qy < a.y_end)
+                            w = loc_weight_sqrt(net, ox, oy, qx, qy, a.nx, a.ny);
+                        keep |= w != 0.0f;
+                        if (w != 0.0f && first_var) ++cnt_p[p];
+                        sw[p] = w * r.z;
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                    const int n = __popc(bal);
+                    if (n == 0) continue;
+                    if (nfill + n > SEG) {
+                        publish(0);
+                        mb = 2 * warp + (segc & 1);
+                        nfill = 0;
+                        ok = wait_bar(&meta_empty[mb], ((segc >> 1) & 1) ^ 1, &abort_flag);
+                        if (!ok) break;
+                    }
+                    if (keep) {
+                        const int e = nfill + __popc(bal & lt_mask);
+                        gidx_s[mb * SEG + e] = s;
+#pragma unroll
+                        for (int p = 0; p < P; ++p) {
+                            sw_s[(mb * P + p) * SEG + e] = sw[p];
+                            su_s[(mb * P + p) * SEG + e] = sw[p] * r.w;
                         }
                     }
+                    nfill += n;
+                }
+            }
             if (!ok) {
                 fail();
                 break;
@@ -365,15 +408,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int 
                     a.nloc[(size_t)(qy - a.y_begin) * a.nx + qx] = c;
             }
         }
-    } else if (warp == kWarpTma) {
+    } else if (warp == kWarpLoad) {
         // ===================== dy rows into the staging ring =====================
-        int segc = 0;
+        // 16-byte cp.async per lane; each lane's arrival on y_full[s] fires once its copies
+        // have landed (cp.async.mbarrier.arrive.noinc)
+        constexpr int PARTS = S::YROW / 16;  // 16-byte pieces of one row
+        int segc[2] = {0, 0}, tcount = 0;
         uint32_t g = 0;
-        for (int tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x) {
+        for (int tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x, ++tcount) {
+            const int ring = tcount & 1;
             bool last = false, ok = true;
             while (!last && ok) {
-                const int mb = segc & 1;
-                if (!(ok = wait_bar(&meta_full[mb], (segc >> 1) & 1, &abort_flag))) break;
+                const int mb = 2 * ring + (segc[ring] & 1);
+                if (!(ok = wait_bar(&meta_full[mb], (segc[ring] >> 1) & 1, &abort_flag))) break;
                 const int4 d = mdesc[mb];
                 last = (d.z & 2) != 0;
                 const int nch = max(1, (d.y + KC - 1) / KC);
@@ -381,55 +428,45 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int 
                     const int s = g % NY;
                     if (!(ok = wait_bar(&y_empty[s], ((g / NY) & 1) ^ 1, &abort_flag))) break;
                     const int cnt = min(KC, d.y - ch * KC);
-                    if (lane == 0)
-                        asm volatile(
-                            "mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
-                                smem_u32(&y_full[s])),
-                            "r"((uint32_t)(max(cnt, 0) * S::YROW))
-                            : "memory");
-                    __syncwarp();
-                    float *dst = ystage + (size_t)s * (S::YSTAGE / 4);
-#pragma unroll
-                    for (int r = 0; r < KC / 32; ++r) {
-                        const int kk = lane + 32 * r;
+                    const uint32_t dst = smem_u32(ystage + (size_t)s * (S::YSTAGE / 4));
+#pragma unroll 4
+                    for (int it = lane; it < KC * PARTS; it += 32) {
+                        const int kk = it / PARTS, part = it - kk * PARTS;
                         if (kk < cnt) {
                             const int row = gidx_s[mb * SEG + ch * KC + kk];
-                            asm volatile(
-                                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
-                                "[%0], [%1], %2, [%3];" ::"r"(smem_u32(dst + kk * KP)),
-                                "l"(a.yb + (size_t)row * KP), "r"((uint32_t)S::YROW),
-                                "r"(smem_u32(&y_full[s]))
-                                : "memory");
+                            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                                             dst + (uint32_t)(kk * S::YROW + part * 16)),
+                                         "l"(a.yb + (size_t)row * KP + part * 4)
+                                         : "memory");
                         }
                     }
+                    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
+                                     smem_u32(&y_full[s]))
+                                 : "memory");
                 }
                 if (!ok) break;
                 bar_arrive(&meta_empty[mb]);
-                ++segc;
+                ++segc[ring];
             }
             if (!ok) {
                 fail();
                 break;
             }
         }
-        // every issued copy has landed before the CTA may exit (bounded)
-        volatile int no_abort = 0;
-        for (int s = 0; s < NY; ++s) {
-            if (g <= (uint32_t)s) continue;
-            const uint32_t last_use = (g - 1 - s) / NY * NY + s;  // last chunk on stage s
-            if (!wait_bar(&y_full[s], (last_use / NY) & 1, &no_abort)) fail();
-        }
+        // every issued copy has landed before the CTA may exit
+        asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (warp == kWarpMma) {
         // ===================== tensor-core issue =====================
-        int segc = 0, tcount = 0;
+        int segc[2] = {0, 0}, tcount = 0;
         uint32_t g = 0;
         const uint32_t op0 = smem_u32(dyn + S::OFF_OP);
         for (int tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x, ++tcount) {
             const int tb = tcount & 1;
             bool last = false, ok = true, firstc = true;
+            const int ring = tcount & 1;
             while (!last && ok) {
-                const int mb = segc & 1;
-                if (!(ok = wait_bar(&meta_full[mb], (segc >> 1) & 1, &abort_flag))) break;
+                const int mb = 2 * ring + (segc[ring] & 1);
+                if (!(ok = wait_bar(&meta_full[mb], (segc[ring] >> 1) & 1, &abort_flag))) break;
                 const int4 d = mdesc[mb];
                 last = (d.z & 2) != 0;
                 const int nch = max(1, (d.y + KC - 1) / KC);
@@ -468,7 +505,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int 
                 }
                 if (!ok) break;
                 bar_arrive(&meta_empty[mb]);
-                ++segc;
+                ++segc[ring];
             }
             if (!ok) {
                 fail();
@@ -562,16 +599,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int 
         const int mq = pw % S::MQ, kq = pw / S::MQ;
         const int m = 32 * mq + lane;
         unsigned char *op = dyn + S::OFF_OP;
-        int segc = 0, par = 0;
+        int segc[2] = {0, 0}, par = 0, tcount = 0;
         uint32_t g = 0, psync = 0;
         float cacc[P];
 #pragma unroll
         for (int p = 0; p < P; ++p) cacc[p] = 0.0f;
-        for (int tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x) {
+        for (int tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x, ++tcount) {
+            const int ring = tcount & 1;
             bool last = false, ok = true;
             while (!last && ok) {
-                const int mb = segc & 1;
-                if (!(ok = wait_bar(&meta_full[mb], (segc >> 1) & 1, &abort_flag))) break;
+                const int mb = 2 * ring + (segc[ring] & 1);
+                if (!(ok = wait_bar(&meta_full[mb], (segc[ring] >> 1) & 1, &abort_flag))) break;
                 const int4 d = mdesc[mb];
                 last = (d.z & 2) != 0;
                 if (d.z & 1) {
@@ -629,7 +667,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int 
                 }
                 if (!ok) break;
                 bar_arrive(&meta_empty[mb]);
-                ++segc;
+                ++segc[ring];
             }
             if (!ok) {
                 fail();
@@ -671,8 +709,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int 
                      "r"(kTmemCols));
 }
 
-// Observation records in bin order: slot j = V * (position in cell_obs) + v holds the row of
-// the scalar in dy, the packed point (x | y << 16), 1 / sigma^2 and yo - reference - ybar.
+// Observation records in bin order: slot j = V * (position in cell_obs) + v holds the row s
+// of the scalar in dy with v in bits 28..29, the packed point (x | y << 16), 1 / sigma and
+// yo - reference - ybar.
 __global__ void obs_records_kernel(ObsNet net, const float *rinv, const float *yo,
                                    const float *ybar, float r0, float r1, float r2,
                                    float4 *rec) {
@@ -681,8 +720,8 @@ __global__ void obs_records_kernel(ObsNet net, const float *rinv, const float *y
     const int o = net.cell_obs[j / net.V], v = j % net.V, s = o * net.V + v;
     const int2 xy = net.xy[o];
     const float ref = v == 0 ? r0 : (v == 1 ? r1 : r2);
-    rec[j] = make_float4(__int_as_float(s), __int_as_float(xy.x | (xy.y << 16)), rinv[s],
-                         (yo[s] - ref) - ybar[s]);
+    rec[j] = make_float4(__int_as_float(s | (v << 28)), __int_as_float(xy.x | (xy.y << 16)),
+                         sqrtf(rinv[s]), (yo[s] - ref) - ybar[s]);
 }
 
 }  // namespace
