@@ -57,6 +57,15 @@ extern "C" {
                                   the tensor cores (tcgen05, FP16 hi+lo operands, FP32
                                   accumulation); for k <= 32 it stays on CUDA cores         */
 
+/* Eigensolve schedules (same results up to rounding; see letkf_config.eig_schedule). */
+#define LETKF_EIG_AUTO        0  /* the handle picks one                                     */
+#define LETKF_EIG_FUSED       1  /* one warp per grid point runs every phase in one launch    */
+#define LETKF_EIG_SPLIT       2  /* tridiagonalization (warp per point), QL (thread per point,
+                                    rotations recorded), replay + update (warp per point)    */
+#define LETKF_EIG_SPLIT_CHECK 3  /* SPLIT with a record of one sweep per point, so that nearly
+                                    every point is handed back to the fused kernel: exercises
+                                    the hand-off; for tests and diagnosis, not for speed      */
+
 /* ---- problem statement --------------------------------------------------
  * Follows the paper's statement of the problem (Sec. II-B): the grid, the
  * ensemble size M (= k), the observation operator H (observation points and
@@ -81,6 +90,7 @@ typedef struct letkf_config {
     float   infl;              /* multiplicative inflation rho: Q = (k-1)/rho I + ...;
                                   1 = none (the paper's Eq. letkf_q)                    */
     int32_t precision;         /* LETKF_FP32 or LETKF_MIXED                             */
+    int32_t eig_schedule;      /* LETKF_EIG_*; 0 (AUTO) lets the handle choose          */
     int64_t chunk_bytes;       /* device bytes for the per-point k x k Gram buffer;
                                   0 = default (256 MiB)                                 */
     void   *stream;            /* cudaStream_t to run on; NULL = a stream the handle
@@ -94,6 +104,8 @@ typedef struct letkf_stats {
     int32_t max_local_obs;     /* l_max: most observation points local to one point     */
     double  mean_local_obs;    /* average observation points per grid point             */
     int32_t n_chunks;          /* Gram/eigensolve launch pairs per analysis             */
+    int32_t eig_schedule;      /* LETKF_EIG_FUSED / SPLIT / SPLIT_CHECK in use (AUTO
+                                  resolved at letkf_init)                               */
 } letkf_stats;
 
 /* Device time of the phases of the most recent forecast and analysis (milliseconds, CUDA

@@ -14,7 +14,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "kernels.h"
@@ -37,6 +40,8 @@ struct Plan {
     int nmem = 0, V = 0, LV = 0, kp = 0;
     int tile_w = 1, tile_h = 1;
     bool tensor_gram = false;  // mixed precision with k in 33..128: tcgen05 split-FP16 Gram
+    int eig_schedule = LETKF_EIG_FUSED;  // as configured; AUTO keeps both schedules' scratch
+    int rcap = 0;              // split schedule: rotation record entries per point
     int chunk_rows = 0;
     size_t chunk_pts = 0;
     int cs = 8, ncx = 1, ncy = 1;
@@ -45,7 +50,7 @@ struct Plan {
     // byte offsets inside the workspace
     size_t off_state[2], off_force, off_xg, off_obs_xy, off_cell_start, off_cell_obs, off_rinv,
         off_yf, off_yb, off_ybar, off_yo, off_orec, off_gram, off_cvec, off_nloc, off_nloc_all,
-        off_eigval, off_status, total;
+        off_eigval, off_de, off_taus, off_rot, off_nrot, off_list, off_status, total;
 };
 
 int validate(const letkf_config *c) {
@@ -60,6 +65,8 @@ int validate(const letkf_config *c) {
         return LETKF_EINVAL;
     if (!(c->infl > 0.0f) || !isfinite(c->infl)) return LETKF_EINVAL;
     if (c->precision != LETKF_FP32 && c->precision != LETKF_MIXED) return LETKF_EINVAL;
+    if (c->eig_schedule < LETKF_EIG_AUTO || c->eig_schedule > LETKF_EIG_SPLIT_CHECK)
+        return LETKF_EINVAL;
     if (c->chunk_bytes < 0) return LETKF_EINVAL;
     const int V = popcount3(c->obs_vars);
     for (int l = 0; l < c->n_obs; ++l) {
@@ -154,6 +161,16 @@ int make_plan(const letkf_config *c, Plan *p) {
     p->off_nloc = take(p->chunk_pts * sizeof(int));
     p->off_nloc_all = take(p->npts * sizeof(int));
     p->off_eigval = take(p->chunk_pts * c->k * sizeof(float));
+    // split eigensolve: the schedule, and a record of about twice the rotations that the
+    // implicit QL needs on these matrices (~k^2 / 2; overflowing points go to the fused kernel)
+    p->eig_schedule = c->eig_schedule;
+    const bool split = p->eig_schedule != LETKF_EIG_FUSED;
+    p->rcap = p->eig_schedule == LETKF_EIG_SPLIT_CHECK ? c->k : c->k * c->k + 4 * c->k;
+    p->off_de = take(split ? p->chunk_pts * c->k * sizeof(float2) : 0);
+    p->off_taus = take(split ? p->chunk_pts * c->k * sizeof(float) : 0);
+    p->off_rot = take(split ? p->chunk_pts * (size_t)p->rcap * sizeof(float2) : 0);
+    p->off_nrot = take(split ? p->chunk_pts * sizeof(int) : 0);
+    p->off_list = take(split ? (p->chunk_pts + 4) * sizeof(int) : 0);
     p->off_status = take(kAlign);
     p->total = align_up(off, kAlign);
     return LETKF_OK;
@@ -181,6 +198,8 @@ struct letkf_handle {
     lk::ObsNet net;
     float yref[3] = {0, 0, 0};
     int eig_blocks = 0;
+    lk::EigSplit eig_split;
+    int eig_schedule = LETKF_EIG_FUSED;  // resolved: FUSED, SPLIT or SPLIT_CHECK
     int tc_ctas = 0;
     letkf_stats stats;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -352,10 +371,15 @@ int enqueue_analysis(letkf_handle *h, letkf_probe *probe) {
         e.x = h->xg;
         e.pt0 = pt0;
         e.npts = npts;
-        e.eigval = (probe && probe->eigval) ? h->eigval : nullptr;
         e.status = h->status;
         e.max_blocks = h->eig_blocks;
-        CK(lk::launch_eigen_update(e, h->stream));
+        if (h->eig_schedule == LETKF_EIG_FUSED) {
+            e.eigval = (probe && probe->eigval) ? h->eigval : nullptr;
+            CK(lk::launch_eigen_update(e, h->stream));
+        } else {
+            e.eigval = h->eigval;
+            CK(lk::launch_eigen_split(e, h->eig_split, h->stream));
+        }
         if ((rc = mark(h, 6 + 2 * chunk))) return rc;
         ++chunk;
         if (probe && probe->eigval)
@@ -420,6 +444,64 @@ int letkf_workspace_size(const letkf_config *cfg, size_t *bytes) {
     return LETKF_OK;
 }
 
+// AUTO eigensolve schedule: both schedules timed on synthetic matrices of this k (a chunk's
+// worth of points, at most 16384) on the handle's stream, the faster kept.  The choice is
+// cached per (device, k, batch) for the life of the process, so that every handle of a
+// process with the same k and chunk size runs the same arithmetic.
+int autotune_eig_schedule(letkf_handle *h, int *out) {
+    static std::mutex mu;
+    static std::map<std::pair<int, std::pair<int, int>>, int> cache;
+    const int k = h->cfg.k;
+    const int batch = (int)std::min<size_t>(h->plan.chunk_pts, 16384);
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_pair(h->device, std::make_pair(k, batch));
+    const auto it = cache.find(key);
+    if (it != cache.end()) {
+        *out = it->second;
+        return LETKF_OK;
+    }
+    lk::EigArgs e;
+    e.k = k;
+    e.diag = (float)(k - 1);
+    e.gram = h->gram;
+    e.cvec = h->cvec;
+    e.nloc = h->nloc;
+    e.x = h->xg;
+    e.pt0 = 0;
+    e.npts = batch;
+    e.eigval = h->eigval;
+    e.status = h->status;
+    e.max_blocks = h->eig_blocks;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    float best[2] = {0.0f, 0.0f};
+    cudaError_t err = cudaEventCreate(&t0);
+    if (err == cudaSuccess) err = cudaEventCreate(&t1);
+    // (both schedules leave A's upper triangle intact: the inputs serve every run)
+    if (err == cudaSuccess) err = lk::launch_eigen_synthetic(e, 0x2308u, h->stream);
+    for (int sch = 0; sch < 2 && err == cudaSuccess; ++sch) {
+        for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
+            err = cudaEventRecord(t0, h->stream);
+            if (err == cudaSuccess)
+                err = sch == 0 ? lk::launch_eigen_update(e, h->stream)
+                               : lk::launch_eigen_split(e, h->eig_split, h->stream);
+            if (err == cudaSuccess) err = cudaEventRecord(t1, h->stream);
+            if (err == cudaSuccess) err = cudaEventSynchronize(t1);
+            float ms = 0.0f;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, t0, t1);
+            if (rep > 0 && (rep == 1 || ms < best[sch])) best[sch] = ms;  // run 0 warms up
+        }
+    }
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (err == cudaSuccess) err = cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
+    if (err != cudaSuccess) return LETKF_ECUDA;
+    *out = best[1] < best[0] ? LETKF_EIG_SPLIT : LETKF_EIG_FUSED;
+    cache[key] = *out;
+    return LETKF_OK;
+}
+
+
 int letkf_init(const letkf_config *cfg, void *workspace, size_t workspace_bytes,
                letkf_handle **out) {
     if (!out) return LETKF_EINVAL;
@@ -477,6 +559,15 @@ int letkf_init(const letkf_config *cfg, void *workspace, size_t workspace_bytes,
     h->nloc = (int *)(w + plan.off_nloc);
     h->nloc_all = (int *)(w + plan.off_nloc_all);
     h->eigval = (float *)(w + plan.off_eigval);
+    if (plan.eig_schedule != LETKF_EIG_FUSED) {
+        h->eig_split.de = (float2 *)(w + plan.off_de);
+        h->eig_split.taus = (float *)(w + plan.off_taus);
+        h->eig_split.rot = (float2 *)(w + plan.off_rot);
+        h->eig_split.nrot = (int *)(w + plan.off_nrot);
+        h->eig_split.list = (int *)(w + plan.off_list);
+        h->eig_split.list_count = h->eig_split.list + plan.chunk_pts;
+        h->eig_split.rcap = plan.rcap;
+    }
     h->status = (int *)(w + plan.off_status);
 
     const size_t npts = plan.npts;
@@ -528,7 +619,9 @@ int letkf_init(const letkf_config *cfg, void *workspace, size_t workspace_bytes,
     h->net.inv2r2 = plan.inv2r2;
 
     if (lk::gram_prepare(plan.kp) != cudaSuccess ||
-        lk::eigen_prepare(cfg->k, &h->eig_blocks) != cudaSuccess)
+        lk::eigen_prepare(cfg->k, &h->eig_blocks) != cudaSuccess ||
+        (plan.eig_schedule != LETKF_EIG_FUSED &&
+         lk::eigen_split_prepare(cfg->k, &h->eig_split) != cudaSuccess))
         return fail(LETKF_ECUDA);
     if (plan.tensor_gram) {
         int sms = 0;
@@ -563,6 +656,13 @@ int letkf_init(const letkf_config *cfg, void *workspace, size_t workspace_bytes,
     h->stats.max_local_obs = mx;
     h->stats.mean_local_obs = (double)sum / (double)npts;
     h->stats.n_chunks = n_chunks(h);
+    if (plan.eig_schedule == LETKF_EIG_AUTO) {
+        const int rc = autotune_eig_schedule(h, &h->eig_schedule);
+        if (rc) return fail(rc);
+    } else {
+        h->eig_schedule = plan.eig_schedule;
+    }
+    h->stats.eig_schedule = h->eig_schedule;
     *out = h;
     return LETKF_OK;
 }

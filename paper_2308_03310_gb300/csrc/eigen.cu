@@ -9,16 +9,25 @@
 //
 // The eigensolver follows the batched-EVD route the paper gives (Sec. III):
 // Householder tridiagonalization Q = H T H^T, then implicit-shift QL on T = Z L Z^T,
-// then the back-transform V = H Z.  It runs as one warp per matrix -- the paper's
-// warp-per-batch mapping -- with the matrix in shared memory.  W is never formed:
+// then the back-transform V = H Z.  W is never formed:
 //     C = [dX; c^T] V            (rows 0..8: dX V, row 9: (V^T c)^T)
 //     mean increment = C[0..8] L^-1 C[9]^T
 //     perturbations  = (sqrt(k-1) C[0..8] L^-1/2) V^T
 // (two 10 x k x k products instead of the k^3 product that forms W and the 9 k^2 one
 // that applies it).
-// In the QL phase every lane runs the same scalar recurrence on (d, e) in shared
-// memory, and each lane rotates its own columns of Z, carrying one row in registers
-// so that a rotation costs one shared load and one store per lane.
+//
+// Two schedules compute the same thing:
+//  * fused: one warp per matrix -- the paper's warp-per-batch mapping -- runs every phase
+//    with the matrix in shared memory.  In its QL phase every lane runs the same scalar
+//    recurrence on (d, e), and each lane rotates its own columns of Z, carrying one row in
+//    registers so that a rotation costs one shared load and one store per lane.
+//  * split: three launches.  (1) warp per matrix: tridiagonalization; (2) thread per
+//    matrix: the QL recurrence of 32 matrices per warp instruction, each thread recording
+//    its matrix's rotations (one header per sweep, then the sweep's (c, s) pairs) in global
+//    memory; (3) warp per matrix: Z = I, the recorded rotations replayed onto Z (no serial
+//    recurrence left on the warp's critical path), back-transform, transform and update.
+//    A matrix whose rotations outgrow its record is recomputed by the fused kernel, which
+//    finds A intact: reflectors live in the strictly lower triangle of the Gram slot.
 #include <float.h>
 
 #include "common.cuh"
@@ -30,21 +39,502 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxIter = 30;   // QL iterations per eigenvalue before ENOTCONV is latched
 constexpr int kRows = 10;      // right-hand-side rows: 9 populations + c
+constexpr int kQlThreads = 64; // split schedule, QL kernel: matrices per block
 
+__host__ __device__ inline int round4(int n) { return (n + 3) & ~3; }  // 16-byte slices
+// fused: S/Z (k x ld), B (kRows x ld), vw (k float2), de (k float2), taus (k), vtmp (k)
 __host__ __device__ inline int smem_floats(int k) {
     const int ld = k + 1;
-    const int n = k * ld + kRows * ld + 6 * k;
-    return (n + 3) & ~3;  // keep every warp's slice 16-byte aligned
+    return round4(k * ld + kRows * ld + 6 * k);
+}
+// split, tridiagonalization: S (k x ld), vw (k float2), de (k float2), taus (k)
+__host__ __device__ inline int tri_smem_floats(int k) { return round4(k * (k + 1) + 5 * k); }
+// split, vectors and update: Z (k x ld), B (kRows x ld), taus (k), vtmp (k)
+__host__ __device__ inline int vec_smem_floats(int k) {
+    const int ld = k + 1;
+    return round4(k * ld + kRows * ld + 2 * k);
+}
+
+// Reflector j (m = k-1-j entries) is kept in row k-1-j of the point's Gram slot, columns
+// 0..m-1: the strictly lower triangle, so the upper triangle and the diagonal, from which
+// Q is read, survive the tridiagonalization.
+__device__ __forceinline__ float *refl_row(float *Ag, int k, int j) {
+    return Ag + (size_t)(k - 1 - j) * k;
 }
 
 // Block shape per NC (columns per lane): warps per block and the resident blocks per SM that
-// the register budget targets, chosen with the shared memory per matrix (k x (k+1) + 10 (k+1)
-// + 6k floats) so that registers and shared memory allow the same number of matrices in flight.
+// the register budget targets, chosen with the shared memory per matrix so that registers
+// and shared memory allow the same number of matrices in flight.
 template <int NC>
 struct EigCfg {
     static constexpr int WARPS = NC == 1 ? 4 : (NC == 2 ? 2 : 1);
     static constexpr int MINB = NC == 1 ? 5 : (NC == 2 ? 5 : 3);
 };
+
+// ---- phases (one warp, one matrix) --------------------------------------------------------
+
+// Q = diag + A into S, symmetrised from the upper triangle of the Gram slot.
+template <int NC>
+__device__ __forceinline__ void load_q(const float *Ag, float *S, int k, int ld, int lane,
+                                       float diag) {
+    // ---- Q = diag + A, symmetrised from the upper triangle.  Rows are fetched eight at a
+    // time with every load of a batch issued before its shared stores.
+    for (int i0 = 0; i0 < k; i0 += 8) {
+        float v[8][NC];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int i = i0 + u, j = lane + 32 * c;
+                v[u][c] = (i < k && j < k) ? __ldcg(Ag + i * k + j) : 0.0f;
+            }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int i = i0 + u, j = lane + 32 * c;
+                if (i < k && j < k && j >= i) {
+                    S[i * ld + j] = v[u][c];
+                    S[j * ld + i] = v[u][c];
+                }
+            }
+    }
+    __syncwarp();
+    for (int i = lane; i < k; i += 32) S[i * ld + i] += diag;
+
+}
+
+// Forecast block of the point: B rows 0..8 = dX (perturbations), row 9 = c; returns X.
+template <int NC>
+__device__ __forceinline__ float *load_forecast(const EigArgs &a, size_t lp, float *B, int k,
+                                                int ld, int lane, float (&xbar)[NV]) {
+    // ---- forecast block: mean and perturbations of the 9 populations, and c
+    float *X = a.x + (size_t)(a.pt0 + lp) * NV * k;
+    float xv[NV][NC], cv[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int t = lane + 32 * c;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) xv[q][c] = t < k ? X[q * k + t] : 0.0f;
+        cv[c] = t < k ? __ldg(a.cvec + (size_t)lp * k + t) : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        float sum = 0.0f;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) sum += xv[q][c];
+        xbar[q] = warp_sum(sum) / (float)k;
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int t = lane + 32 * c;
+        if (t < k) {
+#pragma unroll
+            for (int q = 0; q < NV; ++q) B[q * ld + t] = xv[q][c] - xbar[q];
+            B[9 * ld + t] = cv[c];
+        }
+    }
+    __syncwarp();
+
+    return X;
+}
+
+// Householder tridiagonalization of S in place: (d, e) into de, scalars into taus, the
+// reflectors into shared memory and into the lower triangle of the Gram slot.
+template <int NC>
+__device__ __forceinline__ void tridiagonalize(float *Ag, float *S, float2 *vw, float2 *de,
+                                               float *taus, int k, int ld, int lane) {
+    // ---- Householder tridiagonalization, reflector j stored in row j of S (and in global
+    // memory, see refl_row)
+    for (int j = 0; j < k - 2; ++j) {
+        const int m = k - 1 - j;
+        float *vj = S + j * ld + j + 1;
+        float x[NC];
+        float tail = 0.0f;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int t = lane + 32 * c;
+            x[c] = t < m ? vj[t] : 0.0f;
+            if (t >= 1) tail = fmaf(x[c], x[c], tail);
+        }
+        tail = warp_sum(tail);
+        const float alpha = __shfl_sync(kFull, x[0], 0);
+        // H x = beta e_0 with beta = -sign(alpha) ||x||, tau = 1 + |alpha| / ||x||,
+        // v = x / (alpha - beta), v_0 = 1 (one rsqrt, one reciprocal, no division)
+        float tau = 0.0f, beta = alpha, scale = 0.0f;
+        if (tail > 0.0f) {
+            const float n2 = fmaf(alpha, alpha, tail);
+            float rn = rsqrtf(n2);
+            rn = rn * fmaf(-0.5f * n2, rn * rn, 1.5f);
+            const float nrm = n2 * rn;
+            beta = -copysignf(nrm, alpha);
+            tau = fmaf(fabsf(alpha), rn, 1.0f);
+            scale = copysignf(__frcp_rn(fabsf(alpha) + nrm), alpha);
+        }
+        float vt[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int t = lane + 32 * c;
+            vt[c] = t < m ? (t == 0 ? 1.0f : x[c] * scale) : 0.0f;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int t = lane + 32 * c;
+            if (t < m) {
+                vj[t] = vt[c];
+                refl_row(Ag, k, j)[t] = vt[c];  // lower triangle of the slot
+            }
+        }
+        if (lane == 0) {
+            taus[j] = tau;
+            de[j].y = beta;
+        }
+        __syncwarp();
+        if (tau != 0.0f) {
+            // p = tau S' v, with S' the trailing block (its column t is read by lane t);
+            // two accumulators halve the dependent FMA chain
+            float pv[NC], pw[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) pv[c] = pw[c] = 0.0f;
+            int s = 0;
+            for (; s + 2 <= m; s += 2) {
+                const float vs0 = vj[s], vs1 = vj[s + 1];
+                const float *r0 = S + (j + 1 + s) * ld + j + 1;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const int t = lane + 32 * c;
+                    if (t < m) {
+                        pv[c] = fmaf(r0[t], vs0, pv[c]);
+                        pw[c] = fmaf(r0[ld + t], vs1, pw[c]);
+                    }
+                }
+            }
+            if (s < m) {
+                const float vs0 = vj[s];
+                const float *r0 = S + (j + 1 + s) * ld + j + 1;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const int t = lane + 32 * c;
+                    if (t < m) pv[c] = fmaf(r0[t], vs0, pv[c]);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < NC; ++c) pv[c] += pw[c];
+            float kk = 0.0f;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                pv[c] *= tau;
+                kk = fmaf(pv[c], vt[c], kk);
+            }
+            const float K = 0.5f * tau * warp_sum(kk);
+            float wvl[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int t = lane + 32 * c;
+                wvl[c] = pv[c] - K * vt[c];
+                if (t < m) vw[t] = make_float2(vt[c], wvl[c]);
+            }
+            __syncwarp();
+            // S' -= v w^T + w v^T  (one 8-byte broadcast load of (v_s, w_s) per row)
+#pragma unroll 4
+            for (int s = 0; s < m; ++s) {
+                const float2 p2 = vw[s];
+                float *rowS = S + (j + 1 + s) * ld + j + 1;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const int t = lane + 32 * c;
+                    if (t < m) rowS[t] -= fmaf(p2.x, wvl[c], p2.y * vt[c]);
+                }
+            }
+            __syncwarp();
+        }
+    }
+    // ---- tridiagonal (d, e) into shared memory, e_t couples t and t+1
+    for (int t = lane; t < k; t += 32) {
+        de[t].x = S[t * ld + t];
+        if (t == k - 2) de[t].y = S[t * ld + t + 1];
+        if (t == k - 1) de[t].y = 0.0f;
+    }
+    __syncwarp();
+}
+
+// Z = I (Z[i][:] holds column i of the eigenvector matrix).
+template <int NC>
+__device__ __forceinline__ void set_identity(float *Z, int k, int ld, int lane) {
+    for (int i = 0; i < k; ++i)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int t = lane + 32 * c;
+            if (t < k) Z[i * ld + t] = (i == t) ? 1.0f : 0.0f;
+        }
+    __syncwarp();
+}
+
+// Implicit-shift QL on (d, e) with the rotations accumulated into Z (fused schedule).
+// Returns true if some eigenvalue did not converge.
+template <int NC>
+__device__ __forceinline__ bool ql_warp(float2 *de, float *Z, int k, int ld, int lane) {
+    const float eps = FLT_EPSILON;
+    // ---- implicit-shift QL on (d, e); Z accumulates the rotations (Z[i][:] = column i).
+    // Every lane runs the same scalar recurrence; d and e are read from shared memory
+    // (the next index is fetched one rotation ahead, off the dependency chain) and each
+    // rotation's results are written by all lanes with identical values, ordered by one
+    // __syncwarp per rotation.  The rotation needs 1/sqrt(f^2 + g^2): MUFU rsqrt refined
+    // by one Newton step; there is no branch on the hot path other than the underflow
+    // exit of the classical algorithm.
+    bool notconv = false;
+    for (int l = 0; l < k; ++l) {
+        int iter = 0;
+        for (;;) {
+            // first m >= l whose coupling e_m is negligible against |d_m| + |d_m+1|
+            int msplit = k - 1;
+#pragma unroll
+            for (int c = NC - 1; c >= 0; --c) {
+                const int t = lane + 32 * c;
+                bool small = false;
+                if (t >= l && t < k - 1) {
+                    const float2 a0 = de[t];
+                    small = fabsf(a0.y) <= eps * (fabsf(a0.x) + fabsf(de[t + 1].x));
+                }
+                const unsigned bal = __ballot_sync(kFull, small);
+                if (bal) msplit = 32 * c + __ffs(bal) - 1;
+            }
+            const int m = msplit;
+            if (m == l) break;
+            if (iter++ >= kMaxIter) {
+                notconv = true;
+                break;
+            }
+            // shift: eigenvalue of the leading 2 x 2 block nearer to d_l
+            const float2 del = de[l];
+            const float dl = del.x, el = del.y, dl1 = de[l + 1].x;
+            const float th = (dl1 - dl) / (2.0f * el);
+            const float rt = hypotf(th, 1.0f);
+            float di1 = de[m].x;
+            float g = di1 - dl + el / (th + copysignf(rt, th));
+            float s = 1.0f, co = 1.0f, pacc = 0.0f;
+            float zc[NC];  // carried column entries of row i+1 of Z
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int t = lane + 32 * c;
+                zc[c] = t < k ? Z[m * ld + t] : 0.0f;
+            }
+            float ei = de[m - 1].y, di = de[m - 1].x;
+            bool underflow = false;
+            int i = m - 1;
+            float *zp = Z + i * ld + lane;  // row i of Z at this lane's first column
+            for (; i >= l; --i) {
+                // next index fetched ahead; at i == l == 0 this reads the pair before de,
+                // which lies inside this warp's slice and is never used
+                const float2 dnext = de[i - 1];
+                const float f = s * ei, b = co * ei;
+                const float ff = fmaf(f, f, g * g);
+                __syncwarp();   // every lane has read index i+1 before it is rewritten
+                if (ff < 1e-30f) {  // f and g vanish: the coupling has underflowed
+                    de[i + 1] = make_float2(di1 - pacc, 0.0f);
+                    de[m].y = 0.0f;
+                    underflow = true;
+                    break;
+                }
+                float rinv = rsqrtf(ff);
+                rinv = rinv * fmaf(-0.5f * ff, rinv * rinv, 1.5f);
+                const float enew = ff * rinv;
+                s = f * rinv;
+                co = g * rinv;
+                g = di1 - pacc;
+                const float r = (di - g) * s + 2.0f * co * b;
+                pacc = s * r;
+                de[i + 1] = make_float2(g + pacc, enew);
+                g = co * r - b;
+                // Z <- Z G_i on columns i, i+1: row i+1 is final, row i is carried on
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    if (lane + 32 * c < k) {
+                        const float za = zp[32 * c];
+                        zp[ld + 32 * c] = s * za + co * zc[c];
+                        zc[c] = co * za - s * zc[c];
+                    }
+                }
+                zp -= ld;
+                di1 = di;
+                ei = dnext.y;
+                di = dnext.x;
+            }
+            // the carried row: row i+1 after an underflow break, row l after a full sweep
+            const int last = underflow ? i + 1 : l;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int t = lane + 32 * c;
+                if (t < k) Z[last * ld + t] = zc[c];
+            }
+            __syncwarp();
+            if (!underflow) {
+                de[l] = make_float2(di1 - pacc, g);
+                de[m].y = 0.0f;
+            }
+            __syncwarp();
+        }
+    }
+    return notconv;
+}
+
+// V = H Z in Z (reflectors from the Gram slot, scalars in taus).
+template <int NC>
+__device__ __forceinline__ void back_transform(float *Ag, float *Z, const float *taus,
+                                               float *vtmp, int k, int ld, int lane) {
+    // ---- V = H Z: the reflectors applied from the left, innermost first.  Lane owns
+    // column col of Z (a stored row, odd stride: no bank conflicts); every lane is busy
+    // and no cross-lane reduction is needed.  Reflector j comes back from the point's
+    // Gram slot (L2), fetched one reflector ahead.
+    float vnext[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int t = lane + 32 * c, m0 = 2;  // reflector k-3 has m = 2
+        vnext[c] = (k >= 3 && t < m0) ? __ldcg(refl_row(Ag, k, k - 3) + t) : 0.0f;
+    }
+    for (int j = k - 3; j >= 0; --j) {
+        const int m = k - 1 - j;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int t = lane + 32 * c;
+            if (t < m) vtmp[t] = vnext[c];
+        }
+        __syncwarp();
+        if (j > 0)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int t = lane + 32 * c;
+                vnext[c] = t < m + 1 ? __ldcg(refl_row(Ag, k, j - 1) + t) : 0.0f;
+            }
+        const float tau = taus[j];
+        const float *v = vtmp;
+        if (tau != 0.0f) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int col = lane + 32 * c;
+                if (col < k) {
+                    float *zc_ = Z + col * ld + j + 1;
+                    float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, d3 = 0.0f;
+                    int t = 0;
+                    for (; t + 4 <= m; t += 4) {
+                        d0 = fmaf(v[t], zc_[t], d0);
+                        d1 = fmaf(v[t + 1], zc_[t + 1], d1);
+                        d2 = fmaf(v[t + 2], zc_[t + 2], d2);
+                        d3 = fmaf(v[t + 3], zc_[t + 3], d3);
+                    }
+                    for (; t < m; ++t) d0 = fmaf(v[t], zc_[t], d0);
+                    const float beta = ((d0 + d1) + (d2 + d3)) * tau;
+#pragma unroll 4
+                    for (t = 0; t < m; ++t) zc_[t] = fmaf(-beta, v[t], zc_[t]);
+                }
+            }
+        }
+        __syncwarp();
+    }
+
+}
+
+// C = B V, mean increment, scaled perturbations, X^a written in place.
+template <int NC>
+__device__ __forceinline__ void transform_update(float *X, float *B, const float *Z,
+                                                 const float (&dr)[NC], const float (&xbar)[NV],
+                                                 int k, int ld, int lane, int *status) {
+    const float sk1 = sqrtf((float)(k - 1));
+    // ---- C = B V (C[r][j] = sum_i B[r][i] V[i][j], V[i][j] stored at Z[j][i]); lane owns j
+    float C[NC][kRows];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) C[c][r] = 0.0f;
+    for (int i = 0; i < k; ++i) {
+        float bi[kRows];
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) bi[r] = B[r * ld + i];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int t = lane + 32 * c;
+            const float z = t < k ? Z[t * ld + i] : 0.0f;
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) C[c][r] = fmaf(bi[r], z, C[c][r]);
+        }
+    }
+    // mean increment dX wbar = C[0..8] L^-1 C[9]; perturbation scaling sqrt(k-1) L^-1/2
+    float inc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) inc[q] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int t = lane + 32 * c;
+        if (t < k) {
+            const float lam = dr[c];
+            const float wl = C[c][9] / lam;
+            const float sc = sk1 / sqrtf(lam);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                inc[q] = fmaf(C[c][q], wl, inc[q]);
+                C[c][q] *= sc;
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NV; ++q) inc[q] = warp_sum(inc[q]);
+    __syncwarp();
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int t = lane + 32 * c;
+        if (t < k)
+#pragma unroll
+            for (int q = 0; q < NV; ++q) B[q * ld + t] = C[c][q];
+    }
+    __syncwarp();
+    // ---- F = D V^T: F[q][i] = sum_j D[q][j] V[i][j]; lane owns columns i
+    float E[NC][NV];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) E[c][q] = 0.0f;
+    for (int j = 0; j < k; ++j) {
+        float dj[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) dj[q] = B[q * ld + j];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int t = lane + 32 * c;
+            const float z = t < k ? Z[j * ld + t] : 0.0f;
+#pragma unroll
+            for (int q = 0; q < NV; ++q) E[c][q] = fmaf(dj[q], z, E[c][q]);
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int t = lane + 32 * c;
+        if (t < k)
+#pragma unroll
+            for (int q = 0; q < NV; ++q) B[q * ld + t] = E[c][q];
+    }
+    __syncwarp();
+    // ---- X^a = xbar + increment + perturbation, in place
+    bool bad = false;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        const float base = xbar[q] + inc[q];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int t = lane + 32 * c;
+            if (t < k) {
+                const float v = base + B[q * ld + t];
+                bad |= !isfinite(v);
+                X[q * k + t] = v;
+            }
+        }
+    }
+    if (__any_sync(kFull, bad) && lane == 0) atomicOr(status, ST_NONFINITE);
+    __syncwarp();
+}
+
+// ---- fused schedule -----------------------------------------------------------------------
 
 template <int NC>
 __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB)
@@ -55,7 +545,7 @@ __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB)
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     // S holds Q during the tridiagonalization; its reflectors are then kept in the point's
-    // (already consumed) Gram slot in global memory, and Z reuses S's shared memory.
+    // Gram slot in global memory, and Z reuses S's shared memory.
     float *S = smem + (size_t)wib * smem_floats(k);
     float *Z = S;
     float *B = S + k * ld;
@@ -66,290 +556,23 @@ __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB)
 
     const int warps_per_block = blockDim.x >> 5;
     const int nw = gridDim.x * warps_per_block;
-    const float eps = FLT_EPSILON;
-    const float sk1 = sqrtf((float)(k - 1));
+    // the whole chunk, or only the points of a list (matrices the split schedule hands back)
+    const int n = a.list ? *a.list_count : a.npts;
 
-    for (int lp = blockIdx.x * warps_per_block + wib; lp < a.npts; lp += nw) {
+    for (int it = blockIdx.x * warps_per_block + wib; it < n; it += nw) {
+        const int lp = a.list ? a.list[it] : it;
         if (a.nloc[lp] == 0) {  // no local observation: Q = (k-1)/rho I, X^a = X^f
             if (a.eigval)
                 for (int t = lane; t < k; t += 32) a.eigval[(size_t)lp * k + t] = a.diag;
             continue;
         }
-        // ---- Q = diag + A, symmetrised from the upper triangle.  Rows are fetched eight at a
-        // time with every load of a batch issued before its shared stores.
         float *Ag = a.gram + (size_t)lp * k * k;
-        for (int i0 = 0; i0 < k; i0 += 8) {
-            float v[8][NC];
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    const int i = i0 + u, j = lane + 32 * c;
-                    v[u][c] = (i < k && j < k) ? __ldcg(Ag + i * k + j) : 0.0f;
-                }
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    const int i = i0 + u, j = lane + 32 * c;
-                    if (i < k && j < k && j >= i) {
-                        S[i * ld + j] = v[u][c];
-                        S[j * ld + i] = v[u][c];
-                    }
-                }
-        }
-        __syncwarp();
-        for (int i = lane; i < k; i += 32) S[i * ld + i] += a.diag;
-
-        // ---- forecast block: mean and perturbations of the 9 populations, and c
-        float *X = a.x + (size_t)(a.pt0 + lp) * NV * k;
-        float xv[NV][NC], cv[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            const int t = lane + 32 * c;
-#pragma unroll
-            for (int q = 0; q < NV; ++q) xv[q][c] = t < k ? X[q * k + t] : 0.0f;
-            cv[c] = t < k ? __ldg(a.cvec + (size_t)lp * k + t) : 0.0f;
-        }
+        load_q<NC>(Ag, S, k, ld, lane, a.diag);
         float xbar[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            float sum = 0.0f;
-#pragma unroll
-            for (int c = 0; c < NC; ++c) sum += xv[q][c];
-            xbar[q] = warp_sum(sum) / (float)k;
-        }
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            const int t = lane + 32 * c;
-            if (t < k) {
-#pragma unroll
-                for (int q = 0; q < NV; ++q) B[q * ld + t] = xv[q][c] - xbar[q];
-                B[9 * ld + t] = cv[c];
-            }
-        }
-        __syncwarp();
-
-        // ---- Householder tridiagonalization, reflector j stored in row j of S
-        for (int j = 0; j < k - 2; ++j) {
-            const int m = k - 1 - j;
-            float *vj = S + j * ld + j + 1;
-            float x[NC];
-            float tail = 0.0f;
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const int t = lane + 32 * c;
-                x[c] = t < m ? vj[t] : 0.0f;
-                if (t >= 1) tail = fmaf(x[c], x[c], tail);
-            }
-            tail = warp_sum(tail);
-            const float alpha = __shfl_sync(kFull, x[0], 0);
-            // H x = beta e_0 with beta = -sign(alpha) ||x||, tau = 1 + |alpha| / ||x||,
-            // v = x / (alpha - beta), v_0 = 1 (one rsqrt, one reciprocal, no division)
-            float tau = 0.0f, beta = alpha, scale = 0.0f;
-            if (tail > 0.0f) {
-                const float n2 = fmaf(alpha, alpha, tail);
-                float rn = rsqrtf(n2);
-                rn = rn * fmaf(-0.5f * n2, rn * rn, 1.5f);
-                const float nrm = n2 * rn;
-                beta = -copysignf(nrm, alpha);
-                tau = fmaf(fabsf(alpha), rn, 1.0f);
-                scale = copysignf(__frcp_rn(fabsf(alpha) + nrm), alpha);
-            }
-            float vt[NC];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const int t = lane + 32 * c;
-                vt[c] = t < m ? (t == 0 ? 1.0f : x[c] * scale) : 0.0f;
-            }
-            __syncwarp();
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const int t = lane + 32 * c;
-                if (t < m) {
-                    vj[t] = vt[c];
-                    Ag[j * k + j + 1 + t] = vt[c];  // reflector j kept in row j of the slot
-                }
-            }
-            if (lane == 0) {
-                taus[j] = tau;
-                de[j].y = beta;
-            }
-            __syncwarp();
-            if (tau != 0.0f) {
-                // p = tau S' v, with S' the trailing block (its column t is read by lane t);
-                // two accumulators halve the dependent FMA chain
-                float pv[NC], pw[NC];
-#pragma unroll
-                for (int c = 0; c < NC; ++c) pv[c] = pw[c] = 0.0f;
-                int s = 0;
-                for (; s + 2 <= m; s += 2) {
-                    const float vs0 = vj[s], vs1 = vj[s + 1];
-                    const float *r0 = S + (j + 1 + s) * ld + j + 1;
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) {
-                        const int t = lane + 32 * c;
-                        if (t < m) {
-                            pv[c] = fmaf(r0[t], vs0, pv[c]);
-                            pw[c] = fmaf(r0[ld + t], vs1, pw[c]);
-                        }
-                    }
-                }
-                if (s < m) {
-                    const float vs0 = vj[s];
-                    const float *r0 = S + (j + 1 + s) * ld + j + 1;
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) {
-                        const int t = lane + 32 * c;
-                        if (t < m) pv[c] = fmaf(r0[t], vs0, pv[c]);
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < NC; ++c) pv[c] += pw[c];
-                float kk = 0.0f;
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    pv[c] *= tau;
-                    kk = fmaf(pv[c], vt[c], kk);
-                }
-                const float K = 0.5f * tau * warp_sum(kk);
-                float wvl[NC];
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    const int t = lane + 32 * c;
-                    wvl[c] = pv[c] - K * vt[c];
-                    if (t < m) vw[t] = make_float2(vt[c], wvl[c]);
-                }
-                __syncwarp();
-                // S' -= v w^T + w v^T  (one 8-byte broadcast load of (v_s, w_s) per row)
-#pragma unroll 4
-                for (int s = 0; s < m; ++s) {
-                    const float2 p2 = vw[s];
-                    float *rowS = S + (j + 1 + s) * ld + j + 1;
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) {
-                        const int t = lane + 32 * c;
-                        if (t < m) rowS[t] -= fmaf(p2.x, wvl[c], p2.y * vt[c]);
-                    }
-                }
-                __syncwarp();
-            }
-        }
-        // ---- tridiagonal (d, e) into shared memory, e_t couples t and t+1; Z = I over S
-        for (int t = lane; t < k; t += 32) {
-            de[t].x = S[t * ld + t];
-            if (t == k - 2) de[t].y = S[t * ld + t + 1];
-            if (t == k - 1) de[t].y = 0.0f;
-        }
-        __syncwarp();
-        for (int i = 0; i < k; ++i)
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const int t = lane + 32 * c;
-                if (t < k) Z[i * ld + t] = (i == t) ? 1.0f : 0.0f;
-            }
-        __syncwarp();
-
-        // ---- implicit-shift QL on (d, e); Z accumulates the rotations (Z[i][:] = column i).
-        // Every lane runs the same scalar recurrence; d and e are read from shared memory
-        // (the next index is fetched one rotation ahead, off the dependency chain) and each
-        // rotation's results are written by all lanes with identical values, ordered by one
-        // __syncwarp per rotation.  The rotation needs 1/sqrt(f^2 + g^2): MUFU rsqrt refined
-        // by one Newton step; there is no branch on the hot path other than the underflow
-        // exit of the classical algorithm.
-        bool notconv = false;
-        for (int l = 0; l < k; ++l) {
-            int iter = 0;
-            for (;;) {
-                // first m >= l whose coupling e_m is negligible against |d_m| + |d_m+1|
-                int msplit = k - 1;
-#pragma unroll
-                for (int c = NC - 1; c >= 0; --c) {
-                    const int t = lane + 32 * c;
-                    bool small = false;
-                    if (t >= l && t < k - 1) {
-                        const float2 a0 = de[t];
-                        small = fabsf(a0.y) <= eps * (fabsf(a0.x) + fabsf(de[t + 1].x));
-                    }
-                    const unsigned bal = __ballot_sync(kFull, small);
-                    if (bal) msplit = 32 * c + __ffs(bal) - 1;
-                }
-                const int m = msplit;
-                if (m == l) break;
-                if (iter++ >= kMaxIter) {
-                    notconv = true;
-                    break;
-                }
-                // shift: eigenvalue of the leading 2 x 2 block nearer to d_l
-                const float2 del = de[l];
-                const float dl = del.x, el = del.y, dl1 = de[l + 1].x;
-                const float th = (dl1 - dl) / (2.0f * el);
-                const float rt = hypotf(th, 1.0f);
-                float di1 = de[m].x;
-                float g = di1 - dl + el / (th + copysignf(rt, th));
-                float s = 1.0f, co = 1.0f, pacc = 0.0f;
-                float zc[NC];  // carried column entries of row i+1 of Z
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    const int t = lane + 32 * c;
-                    zc[c] = t < k ? Z[m * ld + t] : 0.0f;
-                }
-                float ei = de[m - 1].y, di = de[m - 1].x;
-                bool underflow = false;
-                int i = m - 1;
-                float *zp = Z + i * ld + lane;  // row i of Z at this lane's first column
-                for (; i >= l; --i) {
-                    // next index fetched ahead; at i == l == 0 this reads the pair before de,
-                    // which lies inside this warp's slice and is never used
-                    const float2 dnext = de[i - 1];
-                    const float f = s * ei, b = co * ei;
-                    const float ff = fmaf(f, f, g * g);
-                    __syncwarp();   // every lane has read index i+1 before it is rewritten
-                    if (ff < 1e-30f) {  // f and g vanish: the coupling has underflowed
-                        de[i + 1] = make_float2(di1 - pacc, 0.0f);
-                        de[m].y = 0.0f;
-                        underflow = true;
-                        break;
-                    }
-                    float rinv = rsqrtf(ff);
-                    rinv = rinv * fmaf(-0.5f * ff, rinv * rinv, 1.5f);
-                    const float enew = ff * rinv;
-                    s = f * rinv;
-                    co = g * rinv;
-                    g = di1 - pacc;
-                    const float r = (di - g) * s + 2.0f * co * b;
-                    pacc = s * r;
-                    de[i + 1] = make_float2(g + pacc, enew);
-                    g = co * r - b;
-                    // Z <- Z G_i on columns i, i+1: row i+1 is final, row i is carried on
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) {
-                        if (lane + 32 * c < k) {
-                            const float za = zp[32 * c];
-                            zp[ld + 32 * c] = s * za + co * zc[c];
-                            zc[c] = co * za - s * zc[c];
-                        }
-                    }
-                    zp -= ld;
-                    di1 = di;
-                    ei = dnext.y;
-                    di = dnext.x;
-                }
-                // the carried row: row i+1 after an underflow break, row l after a full sweep
-                const int last = underflow ? i + 1 : l;
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    const int t = lane + 32 * c;
-                    if (t < k) Z[last * ld + t] = zc[c];
-                }
-                __syncwarp();
-                if (!underflow) {
-                    de[l] = make_float2(di1 - pacc, g);
-                    de[m].y = 0.0f;
-                }
-                __syncwarp();
-            }
-        }
+        float *X = load_forecast<NC>(a, lp, B, k, ld, lane, xbar);
+        tridiagonalize<NC>(Ag, S, vw, de, taus, k, ld, lane);
+        set_identity<NC>(Z, k, ld, lane);
+        const bool notconv = ql_warp<NC>(de, Z, k, ld, lane);
         if (notconv && lane == 0) atomicOr(a.status, ST_NOTCONV);
         __syncwarp();
         float dr[NC];
@@ -358,167 +581,268 @@ __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB)
             const int t = lane + 32 * c;
             dr[c] = t < k ? de[t].x : 1.0f;
         }
-
-        // ---- V = H Z: the reflectors applied from the left, innermost first.  Lane owns
-        // column col of Z (a stored row, odd stride: no bank conflicts); every lane is busy
-        // and no cross-lane reduction is needed.  Reflector j comes back from row j of the
-        // point's Gram slot (L2), fetched one reflector ahead.
-        float vnext[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            const int t = lane + 32 * c, m0 = 2;  // reflector k-3 has m = 2
-            vnext[c] = (k >= 3 && t < m0) ? __ldcg(Ag + (k - 3) * k + (k - 2) + t) : 0.0f;
-        }
-        for (int j = k - 3; j >= 0; --j) {
-            const int m = k - 1 - j;
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const int t = lane + 32 * c;
-                if (t < m) vtmp[t] = vnext[c];
-            }
-            __syncwarp();
-            if (j > 0)
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    const int t = lane + 32 * c;
-                    vnext[c] = t < m + 1 ? __ldcg(Ag + (j - 1) * k + j + t) : 0.0f;
-                }
-            const float tau = taus[j];
-            const float *v = vtmp;
-            if (tau != 0.0f) {
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    const int col = lane + 32 * c;
-                    if (col < k) {
-                        float *zc_ = Z + col * ld + j + 1;
-                        float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, d3 = 0.0f;
-                        int t = 0;
-                        for (; t + 4 <= m; t += 4) {
-                            d0 = fmaf(v[t], zc_[t], d0);
-                            d1 = fmaf(v[t + 1], zc_[t + 1], d1);
-                            d2 = fmaf(v[t + 2], zc_[t + 2], d2);
-                            d3 = fmaf(v[t + 3], zc_[t + 3], d3);
-                        }
-                        for (; t < m; ++t) d0 = fmaf(v[t], zc_[t], d0);
-                        const float beta = ((d0 + d1) + (d2 + d3)) * tau;
-#pragma unroll 4
-                        for (t = 0; t < m; ++t) zc_[t] = fmaf(-beta, v[t], zc_[t]);
-                    }
-                }
-            }
-            __syncwarp();
-        }
-
+        back_transform<NC>(Ag, Z, taus, vtmp, k, ld, lane);
         if (a.eigval)
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 const int t = lane + 32 * c;
                 if (t < k) a.eigval[(size_t)lp * k + t] = dr[c];
             }
+        transform_update<NC>(X, B, Z, dr, xbar, k, ld, lane, a.status);
+    }
+}
 
-        // ---- C = B V (C[r][j] = sum_i B[r][i] V[i][j], V[i][j] stored at Z[j][i]); lane owns j
-        float C[NC][kRows];
-#pragma unroll
-        for (int c = 0; c < NC; ++c)
-#pragma unroll
-            for (int r = 0; r < kRows; ++r) C[c][r] = 0.0f;
-        for (int i = 0; i < k; ++i) {
-            float bi[kRows];
-#pragma unroll
-            for (int r = 0; r < kRows; ++r) bi[r] = B[r * ld + i];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const int t = lane + 32 * c;
-                const float z = t < k ? Z[t * ld + i] : 0.0f;
-#pragma unroll
-                for (int r = 0; r < kRows; ++r) C[c][r] = fmaf(bi[r], z, C[c][r]);
-            }
+// ---- split schedule -----------------------------------------------------------------------
+
+// (1) tridiagonalization, warp per matrix: (d, e) and the reflector scalars to global memory.
+template <int NC>
+__global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS) eig_tridiag_kernel(EigArgs a,
+                                                                             EigSplit sp) {
+    extern __shared__ float smem[];
+    const int k = a.k, ld = k + 1;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float *S = smem + (size_t)wib * tri_smem_floats(k);
+    float2 *vw = reinterpret_cast<float2 *>(S + k * ld);
+    float2 *de = vw + k;
+    float *taus = reinterpret_cast<float *>(de + k);
+    const int warps_per_block = blockDim.x >> 5;
+    const int nw = gridDim.x * warps_per_block;
+    for (int lp = blockIdx.x * warps_per_block + wib; lp < a.npts; lp += nw) {
+        if (a.nloc[lp] == 0) continue;
+        float *Ag = a.gram + (size_t)lp * k * k;
+        load_q<NC>(Ag, S, k, ld, lane, a.diag);
+        tridiagonalize<NC>(Ag, S, vw, de, taus, k, ld, lane);
+        for (int t = lane; t < k; t += 32) {
+            sp.de[(size_t)lp * k + t] = de[t];
+            sp.taus[(size_t)lp * k + t] = taus[t];
         }
-        // mean increment dX wbar = C[0..8] L^-1 C[9]; perturbation scaling sqrt(k-1) L^-1/2
-        float inc[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) inc[q] = 0.0f;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            const int t = lane + 32 * c;
-            if (t < k) {
-                const float lam = dr[c];
-                const float wl = C[c][9] / lam;
-                const float sc = sk1 / sqrtf(lam);
-#pragma unroll
-                for (int q = 0; q < NV; ++q) {
-                    inc[q] = fmaf(C[c][q], wl, inc[q]);
-                    C[c][q] *= sc;
-                }
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < NV; ++q) inc[q] = warp_sum(inc[q]);
-        __syncwarp();
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            const int t = lane + 32 * c;
-            if (t < k)
-#pragma unroll
-                for (int q = 0; q < NV; ++q) B[q * ld + t] = C[c][q];
-        }
-        __syncwarp();
-        // ---- F = D V^T: F[q][i] = sum_j D[q][j] V[i][j]; lane owns columns i
-        float E[NC][NV];
-#pragma unroll
-        for (int c = 0; c < NC; ++c)
-#pragma unroll
-            for (int q = 0; q < NV; ++q) E[c][q] = 0.0f;
-        for (int j = 0; j < k; ++j) {
-            float dj[NV];
-#pragma unroll
-            for (int q = 0; q < NV; ++q) dj[q] = B[q * ld + j];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const int t = lane + 32 * c;
-                const float z = t < k ? Z[j * ld + t] : 0.0f;
-#pragma unroll
-                for (int q = 0; q < NV; ++q) E[c][q] = fmaf(dj[q], z, E[c][q]);
-            }
-        }
-        __syncwarp();
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            const int t = lane + 32 * c;
-            if (t < k)
-#pragma unroll
-                for (int q = 0; q < NV; ++q) B[q * ld + t] = E[c][q];
-        }
-        __syncwarp();
-        // ---- X^a = xbar + increment + perturbation, in place
-        bool bad = false;
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            const float base = xbar[q] + inc[q];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const int t = lane + 32 * c;
-                if (t < k) {
-                    const float v = base + B[q * ld + t];
-                    bad |= !isfinite(v);
-                    X[q * k + t] = v;
-                }
-            }
-        }
-        if (__any_sync(kFull, bad) && lane == 0) atomicOr(a.status, ST_NONFINITE);
         __syncwarp();
     }
 }
 
+// (2) implicit-shift QL, thread per matrix: the recurrence of the fused schedule on (d, e)
+// kept in shared memory as [index][thread] (the threads of a warp touch consecutive words),
+// every rotation recorded.  Record of a point: per sweep a header (m, count) -- bit patterns
+// of two ints -- then the sweep's (c, s) for i = m-1 down to m-count.
+__global__ void __launch_bounds__(kQlThreads) eig_ql_kernel(EigArgs a, EigSplit sp) {
+    extern __shared__ float2 des[];  // [k][kQlThreads]
+    const int k = a.k, tid = threadIdx.x;
+    const int lp0 = blockIdx.x * kQlThreads;
+    const int lp = lp0 + tid;
+    // the block's (d, e) arrays are contiguous in global memory: coalesced load
+    const int nb = min(kQlThreads, a.npts - lp0);
+    for (int e = tid; e < nb * k; e += kQlThreads) {
+        const int p = e / k, i = e - p * k;
+        des[i * kQlThreads + p] = sp.de[(size_t)lp0 * k + e];
+    }
+    __syncthreads();
+    if (lp >= a.npts) return;
+    if (a.nloc[lp] == 0) {
+        for (int t = 0; t < k; ++t) a.eigval[(size_t)lp * k + t] = a.diag;
+        sp.nrot[lp] = 0;
+        return;
+    }
+    float2 *D = des + tid;  // D[i * kQlThreads] = (d_i, e_i)
+    constexpr int L = kQlThreads;
+    float2 *rec = sp.rot + (size_t)lp * sp.rcap;
+    const float eps = FLT_EPSILON;
+    int pos = 0;
+    bool notconv = false, overflow = false;
+    for (int l = 0; l < k && !overflow; ++l) {
+        int iter = 0;
+        for (;;) {
+            int m = l;
+            for (; m < k - 1; ++m) {
+                const float2 dm = D[m * L];
+                if (fabsf(dm.y) <= eps * (fabsf(dm.x) + fabsf(D[(m + 1) * L].x))) break;
+            }
+            if (m == l) break;
+            if (iter++ >= kMaxIter) {
+                notconv = true;
+                break;
+            }
+            if (pos + 1 + (m - l) > sp.rcap) {
+                overflow = true;
+                break;
+            }
+            // shift: eigenvalue of the leading 2 x 2 block nearer to d_l
+            const float2 del = D[l * L];
+            const float dl = del.x, el = del.y, dl1 = D[(l + 1) * L].x;
+            const float th = (dl1 - dl) / (2.0f * el);
+            const float rt = hypotf(th, 1.0f);
+            float di1 = D[m * L].x;
+            float g = di1 - dl + el / (th + copysignf(rt, th));
+            float s = 1.0f, co = 1.0f, pacc = 0.0f;
+            const int hdr = pos++;
+            float2 dcur = D[(m - 1) * L];
+            float ei = dcur.y, di = dcur.x;
+            bool underflow = false;
+            int i = m - 1;
+            for (; i >= l; --i) {
+                const float2 dnext = i > 0 ? D[(i - 1) * L] : make_float2(0.0f, 0.0f);
+                const float f = s * ei, b = co * ei;
+                const float ff = fmaf(f, f, g * g);
+                if (ff < 1e-30f) {  // f and g vanish: the coupling has underflowed
+                    D[(i + 1) * L] = make_float2(di1 - pacc, 0.0f);
+                    D[m * L].y = 0.0f;
+                    underflow = true;
+                    break;
+                }
+                float rinv = rsqrtf(ff);
+                rinv = rinv * fmaf(-0.5f * ff, rinv * rinv, 1.5f);
+                const float enew = ff * rinv;
+                s = f * rinv;
+                co = g * rinv;
+                g = di1 - pacc;
+                const float r = (di - g) * s + 2.0f * co * b;
+                pacc = s * r;
+                D[(i + 1) * L] = make_float2(g + pacc, enew);
+                g = co * r - b;
+                rec[pos++] = make_float2(co, s);
+                di1 = di;
+                ei = dnext.y;
+                di = dnext.x;
+            }
+            rec[hdr] = make_float2(__int_as_float(m), __int_as_float(pos - hdr - 1));
+            if (!underflow) {
+                D[l * L] = make_float2(di1 - pacc, g);
+                D[m * L].y = 0.0f;
+            }
+        }
+    }
+    if (notconv) atomicOr(a.status, ST_NOTCONV);
+    if (overflow) {  // handed to the fused kernel, which recomputes the point from A
+        sp.nrot[lp] = -1;
+        sp.list[atomicAdd(sp.list_count, 1)] = lp;
+        return;
+    }
+    sp.nrot[lp] = pos;
+    for (int t = 0; t < k; ++t) a.eigval[(size_t)lp * k + t] = D[t * L].x;
+}
+
+// (3) vectors, transform and update, warp per matrix: Z = I, the recorded rotations replayed
+// onto Z (each lane its own columns, the carried row in registers), V = H Z, then the
+// fused schedule's transform and update.
 template <int NC>
-cudaError_t prepare_nc(int k, int *max_blocks) {
-    const int warps = EigCfg<NC>::WARPS;
-    const size_t smem = (size_t)smem_floats(k) * sizeof(float) * warps;
-    auto kern = eigen_update_kernel<NC>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
+__global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB)
+    eig_vec_kernel(EigArgs a, EigSplit sp) {
+    extern __shared__ float smem[];
+    const int k = a.k, ld = k + 1;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float *Z = smem + (size_t)wib * vec_smem_floats(k);
+    float *B = Z + k * ld;
+    float *taus = B + kRows * ld;
+    float *vtmp = taus + k;
+    const int warps_per_block = blockDim.x >> 5;
+    const int nw = gridDim.x * warps_per_block;
+    for (int lp = blockIdx.x * warps_per_block + wib; lp < a.npts; lp += nw) {
+        const int nrec = sp.nrot[lp];
+        if (a.nloc[lp] == 0 || nrec < 0) continue;  // unchanged / recomputed by the fused kernel
+        float *Ag = a.gram + (size_t)lp * k * k;
+        float xbar[NV];
+        float *X = load_forecast<NC>(a, lp, B, k, ld, lane, xbar);
+        for (int t = lane; t < k; t += 32) taus[t] = sp.taus[(size_t)lp * k + t];
+        set_identity<NC>(Z, k, ld, lane);
+        // replay: the record is read 32 entries at a time, one per lane, and each entry is
+        // broadcast from its lane
+        const float2 *rec = sp.rot + (size_t)lp * sp.rcap;
+        int wbase = 0;
+        float2 win = lane < nrec ? __ldcs(rec + lane) : make_float2(0.0f, 0.0f);
+        auto entry = [&](int idx) -> float2 {
+            if (idx - wbase >= 32) {
+                wbase = idx;
+                win = idx + lane < nrec ? __ldcs(rec + idx + lane) : make_float2(0.0f, 0.0f);
+            }
+            const int src = idx - wbase;
+            return make_float2(__shfl_sync(kFull, win.x, src), __shfl_sync(kFull, win.y, src));
+        };
+        int pos = 0;
+        while (pos < nrec) {
+            const float2 h = entry(pos++);
+            const int m = __float_as_int(h.x), cnt = __float_as_int(h.y);
+            float zc[NC];  // carried column entries of row i+1 of Z
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int t = lane + 32 * c;
+                zc[c] = t < k ? Z[m * ld + t] : 0.0f;
+            }
+            float *zp = Z + (m - 1) * ld + lane;
+            for (int r = 0; r < cnt; ++r) {
+                const float2 cs = entry(pos++);
+                const float co = cs.x, s = cs.y;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    if (lane + 32 * c < k) {
+                        const float za = zp[32 * c];
+                        zp[ld + 32 * c] = s * za + co * zc[c];
+                        zc[c] = co * za - s * zc[c];
+                    }
+                }
+                zp -= ld;
+            }
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int t = lane + 32 * c;
+                if (t < k) Z[(m - cnt) * ld + t] = zc[c];
+            }
+        }
+        __syncwarp();
+        float dr[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int t = lane + 32 * c;
+            dr[c] = t < k ? a.eigval[(size_t)lp * k + t] : 1.0f;
+        }
+        back_transform<NC>(Ag, Z, taus, vtmp, k, ld, lane);
+        transform_update<NC>(X, B, Z, dr, xbar, k, ld, lane, a.status);
+    }
+}
+
+// Synthetic analysis inputs for timing the schedules: per point A = Y Y^T with Y (k x r),
+// r = min(2k, 12288/k), entries 0.7 u with u uniform in [-1/2, 1/2] from a counter-based
+// hash.  The spectrum of (k-1) I + A then needs about as many QL rotations (~0.9 k^2) as the
+// analyses of the forced-turbulence workloads do; c and the forecast block come from the same
+// hash, and every point gets one local observation so that none is skipped.
+__device__ __forceinline__ float hash_unit(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t h = a * 0x9E3779B1u ^ (b + 0x7F4A7C15u) * 0x85EBCA77u ^ (c + 0x165667B1u) * 0xC2B2AE3Du;
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 12;
+    h *= 0x297A2D39u;
+    h ^= h >> 15;
+    return (float)(h >> 8) * (1.0f / 16777216.0f) - 0.5f;
+}
+
+__host__ __device__ inline int synthetic_rank(int k) { return min(2 * k, 12288 / k); }
+
+__global__ void eig_synthetic_kernel(EigArgs a, uint32_t seed) {
+    extern __shared__ float ys[];  // [k][r] of this block's point
+    const int k = a.k, r = synthetic_rank(k);
+    const int lane = threadIdx.x;
+    const int w = blockIdx.x;
+    for (int e = lane; e < k * r; e += 32) ys[e] = 0.7f * hash_unit(seed + w, e / r, e % r);
+    __syncwarp();
+    float *Ag = a.gram + (size_t)w * k * k;
+    for (int i = 0; i < k; ++i)
+        for (int j = lane; j < k; j += 32) {
+            float s = 0.0f;
+            for (int q = 0; q < r; ++q) s = fmaf(ys[i * r + q], ys[j * r + q], s);
+            Ag[i * k + j] = s;
+        }
+    float *X = a.x + (size_t)(a.pt0 + w) * NV * k;
+    for (int t = lane; t < NV * k; t += 32) X[t] = 0.01f * hash_unit(seed ^ 0x5bd1e995u, w, t);
+    for (int t = lane; t < k; t += 32)
+        const_cast<float *>(a.cvec)[(size_t)w * k + t] = hash_unit(seed ^ 0x1b873593u, w, t);
+    if (lane == 0) const_cast<int *>(a.nloc)[w] = 1;
+}
+
+template <int NC>
+cudaError_t occupancy(const void *kern, int warps, size_t smem, int *max_blocks) {
     int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+        return e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return e;
@@ -530,13 +854,57 @@ cudaError_t prepare_nc(int k, int *max_blocks) {
 }
 
 template <int NC>
+cudaError_t prepare_nc(int k, int *max_blocks) {
+    const int warps = EigCfg<NC>::WARPS;
+    return occupancy<NC>((const void *)eigen_update_kernel<NC>, warps,
+                         (size_t)smem_floats(k) * sizeof(float) * warps, max_blocks);
+}
+
+template <int NC>
+cudaError_t prepare_split_nc(int k, EigSplit *sp) {
+    const int warps = EigCfg<NC>::WARPS;
+    cudaError_t e = occupancy<NC>((const void *)eig_tridiag_kernel<NC>, warps,
+                                  (size_t)tri_smem_floats(k) * sizeof(float) * warps,
+                                  &sp->grid_tri);
+    if (e != cudaSuccess) return e;
+    e = occupancy<NC>((const void *)eig_vec_kernel<NC>, warps,
+                      (size_t)vec_smem_floats(k) * sizeof(float) * warps, &sp->grid_vec);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(eig_ql_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(k * kQlThreads * sizeof(float2)));
+}
+
+unsigned grid_for(int max_blocks, long long npts, int warps) {
+    long long need = (npts + warps - 1) / warps;
+    long long blocks = max_blocks > 0 ? max_blocks : 1;
+    return (unsigned)(blocks > need ? need : blocks);
+}
+
+template <int NC>
 cudaError_t launch_nc(const EigArgs &a, cudaStream_t s) {
     const int warps = EigCfg<NC>::WARPS;
     const size_t smem = (size_t)smem_floats(a.k) * sizeof(float) * warps;
-    long long need = ((long long)a.npts + warps - 1) / warps;
-    long long blocks = a.max_blocks > 0 ? a.max_blocks : 1;
-    if (blocks > need) blocks = need;
-    eigen_update_kernel<NC><<<(unsigned)blocks, 32 * warps, smem, s>>>(a);
+    eigen_update_kernel<NC><<<grid_for(a.max_blocks, a.npts, warps), 32 * warps, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NC>
+cudaError_t launch_split_nc(const EigArgs &a, const EigSplit &sp, cudaStream_t s) {
+    const int warps = EigCfg<NC>::WARPS;
+    cudaError_t e = cudaMemsetAsync(sp.list_count, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    eig_tridiag_kernel<NC><<<grid_for(sp.grid_tri, a.npts, warps), 32 * warps,
+                             (size_t)tri_smem_floats(a.k) * sizeof(float) * warps, s>>>(a, sp);
+    eig_ql_kernel<<<(unsigned)((a.npts + kQlThreads - 1) / kQlThreads), kQlThreads,
+                    (size_t)a.k * kQlThreads * sizeof(float2), s>>>(a, sp);
+    eig_vec_kernel<NC><<<grid_for(sp.grid_vec, a.npts, warps), 32 * warps,
+                         (size_t)vec_smem_floats(a.k) * sizeof(float) * warps, s>>>(a, sp);
+    // matrices whose rotation record overflowed: the fused kernel over the list
+    EigArgs f = a;
+    f.list = sp.list;
+    f.list_count = sp.list_count;
+    eigen_update_kernel<NC><<<grid_for(a.max_blocks, a.npts, warps), 32 * warps,
+                              (size_t)smem_floats(a.k) * sizeof(float) * warps, s>>>(f);
     return cudaGetLastError();
 }
 
@@ -551,11 +919,35 @@ cudaError_t eigen_prepare(int k, int *max_blocks) {
     return cudaErrorInvalidValue;
 }
 
+cudaError_t eigen_split_prepare(int k, EigSplit *sp) {
+    if (k <= 32) return prepare_split_nc<1>(k, sp);
+    if (k <= 64) return prepare_split_nc<2>(k, sp);
+    if (k <= 128) return prepare_split_nc<4>(k, sp);
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_eigen_update(const EigArgs &a, cudaStream_t s) {
     if (a.npts <= 0) return cudaSuccess;
     if (a.k <= 32) return launch_nc<1>(a, s);
     if (a.k <= 64) return launch_nc<2>(a, s);
     if (a.k <= 128) return launch_nc<4>(a, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_eigen_synthetic(const EigArgs &a, uint32_t seed, cudaStream_t s) {
+    if (a.npts <= 0) return cudaSuccess;
+    const size_t smem = (size_t)a.k * synthetic_rank(a.k) * sizeof(float);  // <= 48 KiB
+    eig_synthetic_kernel<<<(unsigned)a.npts, 32, smem, s>>>(a, seed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eigen_split(const EigArgs &a, const EigSplit &sp, cudaStream_t s) {
+    if (a.npts <= 0) return cudaSuccess;
+    if (!a.eigval || !sp.de || !sp.taus || !sp.rot || !sp.nrot || !sp.list || !sp.list_count)
+        return cudaErrorInvalidValue;
+    if (a.k <= 32) return launch_split_nc<1>(a, sp, s);
+    if (a.k <= 64) return launch_split_nc<2>(a, sp, s);
+    if (a.k <= 128) return launch_split_nc<4>(a, sp, s);
     return cudaErrorInvalidValue;
 }
 

@@ -85,20 +85,38 @@ int gram_max_cells();
 
 // ---- eigen.cu -----------------------------------------------------------------
 struct EigArgs {
-    int k;
-    float diag;             // (k - 1) / rho_infl
-    float *gram;            // [npts][k][k]; consumed, then reused for the Householder vectors
-    const float *cvec;      // [npts][k]
-    const int *nloc;        // [npts]
-    float *x;               // grid-point-major ensemble [N][9][k], updated in place
-    long long pt0;          // first grid point of the chunk
-    int npts;
-    float *eigval;          // optional [npts][k] eigenvalues (ascending), NULL normally
-    int *status;            // device status word
-    int max_blocks;         // resident grid from eigen_prepare
+    int k = 0;
+    float diag = 0.0f;              // (k - 1) / rho_infl
+    float *gram = nullptr;          // [npts][k][k]; Q is read from the upper triangle and the
+                                    // diagonal, the Householder vectors go to the lower one
+    const float *cvec = nullptr;    // [npts][k]
+    const int *nloc = nullptr;      // [npts]
+    float *x = nullptr;             // grid-point-major ensemble [N][9][k], updated in place
+    long long pt0 = 0;              // first grid point of the chunk
+    int npts = 0;
+    float *eigval = nullptr;        // [npts][k] eigenvalues; optional for the fused schedule
+    int *status = nullptr;          // device status word
+    int max_blocks = 0;             // resident grid of the fused kernel (eigen_prepare)
+    const int *list = nullptr;      // fused kernel: only these points (count in *list_count)
+    const int *list_count = nullptr;
+};
+// Split schedule: scratch of one chunk and the resident grids of its kernels.
+struct EigSplit {
+    float2 *de = nullptr;           // [npts][k] tridiagonal (d_t, e_t)
+    float *taus = nullptr;          // [npts][k] reflector scalars
+    float2 *rot = nullptr;          // [npts][rcap] recorded QL rotations
+    int *nrot = nullptr;            // [npts] record length, -1: handed to the fused kernel
+    int *list = nullptr;            // [npts] points handed to the fused kernel
+    int *list_count = nullptr;      // [1]
+    int rcap = 0;                   // record capacity per point (entries)
+    int grid_tri = 0, grid_vec = 0; // resident grids (eigen_split_prepare)
 };
 cudaError_t eigen_prepare(int k, int *max_blocks);  // once per process and k
+cudaError_t eigen_split_prepare(int k, EigSplit *sp);
 cudaError_t launch_eigen_update(const EigArgs &a, cudaStream_t s);
+cudaError_t launch_eigen_split(const EigArgs &a, const EigSplit &sp, cudaStream_t s);
+// synthetic Gram matrices, c, forecast blocks and counts for timing the schedules
+cudaError_t launch_eigen_synthetic(const EigArgs &a, uint32_t seed, cudaStream_t s);
 size_t eigen_smem_per_warp(int k);
 
 }  // namespace lk

@@ -35,6 +35,10 @@ LETKF_LOC_GAUSS = 1
 
 LETKF_FP32 = 0
 LETKF_MIXED = 1
+LETKF_EIG_AUTO = 0
+LETKF_EIG_FUSED = 1
+LETKF_EIG_SPLIT = 2
+LETKF_EIG_SPLIT_CHECK = 3
 
 # Every symbol include/letkf.h declares, in declaration order.
 EXPORTED = (
@@ -55,14 +59,15 @@ class letkf_config(C.Structure):
         ("n_obs", C.c_int32), ("obs_xy", C.POINTER(C.c_int32)), ("obs_vars", C.c_int32),
         ("obs_err_var", C.POINTER(C.c_float)), ("loc_kind", C.c_int32),
         ("loc_radius", C.c_float), ("loc_cutoff2", C.c_float), ("infl", C.c_float),
-        ("precision", C.c_int32), ("chunk_bytes", C.c_int64), ("stream", C.c_void_p),
+        ("precision", C.c_int32), ("eig_schedule", C.c_int32), ("chunk_bytes", C.c_int64),
+        ("stream", C.c_void_p),
     ]
 
 
 class letkf_stats(C.Structure):
     _fields_ = [("status", C.c_int32), ("n_points", C.c_int32), ("n_zero_obs", C.c_int32),
                 ("max_local_obs", C.c_int32), ("mean_local_obs", C.c_double),
-                ("n_chunks", C.c_int32)]
+                ("n_chunks", C.c_int32), ("eig_schedule", C.c_int32)]
 
 
 class letkf_timings(C.Structure):
@@ -253,7 +258,8 @@ class Experiment:
 
     def __init__(self, nx, ny, k, tau, obs_xy, obs_err_var, obs_vars=LETKF_OBS_U | LETKF_OBS_V,
                  loc_radius=None, loc_cutoff2=0.0, force=None, n_aux=0, infl=1.0,
-                 precision=LETKF_FP32, chunk_bytes=0, stream=None, device=None):
+                 precision=LETKF_FP32, chunk_bytes=0, stream=None, device=None,
+                 eig_schedule=LETKF_EIG_AUTO):
         import torch
         self.torch = torch
         self.device = torch.device(device if device is not None else "cuda")
@@ -281,6 +287,7 @@ class Experiment:
         cfg.loc_cutoff2 = float(loc_cutoff2)
         cfg.infl = float(infl)
         cfg.precision = int(precision)
+        cfg.eig_schedule = int(eig_schedule)
         cfg.chunk_bytes = int(chunk_bytes)
         cfg.stream = self.stream.cuda_stream
         self.cfg = cfg

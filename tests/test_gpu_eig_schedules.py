@@ -1,0 +1,106 @@
+"""The eigensolve schedules against the FP64 oracle and against each other.
+
+FUSED runs every phase of a point's analysis in one warp; SPLIT runs the tridiagonalization
+(warp per point), the QL recurrence (thread per point, rotations recorded) and the replay,
+back-transform and update (warp per point) as three launches; SPLIT_CHECK is SPLIT with a
+rotation record of one sweep, so that nearly every point is handed back to the fused kernel,
+which recomputes it from the Gram matrix the split kernels left intact.  All three must meet
+the analysis bar (1e-5 relative L2 on mean, mean increment and perturbations) and SPLIT must
+agree with FUSED to within FP32 rounding of the two summation orders.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import lbm
+from paper_2308_03310_gb300 import _build, letkf as L
+from tests import _cases as C
+
+pytestmark = pytest.mark.gpu
+
+UV = L.LETKF_OBS_U | L.LETKF_OBS_V
+SCHEDULES = [L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT, L.LETKF_EIG_SPLIT_CHECK]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    _build.build()
+
+
+def _flat(a):
+    return np.asarray(a).transpose(0, 2, 3, 1).reshape(a.shape[0], -1)
+
+
+def _run(k, nx, ny, stride, radius, seed, schedule, precision=L.LETKF_FP32):
+    f0 = C.perturb_nonequilibrium(C.ensemble_state(k, nx, ny, seed=seed), 1e-4, seed + 1)
+    truth = C.ensemble_state(1, nx, ny, seed=seed + 7)
+    net = synth.regular_obs_network(nx, ny, stride)
+    var = np.full(len(net) * 2, 1e-4, dtype=np.float32)
+    exp = L.Experiment(nx, ny, k, 0.6, net, var, loc_radius=radius, precision=precision,
+                       eig_schedule=schedule)
+    yo = C.observations(truth, net, UV, 0.01, seed + 9)[0]
+    exp.set_state(f0)
+    pts = np.array([0, nx * ny // 2 + nx // 3, nx * ny - 1])
+    pr = exp.analyze_probe(yo, pts, want=("eigval",))
+    dev = C.dev64(exp.get_deviation())
+    assert exp.sync() == 0
+    return f0, yo, net, var, dev, pr["eigval"], pts
+
+
+@pytest.mark.parametrize("k,nx,ny,stride,radius", [
+    (5, 14, 12, 3, 2.5),
+    (16, 16, 16, 4, 3.0),
+    (32, 20, 18, 4, 3.0),
+    (64, 14, 14, 2, 3.0),
+    (100, 10, 10, 2, 2.0),
+    (128, 10, 9, 3, 2.5),
+])
+def test_schedules_match_oracle_and_each_other(k, nx, ny, stride, radius):
+    outs = {}
+    for sch in SCHEDULES:
+        f0, yo, net, var, dev, lam, pts = _run(k, nx, ny, stride, radius, 900 + k, sch)
+        outs[sch] = (dev, lam)
+    Xa_ref, ref = C.oracle_analysis(f0, yo, net, var, radius, UV,
+                                    points=[(p % nx, p // nx) for p in pts])
+    Xa_ref, _ = C.oracle_analysis(f0, yo, net, var, radius, UV)
+    Wb = lbm.W[None, :, None, None]
+    fb = _flat(f0.astype(np.float64) - Wb)
+    for sch, (dev, lam) in outs.items():
+        errs = C.point_parity(_flat(dev), _flat(Xa_ref - Wb), fb)
+        assert max(errs) < 1e-5, (sch, errs)
+        for i, p in enumerate(pts):
+            r = ref[(p % nx, p // nx)]
+            assert np.abs(np.sort(lam[i]) - r["lam"]).max() < 1e-5 * r["lam"].max(), sch
+    # split and fused: the same algorithm and recurrence, different summation orders only
+    fused, split = outs[L.LETKF_EIG_FUSED][0], outs[L.LETKF_EIG_SPLIT][0]
+    errs = C.point_parity(_flat(split), _flat(fused), fb)
+    assert max(errs) < 2e-6, errs
+    lf, ls = np.sort(outs[L.LETKF_EIG_FUSED][1], 1), np.sort(outs[L.LETKF_EIG_SPLIT][1], 1)
+    assert np.abs(lf - ls).max() <= 1e-6 * np.abs(lf).max()
+
+
+def test_split_schedule_in_mixed_precision_matches_oracle():
+    f0, yo, net, var, dev, _, _ = _run(64, 16, 16, 2, 3.0, 951, L.LETKF_EIG_SPLIT,
+                                       precision=L.LETKF_MIXED)
+    Xa_ref, _ = C.oracle_analysis(f0, yo, net, var, 3.0, UV)
+    Wb = lbm.W[None, :, None, None]
+    errs = C.point_parity(_flat(dev), _flat(Xa_ref - Wb), _flat(f0.astype(np.float64) - Wb))
+    assert max(errs) < 1e-5, errs
+
+
+def test_split_schedule_is_reproducible():
+    runs = [_run(32, 16, 16, 4, 3.0, 961, L.LETKF_EIG_SPLIT)[4] for _ in range(2)]
+    assert np.array_equal(runs[0], runs[1])
+
+
+def test_auto_schedule_resolves_once_per_process():
+    picks = []
+    for seed in (971, 972):
+        nx = ny = 12
+        net = synth.regular_obs_network(nx, ny, 3)
+        var = np.full(len(net) * 2, 1e-4, dtype=np.float32)
+        exp = L.Experiment(nx, ny, 48, 0.6, net, var, loc_radius=2.0)
+        picks.append(exp.stats().eig_schedule)
+        assert exp.sync() == 0
+    assert picks[0] in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT)
+    assert picks[0] == picks[1]
