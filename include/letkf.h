@@ -251,6 +251,28 @@ int letkf_local_analysis_noalloc(int32_t npts, int32_t k, int32_t lmaxv, const f
                                  const float *d_loc, const float *rinv_loc, float infl, float *x,
                                  void *stream);
 
+/* ---- batched symmetric eigensolver ----------------------------------------
+ * The eigensolve of the analysis (Sec. III: Householder tridiagonalization, implicit-shift QL,
+ * back-transform; one warp per matrix) on caller-supplied symmetric matrices, exposed on its
+ * own: Q_p = V_p diag(lambda_p) V_p^T for p < npts.
+ *   npts    number of matrices, >= 0
+ *   k       order, 2..128
+ *   q       device [npts][k][k], row-major; only the upper triangle with the diagonal is read.
+ *           The strictly lower triangle is overwritten (it receives the Householder vectors);
+ *           the upper triangle and the diagonal are left as they were.
+ *   eigval  device [npts][k] eigenvalues, in the order of the QL (not sorted)
+ *   evec    device [npts][k][k]; row i is the unit eigenvector of eigval[p][i]; NULL = skip
+ *   refine  1: one FP64 sweep over clustered eigenpairs (eigenvalues within relative distance
+ *           1e-6 of another, closer than the FP32 solve resolves): modified Gram-Schmidt within
+ *           the neighbourhood, then the Rayleigh quotient v^T Q v as the eigenvalue; 0: FP32
+ *           only
+ *   stream  cudaStream_t (NULL = legacy default stream)
+ * Allocates nothing.  Returns after the work has finished: LETKF_OK, LETKF_ENOTCONV (some QL
+ * iteration cap was hit) or LETKF_ENONFINITE; LETKF_EINVAL for bad arguments.  The status
+ * word shares the static scratch of letkf_local_analysis_noalloc: the same overlap rule holds. */
+int letkf_eigh_batch(int32_t npts, int32_t k, float *q, float *eigval, float *evec,
+                     int32_t refine, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -373,6 +373,8 @@ int enqueue_analysis(letkf_handle *h, letkf_probe *probe) {
         e.npts = npts;
         e.status = h->status;
         e.max_blocks = h->eig_blocks;
+        e.refine = c.precision == LETKF_MIXED ? 1 : 0;  // FP64 sweep over clustered eigenpairs
+        e.refine_tau = 1e-6f;
         if (h->eig_schedule == LETKF_EIG_FUSED) {
             e.eigval = (probe && probe->eigval) ? h->eigval : nullptr;
             CK(lk::launch_eigen_update(e, h->stream));

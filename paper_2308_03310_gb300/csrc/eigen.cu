@@ -534,6 +534,147 @@ __device__ __forceinline__ void transform_update(float *X, float *B, const float
     __syncwarp();
 }
 
+// ---- FP64 refinement of clustered eigenpairs ---------------------------------------------
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// One refinement sweep in FP64 for the eigenpairs whose eigenvalue has a neighbour within
+// relative distance tau: in index order, each such eigenvector is re-orthogonalized (modified
+// Gram-Schmidt) against the earlier vectors of its neighbourhood and normalized, then its
+// eigenvalue is replaced by the Rayleigh quotient v^T Q v with Q = diag I + A read from the
+// upper triangle of the Gram slot.  Z[i][:] holds eigenvector i, dr[c] the eigenvalue of
+// index lane + 32 c.  The only FP64 arithmetic of the analysis.
+template <int NC>
+__device__ __forceinline__ void refine_clusters(float *Z, int ld, const float *Ag, float diag,
+                                                int k, float (&dr)[NC], int lane, float tau) {
+    bool clus[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) clus[c] = false;
+    for (int j = 0; j < k; ++j) {
+        const float lj = __shfl_sync(kFull, dr[0], j & 31);
+        float lv = lj;
+#pragma unroll
+        for (int c = 1; c < NC; ++c)
+            if ((j >> 5) == c) lv = __shfl_sync(kFull, dr[c], j & 31);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int t = lane + 32 * c;
+            if (t < k && t != j && fabsf(dr[c] - lv) <= tau * fabsf(dr[c])) clus[c] = true;
+        }
+    }
+    auto value_of = [&](int i) -> float {  // eigenvalue i, broadcast from its lane
+        float v = __shfl_sync(kFull, dr[0], i & 31);
+#pragma unroll
+        for (int c = 1; c < NC; ++c)
+            if ((i >> 5) == c) v = __shfl_sync(kFull, dr[c], i & 31);
+        return v;
+    };
+    unsigned any = 0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) any |= __ballot_sync(kFull, clus[c]);
+    if (!any) return;
+    for (int i = 0; i < k; ++i) {
+        int ci = 0;
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            if ((i >> 5) == c) ci = __shfl_sync(kFull, clus[c] ? 1 : 0, i & 31);
+        if (!ci) continue;
+        const float li = value_of(i);
+        double v[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int t = lane + 32 * c;
+            v[c] = t < k ? (double)Z[i * ld + t] : 0.0;
+        }
+        for (int j = 0; j < i; ++j) {
+            if (fabsf(li - value_of(j)) > tau * fabsf(li)) continue;
+            double d = 0.0;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int t = lane + 32 * c;
+                if (t < k) d = fma(v[c], (double)Z[j * ld + t], d);
+            }
+            d = warp_sum_d(d);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int t = lane + 32 * c;
+                if (t < k) v[c] = fma(-d, (double)Z[j * ld + t], v[c]);
+            }
+        }
+        double n2 = 0.0;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) n2 = fma(v[c], v[c], n2);
+        const double rn = 1.0 / sqrt(warp_sum_d(n2));
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int t = lane + 32 * c;
+            if (t < k) Z[i * ld + t] = (float)(v[c] * rn);
+        }
+        __syncwarp();
+    }
+    // Rayleigh quotients v^T Q v of the re-orthogonalized vectors, up to four per pass over
+    // the upper triangle of Q (row r read coalesced; each off-diagonal entry counted twice)
+    constexpr int RB = 4;
+    int batch[RB], nb = 0;
+    auto flush = [&]() {
+        double part[RB];
+#pragma unroll
+        for (int b = 0; b < RB; ++b) part[b] = 0.0;
+        for (int r = 0; r < k; ++r) {
+            const float *qrow = Ag + (size_t)r * k;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int t = lane + 32 * c;
+                if (t < r || t >= k) continue;
+                double q = (double)__ldcg(qrow + t);
+                if (t == r) q += (double)diag;
+                const double w = t == r ? 1.0 : 2.0;
+#pragma unroll
+                for (int b = 0; b < RB; ++b)
+                    if (b < nb)
+                        part[b] = fma(q * w * (double)Z[batch[b] * ld + r],
+                                      (double)Z[batch[b] * ld + t], part[b]);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+            if (b >= nb) break;
+            const double rq = warp_sum_d(part[b]);
+            const int i = batch[b];
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                if ((i >> 5) == c && lane == (i & 31)) dr[c] = (float)rq;
+        }
+        nb = 0;
+    };
+    for (int i = 0; i < k; ++i) {
+        int ci = 0;
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            if ((i >> 5) == c) ci = __shfl_sync(kFull, clus[c] ? 1 : 0, i & 31);
+        if (!ci) continue;
+        batch[nb++] = i;
+        if (nb == RB) flush();
+    }
+    if (nb) flush();
+}
+
+// Eigenvector i (row i of Z) into out[i][:].
+template <int NC>
+__device__ __forceinline__ void store_vectors(const float *Z, int ld, float *out, int k, int lane) {
+    for (int i = 0; i < k; ++i)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int t = lane + 32 * c;
+            if (t < k) out[(size_t)i * k + t] = Z[i * ld + t];
+        }
+}
+
 // ---- fused schedule -----------------------------------------------------------------------
 
 template <int NC>
@@ -561,7 +702,7 @@ __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB)
 
     for (int it = blockIdx.x * warps_per_block + wib; it < n; it += nw) {
         const int lp = a.list ? a.list[it] : it;
-        if (a.nloc[lp] == 0) {  // no local observation: Q = (k-1)/rho I, X^a = X^f
+        if (a.nloc && a.nloc[lp] == 0) {  // no local observation: Q = (k-1)/rho I, X^a = X^f
             if (a.eigval)
                 for (int t = lane; t < k; t += 32) a.eigval[(size_t)lp * k + t] = a.diag;
             continue;
@@ -569,7 +710,7 @@ __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB)
         float *Ag = a.gram + (size_t)lp * k * k;
         load_q<NC>(Ag, S, k, ld, lane, a.diag);
         float xbar[NV];
-        float *X = load_forecast<NC>(a, lp, B, k, ld, lane, xbar);
+        float *X = a.x ? load_forecast<NC>(a, lp, B, k, ld, lane, xbar) : nullptr;
         tridiagonalize<NC>(Ag, S, vw, de, taus, k, ld, lane);
         set_identity<NC>(Z, k, ld, lane);
         const bool notconv = ql_warp<NC>(de, Z, k, ld, lane);
@@ -582,13 +723,22 @@ __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB)
             dr[c] = t < k ? de[t].x : 1.0f;
         }
         back_transform<NC>(Ag, Z, taus, vtmp, k, ld, lane);
+        if (a.refine) refine_clusters<NC>(Z, ld, Ag, a.diag, k, dr, lane, a.refine_tau);
+        if (a.evec) store_vectors<NC>(Z, ld, a.evec + (size_t)lp * k * k, k, lane);
         if (a.eigval)
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 const int t = lane + 32 * c;
                 if (t < k) a.eigval[(size_t)lp * k + t] = dr[c];
             }
-        transform_update<NC>(X, B, Z, dr, xbar, k, ld, lane, a.status);
+        if (X) {
+            transform_update<NC>(X, B, Z, dr, xbar, k, ld, lane, a.status);
+        } else {  // eigenpairs only: report non-finite eigenvalues
+            bool bad = false;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) bad |= lane + 32 * c < k && !isfinite(dr[c]);
+            if (__any_sync(kFull, bad) && lane == 0) atomicOr(a.status, ST_NONFINITE);
+        }
     }
 }
 
@@ -794,6 +944,15 @@ __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB)
             dr[c] = t < k ? a.eigval[(size_t)lp * k + t] : 1.0f;
         }
         back_transform<NC>(Ag, Z, taus, vtmp, k, ld, lane);
+        if (a.refine) {
+            refine_clusters<NC>(Z, ld, Ag, a.diag, k, dr, lane, a.refine_tau);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int t = lane + 32 * c;
+                if (t < k) a.eigval[(size_t)lp * k + t] = dr[c];
+            }
+        }
+        if (a.evec) store_vectors<NC>(Z, ld, a.evec + (size_t)lp * k * k, k, lane);
         transform_update<NC>(X, B, Z, dr, xbar, k, ld, lane, a.status);
     }
 }

@@ -99,6 +99,9 @@ struct EigArgs {
     int max_blocks = 0;             // resident grid of the fused kernel (eigen_prepare)
     const int *list = nullptr;      // fused kernel: only these points (count in *list_count)
     const int *list_count = nullptr;
+    float *evec = nullptr;          // optional [npts][k][k]: row i = eigenvector of eigval[i]
+    int refine = 0;                 // FP64 refinement sweep of clustered eigenpairs
+    float refine_tau = 0.0f;        // relative eigenvalue distance that makes a cluster
 };
 // Split schedule: scratch of one chunk and the resident grids of its kernels.
 struct EigSplit {

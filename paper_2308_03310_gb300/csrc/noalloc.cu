@@ -205,3 +205,34 @@ extern "C" int letkf_local_analysis_noalloc(int32_t npts, int32_t k, int32_t lma
     if (bits & lk::ST_NOTCONV) return LETKF_ENOTCONV;
     return LETKF_OK;
 }
+
+extern "C" int letkf_eigh_batch(int32_t npts, int32_t k, float *q, float *eigval, float *evec,
+                                int32_t refine, void *stream) {
+    if (npts < 0 || k < 2 || k > 128 || (refine != 0 && refine != 1)) return LETKF_EINVAL;
+    if (npts == 0) return LETKF_OK;
+    if (!q || !eigval) return LETKF_EINVAL;
+    float *base = nullptr;
+    if (lk::scratch_for_current_device(&base) != cudaSuccess) return LETKF_ECUDA;
+    int *status = reinterpret_cast<int *>(base + lk::kScratchFloats - 64);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return LETKF_ECUDA;
+    lk::EigArgs a;
+    a.k = k;
+    a.diag = 0.0f;           // the matrices are Q themselves
+    a.gram = q;
+    a.npts = npts;
+    a.eigval = eigval;
+    a.evec = evec;
+    a.refine = refine;
+    a.refine_tau = 1e-6f;
+    a.status = status;       // no counts, no forecast blocks: eigenpairs only
+    if (lk::eigen_prepare(k, &a.max_blocks) != cudaSuccess) return LETKF_ECUDA;
+    if (lk::launch_eigen_update(a, s) != cudaSuccess) return LETKF_ECUDA;
+    int bits = 0;
+    if (cudaMemcpyAsync(&bits, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return LETKF_ECUDA;
+    if (bits & lk::ST_NONFINITE) return LETKF_ENONFINITE;
+    if (bits & lk::ST_NOTCONV) return LETKF_ENOTCONV;
+    return LETKF_OK;
+}

@@ -46,7 +46,7 @@ EXPORTED = (
     "letkf_get_stats", "letkf_enable_timing", "letkf_get_timings", "letkf_set_state", "letkf_get_state", "letkf_set_deviation",
     "letkf_get_deviation", "letkf_set_macro", "lbm_forecast",
     "letkf_get_obs", "letkf_analyze", "letkf_analyze_probe", "letkf_cycle",
-    "letkf_local_analysis_noalloc",
+    "letkf_local_analysis_noalloc", "letkf_eigh_batch",
 )
 
 LETKF_NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -126,6 +126,7 @@ def load(path: str = LIB):
         "letkf_cycle": (C.c_int, [P, C.c_int32, P, C.c_int32]),
         "letkf_local_analysis_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, P, P,
                                                    C.c_float, P, P]),
+        "letkf_eigh_batch": (C.c_int, [C.c_int32, C.c_int32, P, P, P, C.c_int32, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -233,6 +234,14 @@ def letkf_local_analysis_noalloc(npts, k, lmaxv, dy_ptr, d_ptr, rinv_ptr, infl, 
     return load().letkf_local_analysis_noalloc(int(npts), int(k), int(lmaxv), C.c_void_p(dy_ptr),
                                                C.c_void_p(d_ptr), C.c_void_p(rinv_ptr),
                                                float(infl), C.c_void_p(x_ptr), C.c_void_p(stream))
+
+
+def letkf_eigh_batch(npts, k, q_ptr, eigval_ptr, evec_ptr, refine, stream):
+    """Eigenpairs of npts symmetric k x k matrices (device pointers; evec may be 0).
+    Returns the status code without raising."""
+    return load().letkf_eigh_batch(int(npts), int(k), C.c_void_p(q_ptr), C.c_void_p(eigval_ptr),
+                                   C.c_void_p(evec_ptr or None), int(refine),
+                                   C.c_void_p(stream))
 
 
 # ---------------------------------------------------------------- marshalling helpers
