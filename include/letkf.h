@@ -106,6 +106,8 @@ typedef struct letkf_stats {
     int32_t n_chunks;          /* Gram/eigensolve launch pairs per analysis             */
     int32_t eig_schedule;      /* LETKF_EIG_FUSED / SPLIT / SPLIT_CHECK in use (AUTO
                                   resolved at letkf_init)                               */
+    int32_t cuda_error;        /* first cudaError_t that made a call of this handle
+                                  return LETKF_ECUDA or LETKF_ENOMEM; 0 = none           */
 } letkf_stats;
 
 /* Device time of the phases of the most recent forecast and analysis (milliseconds, CUDA

@@ -217,6 +217,7 @@ namespace {
 int cuda_fail(letkf_handle *h, cudaError_t e) {
     if (e == cudaSuccess) return LETKF_OK;
     if (h && !h->latched) h->latched = LETKF_ECUDA;
+    if (h && !h->stats.cuda_error) h->stats.cuda_error = (int32_t)e;
     return e == cudaErrorMemoryAllocation ? LETKF_ENOMEM : LETKF_ECUDA;
 }
 

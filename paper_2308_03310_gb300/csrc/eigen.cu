@@ -995,12 +995,16 @@ __global__ void eig_synthetic_kernel(EigArgs a, uint32_t seed) {
     if (lane == 0) const_cast<int *>(a.nloc)[w] = 1;
 }
 
+// The dynamic shared-memory cap of a kernel is a process-wide attribute shared by every
+// handle: it is set for the largest k the kernel's template serves (the shared memory grows
+// with k), never for one handle's k, so that no handle can lower it under another's launch.
 template <int NC>
-cudaError_t occupancy(const void *kern, int warps, size_t smem, int *max_blocks) {
+cudaError_t occupancy(const void *kern, int warps, size_t smem, size_t smem_cap,
+                      int *max_blocks) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem)) != cudaSuccess)
+                                  (int)smem_cap)) != cudaSuccess)
         return e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
@@ -1012,11 +1016,14 @@ cudaError_t occupancy(const void *kern, int warps, size_t smem, int *max_blocks)
     return cudaSuccess;
 }
 
+constexpr int kmax_of(int nc) { return 32 * nc; }  // largest k of an NC instantiation
+
 template <int NC>
 cudaError_t prepare_nc(int k, int *max_blocks) {
     const int warps = EigCfg<NC>::WARPS;
     return occupancy<NC>((const void *)eigen_update_kernel<NC>, warps,
-                         (size_t)smem_floats(k) * sizeof(float) * warps, max_blocks);
+                         (size_t)smem_floats(k) * sizeof(float) * warps,
+                         (size_t)smem_floats(kmax_of(NC)) * sizeof(float) * warps, max_blocks);
 }
 
 template <int NC>
@@ -1024,13 +1031,16 @@ cudaError_t prepare_split_nc(int k, EigSplit *sp) {
     const int warps = EigCfg<NC>::WARPS;
     cudaError_t e = occupancy<NC>((const void *)eig_tridiag_kernel<NC>, warps,
                                   (size_t)tri_smem_floats(k) * sizeof(float) * warps,
+                                  (size_t)tri_smem_floats(kmax_of(NC)) * sizeof(float) * warps,
                                   &sp->grid_tri);
     if (e != cudaSuccess) return e;
     e = occupancy<NC>((const void *)eig_vec_kernel<NC>, warps,
-                      (size_t)vec_smem_floats(k) * sizeof(float) * warps, &sp->grid_vec);
+                      (size_t)vec_smem_floats(k) * sizeof(float) * warps,
+                      (size_t)vec_smem_floats(kmax_of(NC)) * sizeof(float) * warps,
+                      &sp->grid_vec);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(eig_ql_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(k * kQlThreads * sizeof(float2)));
+                                (int)(128 * kQlThreads * sizeof(float2)));
 }
 
 unsigned grid_for(int max_blocks, long long npts, int warps) {

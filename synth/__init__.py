@@ -26,7 +26,7 @@ import numpy as np
 __all__ = [
     "generator", "taylor_green_velocity", "kolmogorov_force", "band_limited_force",
     "regular_obs_network", "clustered_obs_network", "gaussian", "Workload", "WORKLOADS",
-    "loc_cutoff2",
+    "loc_cutoff2", "poisson_requests",
 ]
 
 
@@ -232,3 +232,22 @@ WORKLOADS = {
         loc_radius=12.0, steps_per_cycle=100, cycles=50, init="turbulence", truth_noise=1e-3,
         kolmogorov_amp=1e-5, kolmogorov_n=4, random_rms=1e-5, spinup=20000),
 }
+
+
+def poisson_requests(n: int, rate_hz: float, seed: int, grids=(128, 256, 512, 1024),
+                     ks=(16, 32, 64, 128), cycles=(10, 100), strides=(4, 8)) -> list:
+    """A seeded stream of independent DA experiments: Poisson arrivals at rate_hz, grid edge,
+    ensemble size and observation stride drawn uniformly from the given sets, cycle counts
+    uniform in [cycles[0], cycles[1]].  Returns dicts (rid, arrival_s, nx, ny, k, obs_stride,
+    cycles, seed) in arrival order."""
+    rng = generator(seed)
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += float(rng.exponential(1.0 / rate_hz))
+        g = int(rng.choice(grids))
+        out.append(dict(rid=i, arrival_s=t, nx=g, ny=g, k=int(rng.choice(ks)),
+                        obs_stride=int(rng.choice(strides)),
+                        cycles=int(rng.integers(cycles[0], cycles[1] + 1)),
+                        seed=seed * 100003 + i))
+    return out

@@ -104,3 +104,28 @@ def test_auto_schedule_resolves_once_per_process():
         assert exp.sync() == 0
     assert picks[0] in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT)
     assert picks[0] == picks[1]
+
+
+@pytest.mark.parametrize("k_big,k_small", [(16, 8), (128, 100), (64, 33)])
+def test_handles_of_different_k_coexist(k_big, k_small):
+    # the kernels' shared-memory caps are process-wide: a later handle with a smaller k
+    # must not lower them under an earlier handle with a larger k
+    for sch in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT):
+        first = _run(k_big, 10, 10, 2, 2.0, 980 + k_big, sch)          # builds handle 1
+        nx = ny = 10
+        net = synth.regular_obs_network(nx, ny, 2)
+        var = np.full(len(net) * 2, 1e-4, dtype=np.float32)
+        f0 = C.perturb_nonequilibrium(C.ensemble_state(k_big, nx, ny, seed=981), 1e-4, 982)
+        a = L.Experiment(nx, ny, k_big, 0.6, net, var, loc_radius=2.0, eig_schedule=sch)
+        b = L.Experiment(nx, ny, k_small, 0.6, net, var, loc_radius=2.0, eig_schedule=sch)
+        a.set_state(f0)
+        truth = C.ensemble_state(1, nx, ny, seed=983)
+        yo = C.observations(truth, net, UV, 0.01, 984)[0]
+        a.analyze(yo)                                   # after b lowered nothing
+        dev = C.dev64(a.get_deviation())
+        assert a.sync() == 0 and b.sync() == 0
+        Xa_ref, _ = C.oracle_analysis(f0, yo, net, var, 2.0, UV)
+        Wb = lbm.W[None, :, None, None]
+        errs = C.point_parity(_flat(dev), _flat(Xa_ref - Wb), _flat(f0.astype(np.float64) - Wb))
+        assert max(errs) < 1e-5, (sch, errs)
+        del first
