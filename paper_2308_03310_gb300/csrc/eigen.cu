@@ -283,11 +283,23 @@ __device__ __forceinline__ bool ql_warp(float2 *de, float *Z, int k, int ld, int
     // __syncwarp per rotation.  The rotation needs 1/sqrt(f^2 + g^2): MUFU rsqrt refined
     // by one Newton step; there is no branch on the hot path other than the underflow
     // exit of the classical algorithm.
+    // Deflation: a coupling e_m is negligible once |e_m| <= eps ||T|| (||T|| the largest
+    // |d_t| + |e_t| + |e_t-1|).  A test against the local |d_m| + |d_m+1| alone never fires
+    // inside a cluster of small eigenvalues next to large ones: every sweep through the large
+    // entries leaves rounding of order eps ||T|| on the small couplings.
+    float tn = 0.0f;
+    for (int t = lane; t < k; t += 32) {
+        const float2 a0 = de[t];
+        tn = fmaxf(tn, fabsf(a0.x) + fabsf(a0.y) + (t > 0 ? fabsf(de[t - 1].y) : 0.0f));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tn = fmaxf(tn, __shfl_xor_sync(kFull, tn, o));
+    const float tol = eps * tn;
     bool notconv = false;
     for (int l = 0; l < k; ++l) {
         int iter = 0;
         for (;;) {
-            // first m >= l whose coupling e_m is negligible against |d_m| + |d_m+1|
+            // first m >= l whose coupling e_m is negligible
             int msplit = k - 1;
 #pragma unroll
             for (int c = NC - 1; c >= 0; --c) {
@@ -295,7 +307,7 @@ __device__ __forceinline__ bool ql_warp(float2 *de, float *Z, int k, int ld, int
                 bool small = false;
                 if (t >= l && t < k - 1) {
                     const float2 a0 = de[t];
-                    small = fabsf(a0.y) <= eps * (fabsf(a0.x) + fabsf(de[t + 1].x));
+                    small = fabsf(a0.y) <= tol;
                 }
                 const unsigned bal = __ballot_sync(kFull, small);
                 if (bal) msplit = 32 * c + __ffs(bal) - 1;
@@ -796,6 +808,11 @@ __global__ void __launch_bounds__(kQlThreads) eig_ql_kernel(EigArgs a, EigSplit 
     constexpr int L = kQlThreads;
     float2 *rec = sp.rot + (size_t)lp * sp.rcap;
     const float eps = FLT_EPSILON;
+    float tn = 0.0f;  // deflation threshold eps ||T||, as in the fused schedule
+    for (int t = 0; t < k; ++t)
+        tn = fmaxf(tn, fabsf(D[t * L].x) + fabsf(D[t * L].y) +
+                           (t > 0 ? fabsf(D[(t - 1) * L].y) : 0.0f));
+    const float tol = eps * tn;
     int pos = 0;
     bool notconv = false, overflow = false;
     for (int l = 0; l < k && !overflow; ++l) {
@@ -804,7 +821,7 @@ __global__ void __launch_bounds__(kQlThreads) eig_ql_kernel(EigArgs a, EigSplit 
             int m = l;
             for (; m < k - 1; ++m) {
                 const float2 dm = D[m * L];
-                if (fabsf(dm.y) <= eps * (fabsf(dm.x) + fabsf(D[(m + 1) * L].x))) break;
+                if (fabsf(dm.y) <= tol) break;
             }
             if (m == l) break;
             if (iter++ >= kMaxIter) {

@@ -249,6 +249,12 @@ class Server:
             if not progressed:
                 self.sleep(2e-4)
         wall = self.clock() - t0
+        errors = []
+        for slot, _ in active:          # stopped by the time limit: drain, collect the status
+            try:
+                slot.close()
+            except RuntimeError as err:
+                errors.append(str(err))
         lat = [x for s in done for x in s.latencies_ms] + \
               [x for s, _ in active for x in s.latencies_ms]
         return {
@@ -266,6 +272,8 @@ class Server:
             "peak_footprint_bytes": peak,
             "max_concurrent": max_conc,
             "slots": done,
+            "unfinished": len(active) + len(pending),
+            "errors": errors,
             "timeline": timeline,
         }
 

@@ -129,3 +129,26 @@ def test_handles_of_different_k_coexist(k_big, k_small):
         errs = C.point_parity(_flat(dev), _flat(Xa_ref - Wb), _flat(f0.astype(np.float64) - Wb))
         assert max(errs) < 1e-5, (sch, errs)
         del first
+
+
+@pytest.mark.parametrize("sch", [L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT])
+def test_large_ensemble_with_rank_deficient_gram_converges(sch):
+    # k = 128 with ~84 local observed scalars and sigma = 1e-3: Q = 127 I + a rank-84 term
+    # with eigenvalues in the thousands (the case that exhausted the QL iteration cap when
+    # deflation was tested against the local diagonal only)
+    nx = ny = 24
+    k = 128
+    f0 = C.perturb_nonequilibrium(C.ensemble_state(k, nx, ny, seed=991), 2e-3, 992)
+    net = synth.regular_obs_network(nx, ny, 4)
+    var = np.full(len(net) * 2, 1e-6, dtype=np.float32)
+    exp = L.Experiment(nx, ny, k, 0.6, net, var, loc_radius=4.0, eig_schedule=sch)
+    exp.set_state(f0)
+    truth = C.ensemble_state(1, nx, ny, seed=993)
+    yo = C.observations(truth, net, UV, 1e-3, 994)[0]
+    exp.analyze(yo)
+    dev = C.dev64(exp.get_deviation())
+    assert exp.sync() == 0
+    Xa_ref, _ = C.oracle_analysis(f0, yo, net, var, 4.0, UV)
+    Wb = lbm.W[None, :, None, None]
+    errs = C.point_parity(_flat(dev), _flat(Xa_ref - Wb), _flat(f0.astype(np.float64) - Wb))
+    assert max(errs) < 1e-5, errs

@@ -124,3 +124,19 @@ def test_refinement_on_clustered_spectra(k):
     for i in range(2):
         assert errs[1][i] <= 1.02 * errs[0][i] + 1e-8, errs
         assert errs[1][i] < 1e-5, errs
+
+
+@pytest.mark.parametrize("k,rank,top", [(128, 84, 2000.0), (64, 40, 5000.0), (32, 20, 1e4)])
+def test_small_cluster_next_to_large_eigenvalues_converges(k, rank, top):
+    # (k-1) I + a rank-r term with eigenvalues up to `top`: k - r equal eigenvalues beside
+    # large ones.  QL must deflate the equal block although every sweep through the large
+    # entries leaves rounding of order eps ||Q|| on its couplings (threshold eps ||T||).
+    rng = np.random.default_rng(k + rank)
+    Q = np.empty((6, k, k), np.float32)
+    for p in range(6):
+        U, _ = np.linalg.qr(rng.standard_normal((k, rank)))
+        lam = np.geomspace(1.0, top, rank)
+        Q[p] = ((k - 1) * np.eye(k) + (U * lam) @ U.T).astype(np.float32)
+    for refine in (0, 1):
+        _, lam, vec = _solve(Q, refine)                 # LETKF_OK, not ENOTCONV
+        _check_pairs(Q, lam, vec)
