@@ -560,6 +560,10 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // eigenvalue is replaced by the Rayleigh quotient v^T Q v with Q = diag I + A read from the
 // upper triangle of the Gram slot.  Z[i][:] holds eigenvector i, dr[c] the eigenvalue of
 // index lane + 32 c.  The only FP64 arithmetic of the analysis.
+// Eigenvalues at the floor diag (within 1e-4 relative: directions where A is negligible,
+// A's near-null space) are left alone: there Q is diag I to within the cluster's width, the
+// matrix functions of the transform are flat, and a cluster of tens of such eigenvalues would
+// cost O(cluster^2 k + cluster k^2) FP64 operations for nothing.
 template <int NC>
 __device__ __forceinline__ void refine_clusters(float *Z, int ld, const float *Ag, float diag,
                                                 int k, float (&dr)[NC], int lane, float tau) {
@@ -578,6 +582,9 @@ __device__ __forceinline__ void refine_clusters(float *Z, int ld, const float *A
             if (t < k && t != j && fabsf(dr[c] - lv) <= tau * fabsf(dr[c])) clus[c] = true;
         }
     }
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+        if (diag > 0.0f && fabsf(dr[c] - diag) <= 1e-4f * diag) clus[c] = false;
     auto value_of = [&](int i) -> float {  // eigenvalue i, broadcast from its lane
         float v = __shfl_sync(kFull, dr[0], i & 31);
 #pragma unroll

@@ -43,7 +43,6 @@ constexpr int kProdThreads = 32 * kProdWarps, kEpiThreads = 32 * kEpiWarps;
 constexpr uint32_t kTmemCols = 512;
 static_assert(kWarpEpi + kEpiWarps == kWarpProd, "warp roles");
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
-constexpr uint32_t kSuspendNs = 20000;  // a waiting thread sleeps until the phase completes
 
 template <int KP>
 struct TcShape {
@@ -120,10 +119,10 @@ __device__ __forceinline__ void bar_arrive(uint64_t *bar) {
 __device__ __forceinline__ bool bar_try(uint64_t *bar, uint32_t parity) {
     uint32_t done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
+        : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     return done != 0;
 }
@@ -756,11 +755,28 @@ cudaError_t launch_gram_tc(const GramArgs &a, int *status, int max_ctas, cudaStr
     const long long tiles =
         (long long)((a.nx + TW - 1) / TW) * ((a.y_end - a.y_begin + TH - 1) / TH);
     const unsigned grid = (unsigned)(tiles < max_ctas ? tiles : max_ctas);
-    if (a.kp == 64)
-        gram_tc_kernel<64><<<grid, kTcThreads, TcShape<64>::SMEM, s>>>(a, status);
-    else
-        gram_tc_kernel<128><<<grid, kTcThreads, TcShape<128>::SMEM, s>>>(a, status);
-    return cudaGetLastError();
+    // Each CTA needs an SM to itself (~190 KB of shared memory, all tensor-memory columns).
+    // Launched at the device's highest priority, its CTAs are placed ahead of the pending
+    // blocks of other streams as SMs drain, instead of waiting behind kernels with small
+    // blocks that keep refilling them (several handles sharing the GPU).
+    int lo = 0, hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = hi;  // numerically lowest = highest priority
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kTcThreads);
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (a.kp == 64) {
+        cfg.dynamicSmemBytes = TcShape<64>::SMEM;
+        return cudaLaunchKernelEx(&cfg, gram_tc_kernel<64>, a, status);
+    }
+    cfg.dynamicSmemBytes = TcShape<128>::SMEM;
+    return cudaLaunchKernelEx(&cfg, gram_tc_kernel<128>, a, status);
 }
 
 }  // namespace lk
