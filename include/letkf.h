@@ -219,6 +219,29 @@ int letkf_analyze_probe(letkf_handle *h, const float *yo, int32_t where, letkf_p
  * once per nsteps into a CUDA graph and replayed. */
 int letkf_cycle(letkf_handle *h, int32_t nsteps, const float *yo, int32_t where);
 
+/* ---- groups of co-resident ensembles ------------------------------------
+ * Several experiments (handles) of one device analysed as one batch, e.g. ensembles of
+ * different sizes over the same or different grids and observation networks.  Per handle the
+ * observation operator, the transposes and the localized Gram matrices run as in
+ * letkf_analyze; the eigensolve, transform and update of the grid points of all handles run as
+ * one persistent launch per column class (k <= 32, <= 64, <= 128) in which every warp takes the
+ * next grid point from a global counter, so points with any number of local observations
+ * (including none) and matrices of every order balance over the GPU.  The eigensolve is the
+ * fused schedule of each point (the result of every handle equals its LETKF_EIG_FUSED
+ * letkf_analyze bit for bit).
+ *   hs     n distinct handles of one device, 1 <= n <= 8; the work runs on hs[0]'s stream,
+ *          ordered after each handle's earlier work and before its later work
+ *   yo     n observation vectors (where = LETKF_HOST/DEVICE), yo[i] of handle hs[i]
+ * letkf_group_cycle(hs, n, nsteps, yo, where): every handle's lbm_forecast(nsteps) and the
+ * group analysis, captured once per (membership, state buffers, nsteps) into a CUDA graph
+ * kept by hs[0] (at most 8 such graphs, the oldest dropped) and replayed.  Phase timing of the
+ * handles is not recorded by group calls.  Device errors are reported by each handle's
+ * letkf_sync. */
+int letkf_group_analyze(letkf_handle *const *hs, const float *const *yo, int32_t n,
+                        int32_t where);
+int letkf_group_cycle(letkf_handle *const *hs, int32_t n, int32_t nsteps,
+                      const float *const *yo, int32_t where);
+
 /* ---- local analysis without any device allocation -------------------------------
  * The paper has no counterpart of this entry point; it serves callers that cannot call
  * cudaMalloc and therefore cannot create a handle (whose workspace must be allocated by

@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <new>
@@ -204,6 +205,14 @@ struct letkf_handle {
     letkf_stats stats;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int graph_nsteps[2] = {-1, -1};
+    unsigned long long serial = 0;  // unique per handle of the process (group graph keys)
+    struct GroupGraph {             // captured group cycles led by this handle
+        std::vector<unsigned long long> members;
+        std::vector<int> cur;
+        int nsteps = -1;
+        cudaGraphExec_t exec = nullptr;
+    };
+    std::vector<GroupGraph> group_graphs;
     int latched = 0;  // host-side error waiting for letkf_sync
     // phase timing: forecast start/end, then analysis boundaries
     bool timing = false;
@@ -303,6 +312,57 @@ int enqueue_obs(letkf_handle *h) {
 }
 
 // Analysis kernels after yo is on the device.  probe may be NULL.
+lk::GramArgs gram_args(letkf_handle *h, int y0, int y1) {
+    lk::GramArgs g;
+    g.net = h->net;
+    g.nx = h->cfg.nx;
+    g.ny = h->cfg.ny;
+    g.k = h->cfg.k;
+    g.kp = h->plan.kp;
+    g.yb = h->yb;
+    g.ybar = h->ybar;
+    g.yo = h->yo;
+    g.rinv = h->rinv;
+    for (int v = 0; v < 3; ++v) g.yref[v] = h->yref[v];
+    g.y_begin = y0;
+    g.y_end = y1;
+    g.gram = h->gram;
+    g.cvec = h->cvec;
+    g.nloc = h->nloc;
+    g.orec = h->orec;
+    return g;
+}
+
+// Gram matrices and c of the chunk of rows [y0, y1) (the chunk index selects the records pass)
+int enqueue_gram_chunk(letkf_handle *h, int chunk, int y0, int y1) {
+    const lk::GramArgs g = gram_args(h, y0, y1);
+    if (h->plan.tensor_gram && chunk == 0) CK(lk::launch_obs_records(g, h->orec, h->stream));
+    if (h->plan.tensor_gram)
+        CK(lk::launch_gram_tc(g, h->status, h->tc_ctas, h->stream));
+    else
+        CK(lk::launch_gram(g, h->stream));
+    return LETKF_OK;
+}
+
+lk::EigArgs eig_args(letkf_handle *h, int y0, int y1) {
+    const int k = h->cfg.k;
+    lk::EigArgs e;
+    e.k = k;
+    e.diag = (float)((double)(k - 1) / (double)h->cfg.infl);
+    e.gram = h->gram;
+    e.cvec = h->cvec;
+    e.nloc = h->nloc;
+    e.x = h->xg;
+    e.pt0 = (long long)y0 * h->cfg.nx;
+    e.npts = (y1 - y0) * h->cfg.nx;
+    e.eigval = h->eigval;
+    e.status = h->status;
+    e.max_blocks = h->eig_blocks;
+    e.refine = h->cfg.precision == LETKF_MIXED ? 1 : 0;  // FP64 sweep over clustered eigenpairs
+    e.refine_tau = 1e-6f;
+    return e;
+}
+
 int enqueue_analysis(letkf_handle *h, letkf_probe *probe) {
     const Plan &p = h->plan;
     const letkf_config &c = h->cfg;
@@ -321,28 +381,7 @@ int enqueue_analysis(letkf_handle *h, letkf_probe *probe) {
                                cudaMemcpyDeviceToHost, h->stream));
     for (int y0 = 0; y0 < c.ny; y0 += p.chunk_rows) {
         const int y1 = std::min(c.ny, y0 + p.chunk_rows);
-        lk::GramArgs g;
-        g.net = h->net;
-        g.nx = c.nx;
-        g.ny = c.ny;
-        g.k = k;
-        g.kp = p.kp;
-        g.yb = h->yb;
-        g.ybar = h->ybar;
-        g.yo = h->yo;
-        g.rinv = h->rinv;
-        for (int v = 0; v < 3; ++v) g.yref[v] = h->yref[v];
-        g.y_begin = y0;
-        g.y_end = y1;
-        g.gram = h->gram;
-        g.cvec = h->cvec;
-        g.nloc = h->nloc;
-        g.orec = h->orec;
-        if (p.tensor_gram && chunk == 0) CK(lk::launch_obs_records(g, h->orec, h->stream));
-        if (p.tensor_gram)
-            CK(lk::launch_gram_tc(g, h->status, h->tc_ctas, h->stream));
-        else
-            CK(lk::launch_gram(g, h->stream));
+        if ((rc = enqueue_gram_chunk(h, chunk, y0, y1))) return rc;
         if ((rc = mark(h, 5 + 2 * chunk))) return rc;
         const long long pt0 = (long long)y0 * c.nx;
         const int npts = (y1 - y0) * c.nx;
@@ -363,19 +402,7 @@ int enqueue_analysis(letkf_handle *h, letkf_probe *probe) {
                                        h->stream));
             }
         }
-        lk::EigArgs e;
-        e.k = k;
-        e.diag = (float)((double)(k - 1) / (double)c.infl);
-        e.gram = h->gram;
-        e.cvec = h->cvec;
-        e.nloc = h->nloc;
-        e.x = h->xg;
-        e.pt0 = pt0;
-        e.npts = npts;
-        e.status = h->status;
-        e.max_blocks = h->eig_blocks;
-        e.refine = c.precision == LETKF_MIXED ? 1 : 0;  // FP64 sweep over clustered eigenpairs
-        e.refine_tau = 1e-6f;
+        lk::EigArgs e = eig_args(h, y0, y1);
         if (h->eig_schedule == LETKF_EIG_FUSED) {
             e.eigval = (probe && probe->eigval) ? h->eigval : nullptr;
             CK(lk::launch_eigen_update(e, h->stream));
@@ -399,6 +426,116 @@ int enqueue_analysis(letkf_handle *h, letkf_probe *probe) {
     return LETKF_OK;
 }
 
+// ---- groups of handles -----------------------------------------------------------------
+
+constexpr int kMaxGroup = 8;
+
+// Resident grids of the grouped eigen kernels, per device, prepared once per process.
+int group_blocks(int device, const int **out) {
+    static std::mutex mu;
+    static std::map<int, std::vector<int>> grids;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = grids.find(device);
+    if (it == grids.end()) {
+        std::vector<int> g(3, 0);
+        if (lk::eigen_group_prepare(g.data()) != cudaSuccess) return LETKF_ECUDA;
+        it = grids.emplace(device, g).first;
+    }
+    *out = it->second.data();
+    return LETKF_OK;
+}
+
+int check_group(letkf_handle *const *hs, int n) {
+    if (!hs || n < 1 || n > kMaxGroup) return LETKF_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        if (!hs[i] || hs[i]->device != hs[0]->device) return LETKF_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == hs[i]) return LETKF_EINVAL;
+    }
+    return LETKF_OK;
+}
+
+// While it lives, every handle of the group enqueues on the group stream S (the first
+// handle's), with its phase timing switched off.
+struct GroupScope {
+    letkf_handle *const *hs;
+    int n;
+    cudaStream_t st[kMaxGroup];
+    bool tm[kMaxGroup];
+    GroupScope(letkf_handle *const *hs_, int n_) : hs(hs_), n(n_) {
+        for (int i = 0; i < n; ++i) {
+            st[i] = hs[i]->stream;
+            tm[i] = hs[i]->timing;
+            hs[i]->stream = hs[0]->stream;
+            hs[i]->timing = false;
+        }
+    }
+    ~GroupScope() {
+        for (int i = 0; i < n; ++i) {
+            hs[i]->stream = st[i];
+            hs[i]->timing = tm[i];
+        }
+    }
+};
+
+// Orders the group stream after each handle's own stream (join = false), or each handle's
+// stream after the group stream (join = true).
+int group_fence(letkf_handle *const *hs, int n, bool join) {
+    letkf_handle *h = hs[0];
+    for (int i = 1; i < n; ++i) {
+        if (hs[i]->stream == h->stream) continue;
+        cudaEvent_t ev = nullptr;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        const cudaError_t e1 = cudaEventRecord(ev, join ? h->stream : hs[i]->stream);
+        const cudaError_t e2 =
+            e1 == cudaSuccess ? cudaStreamWaitEvent(join ? hs[i]->stream : h->stream, ev, 0) : e1;
+        cudaEventDestroy(ev);
+        CK(e2);
+    }
+    return LETKF_OK;
+}
+
+// The group's work on the group stream (inside a GroupScope): optional forecasts, then per
+// handle the observation operator and transpose; per chunk round every handle's Gram chunk and
+// one grouped eigen launch per column class over all of them; the transposes back.
+int enqueue_group(letkf_handle *const *hs, int n, int nsteps) {
+    letkf_handle *h = hs[0];
+    const int *blocks = nullptr;
+    int rc = group_blocks(h->device, &blocks);
+    if (rc) return rc;
+    for (int i = 0; i < n && nsteps >= 0; ++i)
+        if ((rc = enqueue_forecast(hs[i], nsteps))) return rc;
+    int rounds = 0;
+    for (int i = 0; i < n; ++i) {
+        letkf_handle *g = hs[i];
+        if ((rc = enqueue_obs(g))) return rc;
+        const cudaError_t e = lk::launch_transpose_in(g->state[g->cur], g->xg, g->cfg.k,
+                                                      g->plan.npts, h->stream);
+        if (e != cudaSuccess) return cuda_fail(g, e);
+        rounds = std::max(rounds, (g->cfg.ny + g->plan.chunk_rows - 1) / g->plan.chunk_rows);
+    }
+    for (int r = 0; r < rounds; ++r) {
+        lk::EigArgs segs[kMaxGroup];
+        int m = 0;
+        for (int i = 0; i < n; ++i) {
+            letkf_handle *g = hs[i];
+            const int y0 = r * g->plan.chunk_rows;
+            if (y0 >= g->cfg.ny) continue;
+            const int y1 = std::min(g->cfg.ny, y0 + g->plan.chunk_rows);
+            if ((rc = enqueue_gram_chunk(g, r, y0, y1))) return rc;
+            segs[m++] = eig_args(g, y0, y1);
+        }
+        CK(lk::launch_eigen_group(segs, m, h->status + 16, blocks, h->stream));
+    }
+    for (int i = 0; i < n; ++i) {
+        letkf_handle *g = hs[i];
+        const cudaError_t e = lk::launch_transpose_out(g->xg, g->state[g->cur], g->cfg.k,
+                                                       g->plan.npts, h->stream);
+        if (e != cudaSuccess) return cuda_fail(g, e);
+    }
+    return LETKF_OK;
+}
+
 int status_to_code(int bits) {
     if (bits & lk::ST_NONFINITE) return LETKF_ENONFINITE;
     if (bits & lk::ST_NOTCONV) return LETKF_ENOTCONV;
@@ -413,6 +550,9 @@ void destroy_graphs(letkf_handle *h) {
         h->graph[i] = nullptr;
         h->graph_nsteps[i] = -1;
     }
+    for (auto &gg : h->group_graphs)
+        if (gg.exec) cudaGraphExecDestroy(gg.exec);
+    h->group_graphs.clear();
 }
 
 void destroy_events(letkf_handle *h) {
@@ -522,6 +662,8 @@ int letkf_init(const letkf_config *cfg, void *workspace, size_t workspace_bytes,
     h->cfg.obs_err_var = nullptr;
     h->plan = plan;
     memset(&h->stats, 0, sizeof(h->stats));
+    static std::atomic<unsigned long long> serials{0};
+    h->serial = ++serials;
     auto fail = [&](int code) {
         letkf_destroy(h);
         return code;
@@ -895,6 +1037,82 @@ int letkf_cycle(letkf_handle *h, int32_t nsteps, const float *yo, int32_t where)
     CK(cudaGraphLaunch(h->graph[slot], h->stream));
     h->cur ^= (nsteps & 1);
     return LETKF_OK;
+}
+
+int letkf_group_analyze(letkf_handle *const *hs, const float *const *yo, int32_t n,
+                        int32_t where) {
+    int rc = check_group(hs, n);
+    if (rc) return rc;
+    if (where != LETKF_HOST && where != LETKF_DEVICE) return LETKF_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (hs[i]->plan.LV > 0 && (!yo || !yo[i])) return LETKF_EINVAL;
+    letkf_handle *h = hs[0];
+    if ((rc = device_check(h))) return rc;
+    if ((rc = group_fence(hs, n, false))) return rc;
+    {
+        GroupScope scope(hs, n);
+        for (int i = 0; i < n && !rc; ++i)
+            rc = copy_in(hs[i], hs[i]->yo, yo[i], (size_t)hs[i]->plan.LV * sizeof(float), where);
+        if (!rc) rc = enqueue_group(hs, n, -1);
+    }
+    if (rc) return rc;
+    return group_fence(hs, n, true);
+}
+
+int letkf_group_cycle(letkf_handle *const *hs, int32_t n, int32_t nsteps, const float *const *yo,
+                      int32_t where) {
+    int rc = check_group(hs, n);
+    if (rc) return rc;
+    if (nsteps < 0 || (where != LETKF_HOST && where != LETKF_DEVICE)) return LETKF_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (hs[i]->plan.LV > 0 && (!yo || !yo[i])) return LETKF_EINVAL;
+    letkf_handle *h = hs[0];
+    if ((rc = device_check(h))) return rc;
+    if ((rc = group_fence(hs, n, false))) return rc;
+    {
+        GroupScope scope(hs, n);
+        for (int i = 0; i < n && !rc; ++i)
+            rc = copy_in(hs[i], hs[i]->yo, yo[i], (size_t)hs[i]->plan.LV * sizeof(float), where);
+        if (rc) return rc;
+        // the captured graph of this membership, state buffers and step count
+        std::vector<unsigned long long> ids(n);
+        std::vector<int> cur(n);
+        for (int i = 0; i < n; ++i) {
+            ids[i] = hs[i]->serial;
+            cur[i] = hs[i]->cur;
+        }
+        letkf_handle::GroupGraph *gg = nullptr;
+        for (auto &e : h->group_graphs)
+            if (e.members == ids && e.cur == cur && e.nsteps == nsteps) gg = &e;
+        if (!gg) {
+            if (h->group_graphs.size() >= 8) {  // bounded cache: drop the oldest
+                if (h->group_graphs.front().exec) cudaGraphExecDestroy(h->group_graphs.front().exec);
+                h->group_graphs.erase(h->group_graphs.begin());
+            }
+            CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed));
+            rc = enqueue_group(hs, n, nsteps);
+            cudaGraph_t g = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(h->stream, &g);
+            for (int i = 0; i < n; ++i) hs[i]->cur = cur[i];
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (ec != cudaSuccess) return cuda_fail(h, ec);
+            letkf_handle::GroupGraph e;
+            e.members = ids;
+            e.cur = cur;
+            e.nsteps = nsteps;
+            const cudaError_t ei = cudaGraphInstantiate(&e.exec, g, 0);
+            cudaGraphDestroy(g);
+            if (ei != cudaSuccess) return cuda_fail(h, ei);
+            h->group_graphs.push_back(e);
+            gg = &h->group_graphs.back();
+        }
+        CK(cudaGraphLaunch(gg->exec, h->stream));
+        for (int i = 0; i < n; ++i) hs[i]->cur ^= (nsteps & 1);
+    }
+    return group_fence(hs, n, true);
 }
 
 }  // extern "C"

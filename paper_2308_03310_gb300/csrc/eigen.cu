@@ -30,6 +30,8 @@
 //    finds A intact: reflectors live in the strictly lower triangle of the Gram slot.
 #include <float.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -696,68 +698,97 @@ __device__ __forceinline__ void store_vectors(const float *Z, int ld, float *out
 
 // ---- fused schedule -----------------------------------------------------------------------
 
+// The whole analysis of grid point lp of a (fused schedule) by one warp, in its slice W of
+// shared memory (smem_floats(a.k) floats).
 template <int NC>
-__global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB)
-    eigen_update_kernel(EigArgs a) {
-    extern __shared__ float smem[];
+__device__ __forceinline__ void analyze_point(const EigArgs &a, int lp, float *W, int lane) {
     const int k = a.k;
     const int ld = k + 1;
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
     // S holds Q during the tridiagonalization; its reflectors are then kept in the point's
     // Gram slot in global memory, and Z reuses S's shared memory.
-    float *S = smem + (size_t)wib * smem_floats(k);
+    float *S = W;
     float *Z = S;
     float *B = S + k * ld;
     float2 *vw = reinterpret_cast<float2 *>(B + kRows * ld);  // (v_t, w_t) of the reflection
     float2 *de = vw + k;                    // tridiagonal (d_t, e_t), e_t couples t and t+1
     float *taus = reinterpret_cast<float *>(de + k);  // reflector scalars
     float *vtmp = taus + k;                 // one reflector, back in shared memory
+    if (a.nloc && a.nloc[lp] == 0) {  // no local observation: Q = (k-1)/rho I, X^a = X^f
+        if (a.eigval)
+            for (int t = lane; t < k; t += 32) a.eigval[(size_t)lp * k + t] = a.diag;
+        return;
+    }
+    float *Ag = a.gram + (size_t)lp * k * k;
+    load_q<NC>(Ag, S, k, ld, lane, a.diag);
+    float xbar[NV];
+    float *X = a.x ? load_forecast<NC>(a, lp, B, k, ld, lane, xbar) : nullptr;
+    tridiagonalize<NC>(Ag, S, vw, de, taus, k, ld, lane);
+    set_identity<NC>(Z, k, ld, lane);
+    const bool notconv = ql_warp<NC>(de, Z, k, ld, lane);
+    if (notconv && lane == 0) atomicOr(a.status, ST_NOTCONV);
+    __syncwarp();
+    float dr[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int t = lane + 32 * c;
+        dr[c] = t < k ? de[t].x : 1.0f;
+    }
+    back_transform<NC>(Ag, Z, taus, vtmp, k, ld, lane);
+    if (a.refine) refine_clusters<NC>(Z, ld, Ag, a.diag, k, dr, lane, a.refine_tau);
+    if (a.evec) store_vectors<NC>(Z, ld, a.evec + (size_t)lp * k * k, k, lane);
+    if (a.eigval)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int t = lane + 32 * c;
+            if (t < k) a.eigval[(size_t)lp * k + t] = dr[c];
+        }
+    if (X) {
+        transform_update<NC>(X, B, Z, dr, xbar, k, ld, lane, a.status);
+    } else {  // eigenpairs only: report non-finite eigenvalues
+        bool bad = false;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) bad |= lane + 32 * c < k && !isfinite(dr[c]);
+        if (__any_sync(kFull, bad) && lane == 0) atomicOr(a.status, ST_NONFINITE);
+    }
+    __syncwarp();
+}
 
+template <int NC>
+__global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB)
+    eigen_update_kernel(EigArgs a) {
+    extern __shared__ float smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    float *W = smem + (size_t)wib * smem_floats(a.k);
     const int warps_per_block = blockDim.x >> 5;
     const int nw = gridDim.x * warps_per_block;
     // the whole chunk, or only the points of a list (matrices the split schedule hands back)
     const int n = a.list ? *a.list_count : a.npts;
+    for (int it = blockIdx.x * warps_per_block + wib; it < n; it += nw)
+        analyze_point<NC>(a, a.list ? a.list[it] : it, W, lane);
+}
 
-    for (int it = blockIdx.x * warps_per_block + wib; it < n; it += nw) {
-        const int lp = a.list ? a.list[it] : it;
-        if (a.nloc && a.nloc[lp] == 0) {  // no local observation: Q = (k-1)/rho I, X^a = X^f
-            if (a.eigval)
-                for (int t = lane; t < k; t += 32) a.eigval[(size_t)lp * k + t] = a.diag;
-            continue;
-        }
-        float *Ag = a.gram + (size_t)lp * k * k;
-        load_q<NC>(Ag, S, k, ld, lane, a.diag);
-        float xbar[NV];
-        float *X = a.x ? load_forecast<NC>(a, lp, B, k, ld, lane, xbar) : nullptr;
-        tridiagonalize<NC>(Ag, S, vw, de, taus, k, ld, lane);
-        set_identity<NC>(Z, k, ld, lane);
-        const bool notconv = ql_warp<NC>(de, Z, k, ld, lane);
-        if (notconv && lane == 0) atomicOr(a.status, ST_NOTCONV);
-        __syncwarp();
-        float dr[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            const int t = lane + 32 * c;
-            dr[c] = t < k ? de[t].x : 1.0f;
-        }
-        back_transform<NC>(Ag, Z, taus, vtmp, k, ld, lane);
-        if (a.refine) refine_clusters<NC>(Z, ld, Ag, a.diag, k, dr, lane, a.refine_tau);
-        if (a.evec) store_vectors<NC>(Z, ld, a.evec + (size_t)lp * k * k, k, lane);
-        if (a.eigval)
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const int t = lane + 32 * c;
-                if (t < k) a.eigval[(size_t)lp * k + t] = dr[c];
-            }
-        if (X) {
-            transform_update<NC>(X, B, Z, dr, xbar, k, ld, lane, a.status);
-        } else {  // eigenpairs only: report non-finite eigenvalues
-            bool bad = false;
-#pragma unroll
-            for (int c = 0; c < NC; ++c) bad |= lane + 32 * c < k && !isfinite(dr[c]);
-            if (__any_sync(kFull, bad) && lane == 0) atomicOr(a.status, ST_NONFINITE);
-        }
+// ---- grouped schedule: several ensembles' grid points in one persistent launch -------------
+
+// One launch over the points of up to kMaxGroupSeg segments (chunks of different handles,
+// any k of this NC class): every warp takes the next point from a global counter, so grid
+// points with many, few or no local observations and matrices of different order spread
+// over the warps as they free up.  Segments are ordered by decreasing k (largest jobs first).
+template <int NC>
+__global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB)
+    eigen_group_kernel(const __grid_constant__ EigGroup g) {
+    extern __shared__ float smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    float *W = smem + (size_t)wib * smem_floats(g.kmax);
+    for (;;) {
+        int i = 0;
+        if (lane == 0) i = atomicAdd(g.counter, 1);
+        i = __shfl_sync(kFull, i, 0);
+        if (i >= g.start[g.n]) break;
+        int sg = 0;
+        while (i >= g.start[sg + 1]) ++sg;
+        analyze_point<NC>(g.seg[sg], i - g.start[sg], W, lane);
     }
 }
 
@@ -1125,6 +1156,66 @@ cudaError_t launch_eigen_update(const EigArgs &a, cudaStream_t s) {
     if (a.k <= 64) return launch_nc<2>(a, s);
     if (a.k <= 128) return launch_nc<4>(a, s);
     return cudaErrorInvalidValue;
+}
+
+template <int NC>
+cudaError_t launch_group_nc(EigGroup &g, int max_blocks, cudaStream_t s) {
+    const int warps = EigCfg<NC>::WARPS;
+    const size_t smem = (size_t)smem_floats(g.kmax) * sizeof(float) * warps;
+    cudaError_t e = cudaMemsetAsync(g.counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    eigen_group_kernel<NC><<<grid_for(max_blocks, g.start[g.n], warps), 32 * warps, smem, s>>>(g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eigen_group(const EigArgs *segs, int n, int *counters, const int *max_blocks,
+                               cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (n > kMaxGroupSeg * 3) return cudaErrorInvalidValue;
+    // one launch per column class, segments by decreasing k
+    for (int cls = 0; cls < 3; ++cls) {
+        const int lo = cls == 0 ? 2 : (cls == 1 ? 33 : 65), hi = 32 << cls;
+        EigGroup g;
+        g.n = 0;
+        g.kmax = 0;
+        g.start[0] = 0;
+        g.counter = counters + cls;
+        int order[kMaxGroupSeg * 3], m = 0;
+        for (int i = 0; i < n; ++i)
+            if (segs[i].k >= lo && segs[i].k <= hi && segs[i].npts > 0) order[m++] = i;
+        if (m == 0) continue;
+        if (m > kMaxGroupSeg) return cudaErrorInvalidValue;
+        std::sort(order, order + m, [&](int x, int y) { return segs[x].k > segs[y].k; });
+        for (int j = 0; j < m; ++j) {
+            g.seg[j] = segs[order[j]];
+            g.kmax = std::max(g.kmax, g.seg[j].k);
+            g.start[j + 1] = g.start[j] + g.seg[j].npts;
+        }
+        g.n = m;
+        const cudaError_t e = cls == 0 ? launch_group_nc<1>(g, max_blocks[0], s)
+                            : cls == 1 ? launch_group_nc<2>(g, max_blocks[1], s)
+                                       : launch_group_nc<4>(g, max_blocks[2], s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t eigen_group_prepare(int *max_blocks) {
+    cudaError_t e = occupancy<1>((const void *)eigen_group_kernel<1>, EigCfg<1>::WARPS,
+                                 (size_t)smem_floats(32) * sizeof(float) * EigCfg<1>::WARPS,
+                                 (size_t)smem_floats(32) * sizeof(float) * EigCfg<1>::WARPS,
+                                 &max_blocks[0]);
+    if (e == cudaSuccess)
+        e = occupancy<2>((const void *)eigen_group_kernel<2>, EigCfg<2>::WARPS,
+                         (size_t)smem_floats(64) * sizeof(float) * EigCfg<2>::WARPS,
+                         (size_t)smem_floats(64) * sizeof(float) * EigCfg<2>::WARPS,
+                         &max_blocks[1]);
+    if (e == cudaSuccess)
+        e = occupancy<4>((const void *)eigen_group_kernel<4>, EigCfg<4>::WARPS,
+                         (size_t)smem_floats(128) * sizeof(float) * EigCfg<4>::WARPS,
+                         (size_t)smem_floats(128) * sizeof(float) * EigCfg<4>::WARPS,
+                         &max_blocks[2]);
+    return e;
 }
 
 cudaError_t launch_eigen_synthetic(const EigArgs &a, uint32_t seed, cudaStream_t s) {

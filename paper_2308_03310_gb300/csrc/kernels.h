@@ -114,6 +114,20 @@ struct EigSplit {
     int rcap = 0;                   // record capacity per point (entries)
     int grid_tri = 0, grid_vec = 0; // resident grids (eigen_split_prepare)
 };
+// Grouped schedule: the points of several chunks (segments) of any k, one persistent launch
+// per column class (k <= 32, <= 64, <= 128) with dynamic work distribution.
+constexpr int kMaxGroupSeg = 8;  // segments per column class and launch
+struct EigGroup {
+    int n;                       // segments
+    int kmax;                    // largest k among them: each warp's shared-memory slice
+    int start[kMaxGroupSeg + 1]; // prefix of the segments' point counts
+    int *counter;                // zeroed before the launch
+    EigArgs seg[kMaxGroupSeg];
+};
+cudaError_t eigen_group_prepare(int *max_blocks);  // max_blocks[3], once per process
+// segs: up to 3 kMaxGroupSeg chunks; counters: 3 device ints; max_blocks from the prepare
+cudaError_t launch_eigen_group(const EigArgs *segs, int n, int *counters, const int *max_blocks,
+                               cudaStream_t s);
 cudaError_t eigen_prepare(int k, int *max_blocks);  // once per process and k
 cudaError_t eigen_split_prepare(int k, EigSplit *sp);
 cudaError_t launch_eigen_update(const EigArgs &a, cudaStream_t s);

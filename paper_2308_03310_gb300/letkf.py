@@ -46,7 +46,8 @@ EXPORTED = (
     "letkf_get_stats", "letkf_enable_timing", "letkf_get_timings", "letkf_set_state", "letkf_get_state", "letkf_set_deviation",
     "letkf_get_deviation", "letkf_set_macro", "lbm_forecast",
     "letkf_get_obs", "letkf_analyze", "letkf_analyze_probe", "letkf_cycle",
-    "letkf_local_analysis_noalloc", "letkf_eigh_batch",
+    "letkf_local_analysis_noalloc", "letkf_eigh_batch", "letkf_group_analyze",
+    "letkf_group_cycle",
 )
 
 LETKF_NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -127,6 +128,8 @@ def load(path: str = LIB):
         "letkf_local_analysis_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, P, P,
                                                    C.c_float, P, P]),
         "letkf_eigh_batch": (C.c_int, [C.c_int32, C.c_int32, P, P, P, C.c_int32, P]),
+        "letkf_group_analyze": (C.c_int, [P, P, C.c_int32, C.c_int32]),
+        "letkf_group_cycle": (C.c_int, [P, C.c_int32, C.c_int32, P, C.c_int32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -242,6 +245,33 @@ def letkf_eigh_batch(npts, k, q_ptr, eigval_ptr, evec_ptr, refine, stream):
     return load().letkf_eigh_batch(int(npts), int(k), C.c_void_p(q_ptr), C.c_void_p(eigval_ptr),
                                    C.c_void_p(evec_ptr or None), int(refine),
                                    C.c_void_p(stream))
+
+
+def _group_arrays(exps, yos):
+    hs = (C.c_void_p * len(exps))(*[e.h for e in exps])
+    wheres, ptrs, keep = set(), [], []
+    for y in yos:
+        y = _f32(y) if isinstance(y, np.ndarray) else y
+        keep.append(y)
+        ptr, where = _ptr_where(y)
+        ptrs.append(ptr)
+        wheres.add(where)
+    if len(wheres) > 1:
+        raise ValueError("observations of a group must all be on the host or all on the device")
+    where = wheres.pop() if wheres else LETKF_HOST
+    return hs, (C.c_void_p * len(ptrs))(*ptrs), where, keep
+
+
+def letkf_group_analyze(exps, yos):
+    """One grouped analysis of the Experiments `exps` with observations `yos` (see letkf.h)."""
+    hs, ys, where, keep = _group_arrays(exps, yos)
+    _check(load().letkf_group_analyze(hs, ys, len(exps), where), "letkf_group_analyze")
+
+
+def letkf_group_cycle(exps, nsteps, yos):
+    """One grouped cycle (forecasts + grouped analysis), replayed from a CUDA graph."""
+    hs, ys, where, keep = _group_arrays(exps, yos)
+    _check(load().letkf_group_cycle(hs, len(exps), int(nsteps), ys, where), "letkf_group_cycle")
 
 
 # ---------------------------------------------------------------- marshalling helpers
