@@ -462,6 +462,8 @@ def main(argv=None):
 
     if args.workload == "serve_cfg5":
         return serve_main(args, device, rank, world)
+    if args.workload == "group_cfg4":
+        return group_main(args, device, rank, world)
     w = synth.WORKLOADS[args.workload]
     steps = args.steps if args.steps is not None else DEFAULT_STEPS.get(args.workload, 20)
     warm = max(3, args.warmup)
@@ -501,6 +503,122 @@ def main(argv=None):
         except Exception as e:  # the GPU number stands; say why the baseline is missing
             line["cpu_baseline"] = {"value": None, "unit": UNIT, "kind": "oracle",
                                     "error": str(e)[-300:]}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def group_main(args, device, rank, world):
+    """Uneven batching: four co-resident ensembles (k = 16, 32, 64, 128) on a 512 x 512 grid with
+    a clustered observation network (every 2nd point over a quarter of the domain, every 16th
+    point elsewhere, a band of rows without observations so that ~20 % of the points have no
+    local observation; r = 4).  Timed: graph-captured grouped cycles (forecast of all four +
+    one grouped analysis) against the same four ensembles cycled one after another with their
+    own letkf_cycle.  value = grid-point analyses per second over the four ensembles."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2308_03310_gb300 import letkf as L
+
+    nx = ny = 512
+    ks = (16, 32, 64, 128)
+    r = 4.0
+    cut = float(np.sqrt(synth.loc_cutoff2(r)))
+    band = int(0.2 * ny + 2 * cut + 1)
+    net = synth.clustered_obs_network(nx, ny, 2, 16, patch=(0, 0, nx // 2, ny // 2),
+                                      empty_band=(ny // 2 + 64, band))
+    LV = len(net) * 2
+    sigma = 0.01
+    var = np.full(LV, sigma * sigma, dtype=np.float32)
+    steps_cycle = 25
+    steps = args.steps if args.steps is not None else 10
+    warm = max(3, args.warmup)
+    tx, ty = synth.band_limited_force(nx, ny, 2.0, 5.0, 0.02, 41)
+    out = {}
+    for name, prec in (("fp32", L.LETKF_FP32), ("mixed", L.LETKF_MIXED)):
+        exps, yos = [], []
+        for i, k in enumerate(ks):
+            e = L.Experiment(nx, ny, k, 0.55, net, var, loc_radius=r, precision=prec,
+                             device=device)
+            ux = np.empty((k, ny, nx), np.float32)
+            uy = np.empty((k, ny, nx), np.float32)
+            for m in range(k):
+                px, py = synth.band_limited_force(nx, ny, 2.0, 5.0, 0.005, 1000 * i + m)
+                ux[m], uy[m] = tx + px, ty + py
+            e.set_macro(np.ones((k, ny, nx), np.float32), ux, uy)
+            exps.append(e)
+        st = exps[0].stats()
+        # observations: the truth field observed with noise, one draw per cycle
+        truth_u = np.stack([tx, ty])
+        xs, ys = net[:, 0], net[:, 1]
+        ytrue = np.stack([truth_u[0][ys, xs], truth_u[1][ys, xs]], axis=1).reshape(-1)
+        obs = [torch.from_numpy((ytrue + synth.gaussian(LV, sigma, 77 + c)).astype(np.float32))
+               .to(device) for c in range(warm + steps)]
+        stream = exps[0].stream
+
+        def timed(run_cycle):
+            for c in range(warm):
+                run_cycle(c)
+            torch.cuda.synchronize(device)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+            cyc = []
+            for c in range(steps):
+                ev[c].record(stream)
+                run_cycle(warm + c)
+                ev[c + 1].record(stream)
+                torch.cuda.synchronize(device)
+                cyc.append(ev[c].elapsed_time(ev[c + 1]))
+            return cyc
+
+        def group_cycle(c):
+            L.letkf_group_cycle(exps, steps_cycle, [obs[c]] * len(exps))
+
+        def separate_cycles(c):
+            for e in exps:
+                e.cycle(steps_cycle, obs[c])
+            # the timing events sit on the first handle's stream: join the others
+            for e in exps[1:]:
+                done = torch.cuda.Event()
+                done.record(e.stream)
+                stream.wait_event(done)
+
+        g = timed(group_cycle)
+        sep = timed(separate_cycles)
+        for e in exps:
+            rc = e.sync()
+            if rc:
+                raise RuntimeError(f"group cycle failed: {L.strerror(rc)}")
+        pts = nx * ny * len(ks)
+        out[name] = {
+            "value": pts * len(g) / (sum(g) / 1e3),
+            "ms_per_cycle": statistics.mean(g),
+            "p50_cycle_ms": float(np.percentile(g, 50)),
+            "p99_cycle_ms": float(np.percentile(g, 99)),
+            "separate_value": pts * len(sep) / (sum(sep) / 1e3),
+            "separate_ms_per_cycle": statistics.mean(sep),
+            "zero_obs_fraction": st.n_zero_obs / st.n_points,
+            "max_local_obs": st.max_local_obs, "mean_local_obs": st.mean_local_obs,
+        }
+        for e in exps:
+            e.close()
+        del exps, obs
+        torch.cuda.empty_cache()
+    head = out["fp32"]
+    line = {
+        "metric": METRIC, "value": reduce_sum(head["value"], device), "unit": UNIT,
+        "n_gpus": world, "steps": steps, "warmup": warm, "ms_per_step": head["ms_per_cycle"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "group_cfg4", "grid": "512x512", "k": list(ks),
+                   "network": "clustered: every 2nd point over 25 % of the domain, every 16th "
+                              "elsewhere, an observation-free band", "loc_radius": r,
+                   "steps_per_cycle": steps_cycle, "precision": "fp32",
+                   "parallelism": "one grouped launch per column class"},
+        "p50_cycle_ms": head["p50_cycle_ms"], "p99_cycle_ms": head["p99_cycle_ms"],
+        "group": head, "mixed": dict(out["mixed"],
+                                     speedup_vs_fp32=out["mixed"]["value"] / head["value"]),
+    }
     if rank == 0:
         print(json.dumps(line))
     return 0
