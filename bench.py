@@ -56,6 +56,8 @@ def parse_args(argv=None):
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="turb256_k32")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--eig-schedule", choices=sorted(EIG_SCHEDULES), default="auto",
+                   help="eigensolve schedule (auto: the handle's autotuner picks)")
     p.add_argument("--cpu-sample-seconds", type=float, default=12.0)
     p.add_argument("--precision", choices=["fp32", "mixed", "both"], default="both",
                    help="fp32: the plain form only; mixed: the split-precision form only; "
@@ -202,6 +204,8 @@ def measured_peaks():
             "source": "fallback"}
 
 
+EIG_SCHEDULES = {"auto": 0, "fused": 1, "split": 2}
+EIG_NAMES = {1: "fused", 2: "split", 3: "split_check"}
 PEAK_NAMES = {"hbm": "hbm_gbs", "alu": "FP32 FMA at max SM clock",
               "tensor": "bf16_tflops_sustained (FP16 operands, same nominal rate)"}
 
@@ -214,13 +218,28 @@ def fp32_peak_tflops(sm_mhz: float) -> float:
 def kernel_work(w, k, npts, mean_local_obs, V, nobs_pts, chunks, steps):
     """Algorithmic work of one cycle per kernel: (unit, amount, launches)."""
     return {
-        "lbm_step": ("GB", (72.0 * npts * k + 8.0 * npts) * steps / 1e9, steps),
+        # two steps per launch: one read and one write of the state (+ the force) per launch
+        "lbm_step": ("GB", (72.0 * npts * k + 8.0 * npts) * (steps // 2 + steps % 2) / 1e9,
+                     steps // 2 + steps % 2),
         "obs_operator": ("GB", (36.0 + 8.0 * V) * nobs_pts * k / 1e9, 1),
         "transpose_in": ("GB", 72.0 * k * npts / 1e9, 1),
         "gram": ("TFLOP", 2.0 * k * k * V * mean_local_obs * npts / 1e12, chunks),
         "eigen_update": ("TFLOP", 11.0 * k ** 3 * npts / 1e12, chunks),
         "transpose_out": ("GB", 72.0 * k * npts / 1e9, 1),
     }
+
+
+def lbm_rates(w, forecast_ms, peaks):
+    """D2Q9 throughput of the forecast: million lattice updates per second (all members and
+    per member), and the HBM rate a kernel taking one step per launch would need for it
+    (72 B per update + the force), as a fraction of the measured copy bandwidth: above 1 only
+    with temporal blocking."""
+    updates = float(w.n_points) * w.k * w.steps_per_cycle
+    mlups = updates / (forecast_ms * 1e-3) / 1e6
+    eq_gbs = (72.0 * updates + 8.0 * w.n_points * w.steps_per_cycle) / (forecast_ms * 1e-3) / 1e9
+    return {"mlups": mlups, "mlups_per_member": mlups / w.k, "steps_per_launch": 2,
+            "single_step_equivalent_gbs": eq_gbs,
+            "single_step_equivalent_frac": eq_gbs / peaks["hbm_gbs"]}
 
 
 def roofline_table(work, ms, peaks, sm_mhz, tensor_gram=False):
@@ -303,13 +322,14 @@ def spin_up(w, device):
     return spin, members, (net, var, kw)
 
 
-def make_experiment(w, members, setup, device, precision):
+def make_experiment(w, members, setup, device, precision, eig_schedule=0):
     """A fresh experiment of the workload starting from the spun-up members."""
     import torch
 
     from paper_2308_03310_gb300 import letkf as L
     net, var, kw = setup
-    exp = L.Experiment(w.nx, w.ny, w.k, w.tau, net, var, device=device, precision=precision, **kw)
+    exp = L.Experiment(w.nx, w.ny, w.k, w.tau, net, var, device=device, precision=precision,
+                       eig_schedule=eig_schedule, **kw)
     torch.cuda.synchronize(device)
     L.letkf_set_deviation(exp.h, members.data_ptr(), 0, w.k, L.LETKF_DEVICE)
     assert exp.sync() == 0
@@ -472,7 +492,8 @@ def main(argv=None):
     spin.close()
     forms = {"fp32": [L.LETKF_FP32], "mixed": [L.LETKF_MIXED],
              "both": [L.LETKF_FP32, L.LETKF_MIXED]}[args.precision]
-    results = [measure(w, members, setup, yos, device, prec, steps, warm, world)
+    sched = EIG_SCHEDULES[args.eig_schedule]
+    results = [measure(w, members, setup, yos, device, prec, steps, warm, world, sched)
                for prec in forms]
     head = results[0]
     line = {
@@ -482,14 +503,17 @@ def main(argv=None):
         "config": workload_config(w, head["precision"]),
         "p50_cycle_ms": head["p50_cycle_ms"], "p99_cycle_ms": head["p99_cycle_ms"],
         "roofline": head["roofline"], "kernels": head["kernels"], "e2e": head["e2e"],
-        "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
+        "gpu_launches": head["gpu_launches"], "eig_schedule": head["eig_schedule"],
+        "lbm": head["lbm"],
+        "clocks": head["clocks"],
         "local_obs": head["local_obs"],
         "mixed": None,
     }
     if len(results) > 1:
         mx = results[1]
         line["mixed"] = {k: mx[k] for k in ("precision", "value", "ms_per_step", "p50_cycle_ms",
-                                             "p99_cycle_ms", "e2e", "gpu_launches", "clocks")}
+                                             "p99_cycle_ms", "e2e", "gpu_launches", "eig_schedule",
+                                             "clocks")}
         line["mixed"]["kernels"] = {n: {"ms_per_cycle": d["ms_per_cycle"], "frac": d["frac"],
                                          "unit": d["unit"]} for n, d in mx["kernels"].items()}
         line["mixed"]["speedup_vs_fp32"] = mx["value"] / head["value"]
@@ -688,7 +712,7 @@ def serve_main(args, device, rank, world):
     return 0
 
 
-def measure(w, members, setup, yos, device, precision, steps, warm, world):
+def measure(w, members, setup, yos, device, precision, steps, warm, world, eig_schedule=0):
     """Time `steps` cycles of one precision form (device-resident inputs), then the same
     through the public API with host buffers."""
     import numpy as np
@@ -696,7 +720,7 @@ def measure(w, members, setup, yos, device, precision, steps, warm, world):
 
     from paper_2308_03310_gb300 import letkf as L
 
-    exp = make_experiment(w, members, setup, device, precision)
+    exp = make_experiment(w, members, setup, device, precision, eig_schedule)
     st = exp.stats()
     LV = exp.L * exp.V
     stream = exp.stream
@@ -783,6 +807,8 @@ def measure(w, members, setup, yos, device, precision, steps, warm, world):
     rc = exp.sync()
     if rc:
         raise RuntimeError(f"end-to-end cycles failed: {L.strerror(rc)}")
+    st_end = exp.stats()                           # schedule resolved at the first analysis
+    cycle_kernels = st_end.cycle_kernels            # kernel nodes of the cycle's graph
     exp.close()
     del flush
     return {
@@ -795,7 +821,9 @@ def measure(w, members, setup, yos, device, precision, steps, warm, world):
                         for kk, vv in d.items()} for n, d in table.items()},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": LV * 4,
                 "d2h_bytes_per_step": exp.nmem * LV * 4},
-        "gpu_launches": (w.steps_per_cycle + 3 + 2 * st.n_chunks) * steps,
+        "gpu_launches": cycle_kernels * steps,
+        "eig_schedule": EIG_NAMES.get(st_end.eig_schedule, str(st_end.eig_schedule)),
+        "lbm": lbm_rates(w, ms["lbm_step"], peaks),
         "clocks": clocks,
         "local_obs": {"mean": st.mean_local_obs, "max": st.max_local_obs,
                       "zero_fraction": st.n_zero_obs / st.n_points},

@@ -58,7 +58,14 @@ extern "C" {
                                   accumulation); for k <= 32 it stays on CUDA cores         */
 
 /* Eigensolve schedules (same results up to rounding; see letkf_config.eig_schedule). */
-#define LETKF_EIG_AUTO        0  /* the handle picks one                                     */
+#define LETKF_EIG_AUTO        0  /* the handle picks one: at its first analysis both schedules
+                                    are timed on that analysis' first chunk of Gram matrices
+                                    (applied to a scratch copy of the forecast, so the analysis
+                                    itself is unaffected; one host synchronisation), and the
+                                    faster is kept.  The pick is cached per (device, k, chunk
+                                    size) for the process: later handles of that shape take it
+                                    at letkf_init.  A letkf_cycle that must still pick runs
+                                    without graph capture; the next one captures.          */
 #define LETKF_EIG_FUSED       1  /* one warp per grid point runs every phase in one launch    */
 #define LETKF_EIG_SPLIT       2  /* tridiagonalization (warp per point), QL (thread per point,
                                     rotations recorded), replay + update (warp per point)    */
@@ -104,10 +111,13 @@ typedef struct letkf_stats {
     int32_t max_local_obs;     /* l_max: most observation points local to one point     */
     double  mean_local_obs;    /* average observation points per grid point             */
     int32_t n_chunks;          /* Gram/eigensolve launch pairs per analysis             */
-    int32_t eig_schedule;      /* LETKF_EIG_FUSED / SPLIT / SPLIT_CHECK in use (AUTO
-                                  resolved at letkf_init)                               */
+    int32_t eig_schedule;      /* LETKF_EIG_FUSED / SPLIT / SPLIT_CHECK in use; AUTO (0)
+                                  until the first analysis resolves it                   */
     int32_t cuda_error;        /* first cudaError_t that made a call of this handle
                                   return LETKF_ECUDA or LETKF_ENOMEM; 0 = none           */
+    int32_t cycle_kernels;     /* kernel launches of the most recent letkf_cycle (or group
+                                  cycle led by this handle): the kernel nodes of its
+                                  captured graph; 0 before the first cycle               */
 } letkf_stats;
 
 /* Device time of the phases of the most recent forecast and analysis (milliseconds, CUDA

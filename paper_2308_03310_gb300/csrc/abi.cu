@@ -205,11 +205,13 @@ struct letkf_handle {
     letkf_stats stats;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int graph_nsteps[2] = {-1, -1};
+    int graph_kernels[2] = {0, 0};  // kernel nodes of each captured cycle
     unsigned long long serial = 0;  // unique per handle of the process (group graph keys)
     struct GroupGraph {             // captured group cycles led by this handle
         std::vector<unsigned long long> members;
         std::vector<int> cur;
         int nsteps = -1;
+        int kernels = 0;
         cudaGraphExec_t exec = nullptr;
     };
     std::vector<GroupGraph> group_graphs;
@@ -222,6 +224,21 @@ struct letkf_handle {
 };
 
 namespace {
+
+// Kernel nodes of a captured graph (the launches one replay makes).
+int graph_kernel_nodes(cudaGraph_t g) {
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) return 0;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return 0;
+    int kernels = 0;
+    for (size_t i = 0; i < n; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+            ++kernels;
+    }
+    return kernels;
+}
 
 int cuda_fail(letkf_handle *h, cudaError_t e) {
     if (e == cudaSuccess) return LETKF_OK;
@@ -279,11 +296,19 @@ int mark(letkf_handle *h, int idx) {
     return LETKF_OK;
 }
 
+// Ping-pong buffer flips of a forecast: two steps per launch, a single step for an odd rest.
+int forecast_flips(int nsteps) { return nsteps / 2 + (nsteps & 1); }
+
 int enqueue_forecast(letkf_handle *h, int nsteps) {
     const Plan &p = h->plan;
     int rc = mark(h, 0);
     if (rc) return rc;
-    for (int s = 0; s < nsteps; ++s) {
+    for (int s = 0; s + 2 <= nsteps; s += 2) {
+        CK(lk::launch_lbm_2step(h->state[h->cur], h->state[h->cur ^ 1], h->force, h->cfg.nx,
+                                h->cfg.ny, p.nmem, h->cfg.tau, h->stream));
+        h->cur ^= 1;
+    }
+    if (nsteps & 1) {
         CK(lk::launch_lbm_step(h->state[h->cur], h->state[h->cur ^ 1], h->force, h->cfg.nx,
                                h->cfg.ny, p.nmem, h->cfg.tau, h->stream));
         h->cur ^= 1;
@@ -363,6 +388,89 @@ lk::EigArgs eig_args(letkf_handle *h, int y0, int y1) {
     return e;
 }
 
+// ---- AUTO eigensolve schedule ----------------------------------------------------------
+// Both schedules are timed on the handle's first analysis, on the Gram matrices of its first
+// chunk (at most 16384 points), just before that chunk's eigensolve: each runs the full
+// eigensolve, transform and update, applied to a scratch copy of the chunk's forecast
+// perturbations in the state buffer the next forecast overwrites.  The Gram matrices' upper
+// triangles, c and the local counts are left intact by both, so the analysis proper then runs
+// on unchanged inputs with the faster schedule.  The choice is cached per (device, k, batch)
+// for the life of the process: later handles of that shape take it at letkf_init, so every
+// handle of a process with the same k and chunk size runs the same arithmetic.
+
+struct EigTuneCache {
+    std::mutex mu;
+    std::map<std::pair<int, std::pair<int, int>>, int> pick;
+};
+
+EigTuneCache &eig_tune_cache() {
+    static EigTuneCache c;
+    return c;
+}
+
+std::pair<int, std::pair<int, int>> eig_tune_key(const letkf_handle *h) {
+    const int batch = (int)std::min<size_t>(h->plan.chunk_pts, 16384);
+    return std::make_pair(h->device, std::make_pair(h->cfg.k, batch));
+}
+
+int cached_eig_schedule(const letkf_handle *h) {
+    EigTuneCache &c = eig_tune_cache();
+    std::lock_guard<std::mutex> lock(c.mu);
+    const auto it = c.pick.find(eig_tune_key(h));
+    return it == c.pick.end() ? LETKF_EIG_AUTO : it->second;
+}
+
+int tune_eig_schedule(letkf_handle *h, int y0, int y1) {
+    const int cached = cached_eig_schedule(h);
+    if (cached != LETKF_EIG_AUTO) {
+        h->eig_schedule = h->stats.eig_schedule = cached;
+        return LETKF_OK;
+    }
+    const int k = h->cfg.k;
+    lk::EigArgs e = eig_args(h, y0, y1);
+    e.npts = std::min(e.npts, 16384);
+    float *scratch = h->state[h->cur ^ 1];  // >= k * 9 * npts floats, free until the forecast
+    const size_t xbytes = (size_t)e.npts * 9 * k * sizeof(float);
+    CK(cudaMemcpyAsync(scratch, h->xg + (size_t)e.pt0 * 9 * k, xbytes,
+                       cudaMemcpyDeviceToDevice, h->stream));
+    e.x = scratch;
+    e.pt0 = 0;
+    int saved = 0;                          // status word: the timed runs must not latch
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaMemcpy(&saved, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    float best[2] = {0.0f, 0.0f};
+    cudaError_t err = cudaEventCreate(&t0);
+    if (err == cudaSuccess) err = cudaEventCreate(&t1);
+    for (int sch = 0; sch < 2 && err == cudaSuccess; ++sch) {
+        for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
+            err = cudaEventRecord(t0, h->stream);
+            if (err == cudaSuccess)
+                err = sch == 0 ? lk::launch_eigen_update(e, h->stream)
+                               : lk::launch_eigen_split(e, h->eig_split, h->stream);
+            if (err == cudaSuccess) err = cudaEventRecord(t1, h->stream);
+            if (err == cudaSuccess) err = cudaEventSynchronize(t1);
+            float ms = 0.0f;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, t0, t1);
+            if (rep > 0 && (rep == 1 || ms < best[sch])) best[sch] = ms;  // run 0 warms up
+        }
+    }
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(h->status, &saved, sizeof(int), cudaMemcpyHostToDevice, h->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
+    if (err != cudaSuccess) return cuda_fail(h, err);
+    const int pick = best[1] < best[0] ? LETKF_EIG_SPLIT : LETKF_EIG_FUSED;
+    {
+        EigTuneCache &c = eig_tune_cache();
+        std::lock_guard<std::mutex> lock(c.mu);
+        h->eig_schedule = c.pick.emplace(eig_tune_key(h), pick).first->second;  // first wins
+    }
+    h->stats.eig_schedule = h->eig_schedule;
+    return LETKF_OK;
+}
+
 int enqueue_analysis(letkf_handle *h, letkf_probe *probe) {
     const Plan &p = h->plan;
     const letkf_config &c = h->cfg;
@@ -402,6 +510,7 @@ int enqueue_analysis(letkf_handle *h, letkf_probe *probe) {
                                        h->stream));
             }
         }
+        if (h->eig_schedule == LETKF_EIG_AUTO && (rc = tune_eig_schedule(h, y0, y1))) return rc;
         lk::EigArgs e = eig_args(h, y0, y1);
         if (h->eig_schedule == LETKF_EIG_FUSED) {
             e.eigval = (probe && probe->eigval) ? h->eigval : nullptr;
@@ -587,64 +696,6 @@ int letkf_workspace_size(const letkf_config *cfg, size_t *bytes) {
     return LETKF_OK;
 }
 
-// AUTO eigensolve schedule: both schedules timed on synthetic matrices of this k (a chunk's
-// worth of points, at most 16384) on the handle's stream, the faster kept.  The choice is
-// cached per (device, k, batch) for the life of the process, so that every handle of a
-// process with the same k and chunk size runs the same arithmetic.
-int autotune_eig_schedule(letkf_handle *h, int *out) {
-    static std::mutex mu;
-    static std::map<std::pair<int, std::pair<int, int>>, int> cache;
-    const int k = h->cfg.k;
-    const int batch = (int)std::min<size_t>(h->plan.chunk_pts, 16384);
-    std::lock_guard<std::mutex> lock(mu);
-    const auto key = std::make_pair(h->device, std::make_pair(k, batch));
-    const auto it = cache.find(key);
-    if (it != cache.end()) {
-        *out = it->second;
-        return LETKF_OK;
-    }
-    lk::EigArgs e;
-    e.k = k;
-    e.diag = (float)(k - 1);
-    e.gram = h->gram;
-    e.cvec = h->cvec;
-    e.nloc = h->nloc;
-    e.x = h->xg;
-    e.pt0 = 0;
-    e.npts = batch;
-    e.eigval = h->eigval;
-    e.status = h->status;
-    e.max_blocks = h->eig_blocks;
-    cudaEvent_t t0 = nullptr, t1 = nullptr;
-    float best[2] = {0.0f, 0.0f};
-    cudaError_t err = cudaEventCreate(&t0);
-    if (err == cudaSuccess) err = cudaEventCreate(&t1);
-    // (both schedules leave A's upper triangle intact: the inputs serve every run)
-    if (err == cudaSuccess) err = lk::launch_eigen_synthetic(e, 0x2308u, h->stream);
-    for (int sch = 0; sch < 2 && err == cudaSuccess; ++sch) {
-        for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
-            err = cudaEventRecord(t0, h->stream);
-            if (err == cudaSuccess)
-                err = sch == 0 ? lk::launch_eigen_update(e, h->stream)
-                               : lk::launch_eigen_split(e, h->eig_split, h->stream);
-            if (err == cudaSuccess) err = cudaEventRecord(t1, h->stream);
-            if (err == cudaSuccess) err = cudaEventSynchronize(t1);
-            float ms = 0.0f;
-            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, t0, t1);
-            if (rep > 0 && (rep == 1 || ms < best[sch])) best[sch] = ms;  // run 0 warms up
-        }
-    }
-    if (t0) cudaEventDestroy(t0);
-    if (t1) cudaEventDestroy(t1);
-    if (err == cudaSuccess) err = cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
-    if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
-    if (err != cudaSuccess) return LETKF_ECUDA;
-    *out = best[1] < best[0] ? LETKF_EIG_SPLIT : LETKF_EIG_FUSED;
-    cache[key] = *out;
-    return LETKF_OK;
-}
-
-
 int letkf_init(const letkf_config *cfg, void *workspace, size_t workspace_bytes,
                letkf_handle **out) {
     if (!out) return LETKF_EINVAL;
@@ -763,7 +814,7 @@ int letkf_init(const letkf_config *cfg, void *workspace, size_t workspace_bytes,
     h->net.cr = plan.cr;
     h->net.inv2r2 = plan.inv2r2;
 
-    if (lk::gram_prepare(plan.kp) != cudaSuccess ||
+    if (lk::lbm_prepare() != cudaSuccess || lk::gram_prepare(plan.kp) != cudaSuccess ||
         lk::eigen_prepare(cfg->k, &h->eig_blocks) != cudaSuccess ||
         (plan.eig_schedule != LETKF_EIG_FUSED &&
          lk::eigen_split_prepare(cfg->k, &h->eig_split) != cudaSuccess))
@@ -801,12 +852,9 @@ int letkf_init(const letkf_config *cfg, void *workspace, size_t workspace_bytes,
     h->stats.max_local_obs = mx;
     h->stats.mean_local_obs = (double)sum / (double)npts;
     h->stats.n_chunks = n_chunks(h);
-    if (plan.eig_schedule == LETKF_EIG_AUTO) {
-        const int rc = autotune_eig_schedule(h, &h->eig_schedule);
-        if (rc) return fail(rc);
-    } else {
-        h->eig_schedule = plan.eig_schedule;
-    }
+    // AUTO: the process' earlier pick for this shape, else timed at the first analysis
+    h->eig_schedule =
+        plan.eig_schedule == LETKF_EIG_AUTO ? cached_eig_schedule(h) : plan.eig_schedule;
     h->stats.eig_schedule = h->eig_schedule;
     *out = h;
     return LETKF_OK;
@@ -1011,6 +1059,10 @@ int letkf_cycle(letkf_handle *h, int32_t nsteps, const float *yo, int32_t where)
     int rc = device_check(h);
     if (rc) return rc;
     if ((rc = copy_in(h, h->yo, yo, (size_t)h->plan.LV * sizeof(float), where))) return rc;
+    if (h->eig_schedule == LETKF_EIG_AUTO) {  // the first analysis times the schedules: eager
+        rc = enqueue_forecast(h, nsteps);
+        return rc ? rc : enqueue_analysis(h, nullptr);
+    }
     const int slot = h->cur;
     if (h->graph_nsteps[slot] != nsteps) {
         if (h->graph[slot]) {
@@ -1029,13 +1081,15 @@ int letkf_cycle(letkf_handle *h, int32_t nsteps, const float *yo, int32_t where)
             return rc;
         }
         if (ec != cudaSuccess) return cuda_fail(h, ec);
+        h->graph_kernels[slot] = graph_kernel_nodes(g);
         const cudaError_t ei = cudaGraphInstantiate(&h->graph[slot], g, 0);
         cudaGraphDestroy(g);
         if (ei != cudaSuccess) return cuda_fail(h, ei);
         h->graph_nsteps[slot] = nsteps;
     }
     CK(cudaGraphLaunch(h->graph[slot], h->stream));
-    h->cur ^= (nsteps & 1);
+    h->stats.cycle_kernels = h->graph_kernels[slot];
+    h->cur ^= (forecast_flips(nsteps) & 1);
     return LETKF_OK;
 }
 
@@ -1103,6 +1157,7 @@ int letkf_group_cycle(letkf_handle *const *hs, int32_t n, int32_t nsteps, const 
             e.members = ids;
             e.cur = cur;
             e.nsteps = nsteps;
+            e.kernels = graph_kernel_nodes(g);
             const cudaError_t ei = cudaGraphInstantiate(&e.exec, g, 0);
             cudaGraphDestroy(g);
             if (ei != cudaSuccess) return cuda_fail(h, ei);
@@ -1110,7 +1165,8 @@ int letkf_group_cycle(letkf_handle *const *hs, int32_t n, int32_t nsteps, const 
             gg = &h->group_graphs.back();
         }
         CK(cudaGraphLaunch(gg->exec, h->stream));
-        for (int i = 0; i < n; ++i) hs[i]->cur ^= (nsteps & 1);
+        h->stats.cycle_kernels = gg->kernels;
+        for (int i = 0; i < n; ++i) hs[i]->cur ^= (forecast_flips(nsteps) & 1);
     }
     return group_fence(hs, n, true);
 }

@@ -1012,44 +1012,6 @@ __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB)
     }
 }
 
-// Synthetic analysis inputs for timing the schedules: per point A = Y Y^T with Y (k x r),
-// r = min(2k, 12288/k), entries 0.7 u with u uniform in [-1/2, 1/2] from a counter-based
-// hash.  The spectrum of (k-1) I + A then needs about as many QL rotations (~0.9 k^2) as the
-// analyses of the forced-turbulence workloads do; c and the forecast block come from the same
-// hash, and every point gets one local observation so that none is skipped.
-__device__ __forceinline__ float hash_unit(uint32_t a, uint32_t b, uint32_t c) {
-    uint32_t h = a * 0x9E3779B1u ^ (b + 0x7F4A7C15u) * 0x85EBCA77u ^ (c + 0x165667B1u) * 0xC2B2AE3Du;
-    h ^= h >> 15;
-    h *= 0x2C1B3C6Du;
-    h ^= h >> 12;
-    h *= 0x297A2D39u;
-    h ^= h >> 15;
-    return (float)(h >> 8) * (1.0f / 16777216.0f) - 0.5f;
-}
-
-__host__ __device__ inline int synthetic_rank(int k) { return min(2 * k, 12288 / k); }
-
-__global__ void eig_synthetic_kernel(EigArgs a, uint32_t seed) {
-    extern __shared__ float ys[];  // [k][r] of this block's point
-    const int k = a.k, r = synthetic_rank(k);
-    const int lane = threadIdx.x;
-    const int w = blockIdx.x;
-    for (int e = lane; e < k * r; e += 32) ys[e] = 0.7f * hash_unit(seed + w, e / r, e % r);
-    __syncwarp();
-    float *Ag = a.gram + (size_t)w * k * k;
-    for (int i = 0; i < k; ++i)
-        for (int j = lane; j < k; j += 32) {
-            float s = 0.0f;
-            for (int q = 0; q < r; ++q) s = fmaf(ys[i * r + q], ys[j * r + q], s);
-            Ag[i * k + j] = s;
-        }
-    float *X = a.x + (size_t)(a.pt0 + w) * NV * k;
-    for (int t = lane; t < NV * k; t += 32) X[t] = 0.01f * hash_unit(seed ^ 0x5bd1e995u, w, t);
-    for (int t = lane; t < k; t += 32)
-        const_cast<float *>(a.cvec)[(size_t)w * k + t] = hash_unit(seed ^ 0x1b873593u, w, t);
-    if (lane == 0) const_cast<int *>(a.nloc)[w] = 1;
-}
-
 // The dynamic shared-memory cap of a kernel is a process-wide attribute shared by every
 // handle: it is set for the largest k the kernel's template serves (the shared memory grows
 // with k), never for one handle's k, so that no handle can lower it under another's launch.
@@ -1216,13 +1178,6 @@ cudaError_t eigen_group_prepare(int *max_blocks) {
                          (size_t)smem_floats(128) * sizeof(float) * EigCfg<4>::WARPS,
                          &max_blocks[2]);
     return e;
-}
-
-cudaError_t launch_eigen_synthetic(const EigArgs &a, uint32_t seed, cudaStream_t s) {
-    if (a.npts <= 0) return cudaSuccess;
-    const size_t smem = (size_t)a.k * synthetic_rank(a.k) * sizeof(float);  // <= 48 KiB
-    eig_synthetic_kernel<<<(unsigned)a.npts, 32, smem, s>>>(a, seed);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_eigen_split(const EigArgs &a, const EigSplit &sp, cudaStream_t s) {

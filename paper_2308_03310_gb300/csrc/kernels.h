@@ -31,6 +31,10 @@ struct ObsNet {
 // ---- lbm.cu -------------------------------------------------------------------
 cudaError_t launch_lbm_step(const float *gin, float *gout, const float2 *force, int nx, int ny,
                             int nmem, float tau, cudaStream_t s);
+// two steps in one launch (temporal blocking through shared memory); lbm_prepare once
+cudaError_t lbm_prepare();
+cudaError_t launch_lbm_2step(const float *gin, float *gout, const float2 *force, int nx, int ny,
+                             int nmem, float tau, cudaStream_t s);
 cudaError_t launch_f_to_g(const float *f, float *g, int nmem, size_t npts, cudaStream_t s);
 cudaError_t launch_g_to_f(const float *g, float *f, int nmem, size_t npts, cudaStream_t s);
 cudaError_t launch_macro_to_g(const float *rho, const float *ux, const float *uy, float *g,
@@ -132,8 +136,6 @@ cudaError_t eigen_prepare(int k, int *max_blocks);  // once per process and k
 cudaError_t eigen_split_prepare(int k, EigSplit *sp);
 cudaError_t launch_eigen_update(const EigArgs &a, cudaStream_t s);
 cudaError_t launch_eigen_split(const EigArgs &a, const EigSplit &sp, cudaStream_t s);
-// synthetic Gram matrices, c, forecast blocks and counts for timing the schedules
-cudaError_t launch_eigen_synthetic(const EigArgs &a, uint32_t seed, cudaStream_t s);
 size_t eigen_smem_per_warp(int k);
 
 }  // namespace lk

@@ -68,7 +68,8 @@ class letkf_config(C.Structure):
 class letkf_stats(C.Structure):
     _fields_ = [("status", C.c_int32), ("n_points", C.c_int32), ("n_zero_obs", C.c_int32),
                 ("max_local_obs", C.c_int32), ("mean_local_obs", C.c_double),
-                ("n_chunks", C.c_int32), ("eig_schedule", C.c_int32), ("cuda_error", C.c_int32)]
+                ("n_chunks", C.c_int32), ("eig_schedule", C.c_int32), ("cuda_error", C.c_int32),
+                ("cycle_kernels", C.c_int32)]
 
 
 class letkf_timings(C.Structure):

@@ -93,17 +93,52 @@ def test_split_schedule_is_reproducible():
     assert np.array_equal(runs[0], runs[1])
 
 
-def test_auto_schedule_resolves_once_per_process():
-    picks = []
-    for seed in (971, 972):
-        nx = ny = 12
-        net = synth.regular_obs_network(nx, ny, 3)
-        var = np.full(len(net) * 2, 1e-4, dtype=np.float32)
-        exp = L.Experiment(nx, ny, 48, 0.6, net, var, loc_radius=2.0)
-        picks.append(exp.stats().eig_schedule)
-        assert exp.sync() == 0
-    assert picks[0] in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT)
-    assert picks[0] == picks[1]
+def _auto_case(k, schedule, seed):
+    nx = ny = 12
+    net = synth.regular_obs_network(nx, ny, 3)
+    var = np.full(len(net) * 2, 1e-4, dtype=np.float32)
+    f0 = C.perturb_nonequilibrium(C.ensemble_state(k, nx, ny, seed=seed), 1e-4, seed + 1)
+    yo = C.observations(C.ensemble_state(1, nx, ny, seed=seed + 2), net, UV, 0.01, seed + 3)[0]
+    exp = L.Experiment(nx, ny, k, 0.6, net, var, loc_radius=2.0, eig_schedule=schedule)
+    exp.set_state(f0)
+    return exp, yo
+
+
+def test_auto_schedule_resolves_at_the_first_analysis_once_per_process():
+    # k = 47 is a shape no other test uses, so the process has no pick for it yet
+    exp, yo = _auto_case(47, L.LETKF_EIG_AUTO, 971)
+    assert exp.stats().eig_schedule == L.LETKF_EIG_AUTO         # unresolved before analysing
+    exp.analyze(yo)
+    pick = exp.stats().eig_schedule
+    assert pick in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT)
+    got = exp.get_deviation()
+    assert exp.sync() == 0
+    # the timed runs worked on scratch: the analysis is the picked schedule's, bit for bit
+    ref, _ = _auto_case(47, pick, 971)
+    ref.analyze(yo)
+    assert np.array_equal(got, ref.get_deviation()) and ref.sync() == 0
+    # a later handle of the same shape takes the pick at letkf_init
+    later, _ = _auto_case(47, L.LETKF_EIG_AUTO, 972)
+    assert later.stats().eig_schedule == pick and later.sync() == 0
+
+
+def test_auto_schedule_first_cycle_runs_eagerly_then_captures():
+    # k = 45: unused elsewhere.  The first cycle times the schedules (no graph), the next
+    # ones replay a captured graph; all equal the picked schedule's cycles bit for bit.
+    a, yo = _auto_case(45, L.LETKF_EIG_AUTO, 975)
+    a.cycle(3, yo)
+    assert a.stats().cycle_kernels == 0                        # eager: no graph yet
+    pick = a.stats().eig_schedule
+    assert pick in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT)
+    b, _ = _auto_case(45, pick, 975)
+    b.cycle(3, yo)
+    for _ in range(2):
+        a.cycle(3, yo)
+        b.cycle(3, yo)
+    assert a.stats().cycle_kernels > 0
+    assert a.stats().cycle_kernels == b.stats().cycle_kernels
+    assert np.array_equal(a.get_deviation(), b.get_deviation())
+    assert a.sync() == 0 and b.sync() == 0
 
 
 @pytest.mark.parametrize("k_big,k_small", [(16, 8), (128, 100), (64, 33)])
