@@ -925,6 +925,98 @@ __global__ void __launch_bounds__(kQlThreads) eig_ql_kernel(EigArgs a, EigSplit 
     for (int t = 0; t < k; ++t) a.eigval[(size_t)lp * k + t] = D[t * L].x;
 }
 
+// One recorded rotation of the replay with the lane's entries of Z in registers: rows I and
+// I + 1 of Z (columns I, I + 1 of the eigenvector matrix) turned by (c, s) = cs[I].
+template <int NC, int I>
+__device__ __forceinline__ void replay_rot(float (&z)[NC][32 * NC], const float2 *cs) {
+    if constexpr (I + 1 < 32 * NC) {
+        const float2 g = cs[I];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const float za = z[c][I], zb = z[c][I + 1];
+            z[c][I + 1] = fmaf(g.y, za, g.x * zb);
+            z[c][I] = fmaf(g.x, za, -(g.y * zb));
+        }
+    }
+}
+
+// Replay of the recorded QL rotations onto Z = I with Z held in registers (k <= 64): the lane
+// keeps its NC columns of the shared-memory image of Z, all 32 NC rows, so a rotation costs
+// one broadcast load of (c, s) and four multiply-adds per column, with no shared-memory
+// traffic for Z.  A sweep's rotations act on rows m-1, m-2, ..., m-cnt in that order; the
+// sweep enters an unrolled chain of rotation steps at row m-1 (a jump table on m) and leaves
+// it after row m-cnt.  Each sweep's record (header and pairs, at most 32 NC entries) is read
+// as one window, one entry per lane and column, the next window's loads in flight while the
+// current sweep runs; its pairs are staged in shared memory at cs[row].  Z is written to
+// shared memory at the end (rows 0..k-1).
+template <int NC>
+__device__ __forceinline__ void replay_in_registers(const float2 *__restrict__ rec, int nrec,
+                                                    float *Z, float2 *cs, int k, int ld,
+                                                    int lane) {
+    constexpr int KM = 32 * NC;
+    float z[NC][KM];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int i = 0; i < KM; ++i) z[c][i] = i == lane + 32 * c ? 1.0f : 0.0f;
+    float2 win[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int idx = lane + 32 * c;
+        win[c] = idx < nrec ? __ldcs(rec + idx) : make_float2(0.0f, 0.0f);
+    }
+    int pos = 0;
+    while (pos < nrec) {
+        const int m = __float_as_int(__shfl_sync(kFull, win[0].x, 0));
+        const int cnt = __float_as_int(__shfl_sync(kFull, win[0].y, 0));
+        const int next = pos + 1 + cnt;
+        float2 nwin[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int idx = next + lane + 32 * c;
+            nwin[c] = idx < nrec ? __ldcs(rec + idx) : make_float2(0.0f, 0.0f);
+        }
+        const bool valid = cnt > 0 && cnt <= m && m <= k - 1;  // as the QL kernel writes them
+        if (valid) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int r = lane + 32 * c - 1;  // window entry 1 + r is pair r
+                if (r >= 0 && r < cnt) cs[m - 1 - r] = win[c];
+            }
+        }
+        __syncwarp();
+        if (valid) {
+            const int lo = m - cnt;
+#define LK_REPLAY_CASE(i)                 \
+    case i:                               \
+        replay_rot<NC, i>(z, cs);         \
+        if (i == lo) break;
+#define LK_REPLAY_CASE8(b)                                                                  \
+    LK_REPLAY_CASE(b + 7) LK_REPLAY_CASE(b + 6) LK_REPLAY_CASE(b + 5) LK_REPLAY_CASE(b + 4) \
+    LK_REPLAY_CASE(b + 3) LK_REPLAY_CASE(b + 2) LK_REPLAY_CASE(b + 1) LK_REPLAY_CASE(b)
+            switch (m - 1) {
+                LK_REPLAY_CASE8(56) LK_REPLAY_CASE8(48) LK_REPLAY_CASE8(40) LK_REPLAY_CASE8(32)
+                LK_REPLAY_CASE8(24) LK_REPLAY_CASE8(16) LK_REPLAY_CASE8(8) LK_REPLAY_CASE8(0)
+                default: break;
+            }
+#undef LK_REPLAY_CASE8
+#undef LK_REPLAY_CASE
+        }
+        __syncwarp();
+        pos = next;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) win[c] = nwin[c];
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int t = lane + 32 * c;
+#pragma unroll
+        for (int i = 0; i < KM; ++i)
+            if (i < k && t < k) Z[i * ld + t] = z[c][i];
+    }
+    __syncwarp();
+}
+
 // (3) vectors, transform and update, warp per matrix: Z = I, the recorded rotations replayed
 // onto Z (each lane its own columns, the carried row in registers), V = H Z, then the
 // fused schedule's transform and update.
@@ -947,48 +1039,53 @@ __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB)
         float xbar[NV];
         float *X = load_forecast<NC>(a, lp, B, k, ld, lane, xbar);
         for (int t = lane; t < k; t += 32) taus[t] = sp.taus[(size_t)lp * k + t];
-        set_identity<NC>(Z, k, ld, lane);
-        // replay: the record is read 32 entries at a time, one per lane, and each entry is
-        // broadcast from its lane
         const float2 *rec = sp.rot + (size_t)lp * sp.rcap;
-        int wbase = 0;
-        float2 win = lane < nrec ? __ldcs(rec + lane) : make_float2(0.0f, 0.0f);
-        auto entry = [&](int idx) -> float2 {
-            if (idx - wbase >= 32) {
-                wbase = idx;
-                win = idx + lane < nrec ? __ldcs(rec + idx + lane) : make_float2(0.0f, 0.0f);
-            }
-            const int src = idx - wbase;
-            return make_float2(__shfl_sync(kFull, win.x, src), __shfl_sync(kFull, win.y, src));
-        };
-        int pos = 0;
-        while (pos < nrec) {
-            const float2 h = entry(pos++);
-            const int m = __float_as_int(h.x), cnt = __float_as_int(h.y);
-            float zc[NC];  // carried column entries of row i+1 of Z
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const int t = lane + 32 * c;
-                zc[c] = t < k ? Z[m * ld + t] : 0.0f;
-            }
-            float *zp = Z + (m - 1) * ld + lane;
-            for (int r = 0; r < cnt; ++r) {
-                const float2 cs = entry(pos++);
-                const float co = cs.x, s = cs.y;
+        if constexpr (NC <= 2) {
+            // Z's shared memory is free until the replay ends: it holds the staged (c, s)
+            replay_in_registers<NC>(rec, nrec, Z, reinterpret_cast<float2 *>(Z), k, ld, lane);
+        } else {
+            set_identity<NC>(Z, k, ld, lane);
+            // replay: the record is read 32 entries at a time, one per lane, and each entry is
+            // broadcast from its lane
+            int wbase = 0;
+            float2 win = lane < nrec ? __ldcs(rec + lane) : make_float2(0.0f, 0.0f);
+            auto entry = [&](int idx) -> float2 {
+                if (idx - wbase >= 32) {
+                    wbase = idx;
+                    win = idx + lane < nrec ? __ldcs(rec + idx + lane) : make_float2(0.0f, 0.0f);
+                }
+                const int src = idx - wbase;
+                return make_float2(__shfl_sync(kFull, win.x, src), __shfl_sync(kFull, win.y, src));
+            };
+            int pos = 0;
+            while (pos < nrec) {
+                const float2 h = entry(pos++);
+                const int m = __float_as_int(h.x), cnt = __float_as_int(h.y);
+                float zc[NC];  // carried column entries of row i+1 of Z
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    if (lane + 32 * c < k) {
-                        const float za = zp[32 * c];
-                        zp[ld + 32 * c] = s * za + co * zc[c];
-                        zc[c] = co * za - s * zc[c];
-                    }
+                    const int t = lane + 32 * c;
+                    zc[c] = t < k ? Z[m * ld + t] : 0.0f;
                 }
-                zp -= ld;
-            }
+                float *zp = Z + (m - 1) * ld + lane;
+                for (int r = 0; r < cnt; ++r) {
+                    const float2 cs = entry(pos++);
+                    const float co = cs.x, s = cs.y;
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const int t = lane + 32 * c;
-                if (t < k) Z[(m - cnt) * ld + t] = zc[c];
+                    for (int c = 0; c < NC; ++c) {
+                        if (lane + 32 * c < k) {
+                            const float za = zp[32 * c];
+                            zp[ld + 32 * c] = s * za + co * zc[c];
+                            zc[c] = co * za - s * zc[c];
+                        }
+                    }
+                    zp -= ld;
+                }
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const int t = lane + 32 * c;
+                    if (t < k) Z[(m - cnt) * ld + t] = zc[c];
+                }
             }
         }
         __syncwarp();
