@@ -49,8 +49,12 @@ __host__ __device__ inline int smem_floats(int k) {
     const int ld = k + 1;
     return round4(k * ld + kRows * ld + 6 * k);
 }
-// split, tridiagonalization: S (k x ld), vw (k float2), de (k float2), taus (k)
-__host__ __device__ inline int tri_smem_floats(int k) { return round4(k * (k + 1) + 5 * k); }
+// split, tridiagonalization: S (k x ld), vw (tri_vw(k) float2: k rounded up to a multiple of
+// 32, the rows the register chains of k <= 64 read), de (k float2), taus (k)
+__host__ __device__ inline int tri_vw(int k) { return (k + 31) & ~31; }
+__host__ __device__ inline int tri_smem_floats(int k) {
+    return round4(k * (k + 1) + 2 * tri_vw(k) + 3 * k);
+}
 // split, vectors and update: Z (k x ld), B (kRows x ld), taus (k), vtmp (k)
 __host__ __device__ inline int vec_smem_floats(int k) {
     const int ld = k + 1;
@@ -794,6 +798,176 @@ __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB)
 
 // ---- split schedule -----------------------------------------------------------------------
 
+// ---- tridiagonalization with Q in registers (split schedule) ------------------------------
+// Written for NC <= 2 and used for k <= 32: at 33 <= k <= 64 the 212-register form ran 10 %
+// slower than the shared-memory one (occupancy), at k <= 32 it cut the kernel by ~40 %.
+// The lane keeps its NC columns of Q, all 32 NC rows, in registers: q[c][i] = Q[i][t] with
+// t = lane + 32 c.  Every loop over the rows of the trailing block (the product Q'v and the
+// rank-2 update) enters an unrolled chain of row steps at row j + 1 through a jump table on j
+// and runs to row 32 NC - 1; rows at and beyond k hold zeros (their v and w are zero, and
+// step j writes v and w of rows j + 1..k - 1 before its chains read them).  The broadcast
+// operands (v, then w) come from shared memory at compile-time offsets.
+
+// q[c][row] for a row index uniform across the warp (jump table)
+template <int NC, int I>
+__device__ __forceinline__ void tri_pick(const float (&q)[NC][32 * NC], float (&x)[NC]) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) x[c] = q[c][I];
+}
+
+// p += Q'[s][t] v_s for row s = I + 1
+template <int NC, int I>
+__device__ __forceinline__ void tri_mv(const float (&q)[NC][32 * NC], const float2 *vw,
+                                       float (&p)[NC]) {
+    if constexpr (I + 1 < 32 * NC) {
+        const float vs = vw[I + 1].x;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) p[c] = fmaf(q[c][I + 1], vs, p[c]);
+    }
+}
+
+// Q'[s][t] -= v_s w_t + w_s v_t for row s = I + 1
+template <int NC, int I>
+__device__ __forceinline__ void tri_up(float (&q)[NC][32 * NC], const float2 *vw,
+                                       const float (&vt)[NC], const float (&wt)[NC]) {
+    if constexpr (I + 1 < 32 * NC) {
+        const float2 g = vw[I + 1];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) q[c][I + 1] -= fmaf(g.x, wt[c], g.y * vt[c]);
+    }
+}
+
+// Case labels 0..63 in increasing order: a chain entered at case j falls through the rows
+// above j + 1.
+#define LK_CASE8(M, b) M(b) M(b + 1) M(b + 2) M(b + 3) M(b + 4) M(b + 5) M(b + 6) M(b + 7)
+#define LK_CASES64(M)                                                                      \
+    LK_CASE8(M, 0) LK_CASE8(M, 8) LK_CASE8(M, 16) LK_CASE8(M, 24) LK_CASE8(M, 32)         \
+    LK_CASE8(M, 40) LK_CASE8(M, 48) LK_CASE8(M, 56)
+
+// Householder tridiagonalization of Q (symmetric, in S) with the same reflectors, scalars and
+// outputs as tridiagonalize(): reflector j into the lower triangle of the Gram slot, tau_j into
+// taus, (d, e) into de.  S is only read.
+template <int NC>
+__device__ __forceinline__ void tridiagonalize_registers(float *Ag, const float *S, float2 *vw,
+                                                         float2 *de, float *taus, int k,
+                                                         int ld, int lane) {
+    constexpr int KM = 32 * NC;
+    float q[NC][KM];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int t = lane + 32 * c;
+#pragma unroll
+        for (int i = 0; i < KM; ++i) q[c][i] = (i < k && t < k) ? S[i * ld + t] : 0.0f;
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) vw[lane + 32 * c] = make_float2(0.0f, 0.0f);
+    __syncwarp();
+    for (int j = 0; j < k - 2; ++j) {
+        // x_t = Q'[t][j] = Q'[j][t] for t > j: the lane's own entries of row j
+        float x[NC];
+        switch (j) {
+#define LK_PICK(i) \
+    case i: tri_pick<NC, (i < KM ? i : 0)>(q, x); break;
+            LK_CASES64(LK_PICK)
+#undef LK_PICK
+            default: break;
+        }
+        float tail = 0.0f;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int t = lane + 32 * c;
+            if (t <= j || t >= k) x[c] = 0.0f;
+            if (t > j + 1) tail = fmaf(x[c], x[c], tail);
+        }
+        tail = warp_sum(tail);
+        const int ta = j + 1;
+        const float alpha =
+            __shfl_sync(kFull, NC == 1 || ta < 32 ? x[0] : x[NC > 1 ? 1 : 0], ta & 31);
+        // H x = beta e_0 with beta = -sign(alpha) ||x||, tau = 1 + |alpha| / ||x||,
+        // v = x / (alpha - beta), v_0 = 1 (one rsqrt, one reciprocal, no division)
+        float tau = 0.0f, beta = alpha, scale = 0.0f;
+        if (tail > 0.0f) {
+            const float n2 = fmaf(alpha, alpha, tail);
+            float rn = rsqrtf(n2);
+            rn = rn * fmaf(-0.5f * n2, rn * rn, 1.5f);
+            const float nrm = n2 * rn;
+            beta = -copysignf(nrm, alpha);
+            tau = fmaf(fabsf(alpha), rn, 1.0f);
+            scale = copysignf(__frcp_rn(fabsf(alpha) + nrm), alpha);
+        }
+        float vt[NC];
+        float *refl = refl_row(Ag, k, j);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int t = lane + 32 * c;
+            vt[c] = t > j + 1 ? x[c] * scale : (t == j + 1 ? 1.0f : 0.0f);
+            if (t > j && t < k) {
+                vw[t].x = vt[c];
+                refl[t - j - 1] = vt[c];  // lower triangle of the slot
+            }
+        }
+        if (lane == 0) {
+            taus[j] = tau;
+            de[j].y = beta;
+        }
+        __syncwarp();
+        if (tau != 0.0f) {
+            float p[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) p[c] = 0.0f;
+            switch (j) {
+#define LK_MV(i) \
+    case i: tri_mv<NC, i>(q, vw, p);
+                LK_CASES64(LK_MV)
+#undef LK_MV
+                default: break;
+            }
+            float kk = 0.0f;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                p[c] *= tau;
+                kk = fmaf(p[c], vt[c], kk);
+            }
+            const float K = 0.5f * tau * warp_sum(kk);
+            float wt[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int t = lane + 32 * c;
+                wt[c] = t > j && t < k ? p[c] - K * vt[c] : 0.0f;
+                if (t > j && t < k) vw[t].y = wt[c];
+            }
+            __syncwarp();
+            switch (j) {
+#define LK_UP(i) \
+    case i: tri_up<NC, i>(q, vw, vt, wt);
+                LK_CASES64(LK_UP)
+#undef LK_UP
+                default: break;
+            }
+        }
+        __syncwarp();  // every row step has read vw before the next step rewrites it
+    }
+    // ---- (d, e): d_t = Q'[t][t] (the lane's own diagonal), e_{k-2} = Q'[k-2][k-1]
+    float dg[NC], el[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        dg[c] = 0.0f;
+        el[c] = 0.0f;
+        const int t = lane + 32 * c;
+#pragma unroll
+        for (int i = 0; i < KM; ++i) {
+            if (i == t) dg[c] = q[c][i];
+            if (i == k - 2) el[c] = q[c][i];
+        }
+        if (t < k) de[t].x = dg[c];
+        if (t == k - 1 && k >= 2) de[k - 2].y = el[c];
+        if (t == k - 1) de[t].y = 0.0f;
+    }
+    __syncwarp();
+}
+#undef LK_CASES64
+#undef LK_CASE8
+
 // (1) tridiagonalization, warp per matrix: (d, e) and the reflector scalars to global memory.
 template <int NC>
 __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS) eig_tridiag_kernel(EigArgs a,
@@ -803,7 +977,7 @@ __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS) eig_tridiag_kernel(Eig
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     float *S = smem + (size_t)wib * tri_smem_floats(k);
     float2 *vw = reinterpret_cast<float2 *>(S + k * ld);
-    float2 *de = vw + k;
+    float2 *de = vw + tri_vw(k);
     float *taus = reinterpret_cast<float *>(de + k);
     const int warps_per_block = blockDim.x >> 5;
     const int nw = gridDim.x * warps_per_block;
@@ -811,7 +985,10 @@ __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS) eig_tridiag_kernel(Eig
         if (a.nloc[lp] == 0) continue;
         float *Ag = a.gram + (size_t)lp * k * k;
         load_q<NC>(Ag, S, k, ld, lane, a.diag);
-        tridiagonalize<NC>(Ag, S, vw, de, taus, k, ld, lane);
+        if constexpr (NC == 1)  // at k <= 64 (212 registers) the shared-memory form is faster
+            tridiagonalize_registers<NC>(Ag, S, vw, de, taus, k, ld, lane);
+        else
+            tridiagonalize<NC>(Ag, S, vw, de, taus, k, ld, lane);
         for (int t = lane; t < k; t += 32) {
             sp.de[(size_t)lp * k + t] = de[t];
             sp.taus[(size_t)lp * k + t] = taus[t];
