@@ -55,10 +55,11 @@ __host__ __device__ inline int tri_vw(int k) { return (k + 31) & ~31; }
 __host__ __device__ inline int tri_smem_floats(int k) {
     return round4(k * (k + 1) + 2 * tri_vw(k) + 3 * k);
 }
-// split, vectors and update: Z (k x ld), B (kRows x ld), taus (k), vtmp (k)
+// split, vectors and update: vtmp (tri_vw(k): one reflector by absolute row, zero-padded to a
+// multiple of 32, first so that it is 16-byte aligned), Z (k x ld), B (kRows x ld), taus (k)
 __host__ __device__ inline int vec_smem_floats(int k) {
     const int ld = k + 1;
-    return round4(k * ld + kRows * ld + 2 * k);
+    return round4(tri_vw(k) + k * ld + kRows * ld + k);
 }
 
 // Reflector j (m = k-1-j entries) is kept in row k-1-j of the point's Gram slot, columns
@@ -455,6 +456,122 @@ __device__ __forceinline__ void back_transform(float *Ag, float *Z, const float 
     }
 
 }
+
+// ---- V = H Z with the lane's rows of Z in registers (split schedule, k <= 64) --------------
+// Lane owns rows col = lane + 32 c of the stored Z (columns of the eigenvector matrix), all
+// 32 NC entries, in registers.  Reflector j is staged in vtmp by absolute row (rows j+1..k-1;
+// rows above k and the rows of its first 4-row group below j+1 stay zero), so the dot product
+// and the update run over whole 4-row groups from the group holding row j + 1: one 16-byte
+// broadcast load and 4 NC multiply-adds per group, entered through a jump table on the group.
+
+template <int NC, int G>
+__device__ __forceinline__ void bt_dot(const float (&zr)[NC][32 * NC], const float4 *v4,
+                                       float (&acc)[NC][4]) {
+    if constexpr (4 * G < 32 * NC) {
+        const float4 v = v4[G];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            acc[c][0] = fmaf(v.x, zr[c][4 * G], acc[c][0]);
+            acc[c][1] = fmaf(v.y, zr[c][4 * G + 1], acc[c][1]);
+            acc[c][2] = fmaf(v.z, zr[c][4 * G + 2], acc[c][2]);
+            acc[c][3] = fmaf(v.w, zr[c][4 * G + 3], acc[c][3]);
+        }
+    }
+}
+
+template <int NC, int G>
+__device__ __forceinline__ void bt_update(float (&zr)[NC][32 * NC], const float4 *v4,
+                                          const float (&beta)[NC]) {
+    if constexpr (4 * G < 32 * NC) {
+        const float4 v = v4[G];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            zr[c][4 * G] = fmaf(-beta[c], v.x, zr[c][4 * G]);
+            zr[c][4 * G + 1] = fmaf(-beta[c], v.y, zr[c][4 * G + 1]);
+            zr[c][4 * G + 2] = fmaf(-beta[c], v.z, zr[c][4 * G + 2]);
+            zr[c][4 * G + 3] = fmaf(-beta[c], v.w, zr[c][4 * G + 3]);
+        }
+    }
+}
+
+#define LK_G8(M, b) M(b) M(b + 1) M(b + 2) M(b + 3) M(b + 4) M(b + 5) M(b + 6) M(b + 7)
+#define LK_GROUPS16(M) LK_G8(M, 0) LK_G8(M, 8)
+
+// The same V = H Z as back_transform(); vtmp holds 32 NC floats, 16-byte aligned.
+template <int NC>
+__device__ __forceinline__ void back_transform_registers(float *Ag, float *Z, const float *taus,
+                                                         float *vtmp, int k, int ld, int lane) {
+    constexpr int KM = 32 * NC;
+    static_assert(KM / 4 <= 16, "group chain covers 64 rows");
+    float zr[NC][KM];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int col = lane + 32 * c;
+#pragma unroll
+        for (int t = 0; t < KM; ++t) zr[c][t] = (col < k && t < k) ? Z[col * ld + t] : 0.0f;
+        vtmp[col] = 0.0f;
+    }
+    float vnext[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int t = lane + 32 * c;  // reflector k-3 has m = 2
+        vnext[c] = (k >= 3 && t < 2) ? __ldcg(refl_row(Ag, k, k - 3) + t) : 0.0f;
+    }
+    __syncwarp();
+    const float4 *v4 = reinterpret_cast<const float4 *>(vtmp);
+    for (int j = k - 3; j >= 0; --j) {
+        const int m = k - 1 - j;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int t = lane + 32 * c;
+            if (t < m) vtmp[j + 1 + t] = vnext[c];
+        }
+        __syncwarp();
+        if (j > 0)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int t = lane + 32 * c;
+                vnext[c] = t < m + 1 ? __ldcg(refl_row(Ag, k, j - 1) + t) : 0.0f;
+            }
+        const float tau = taus[j];
+        if (tau != 0.0f) {
+            float acc[NC][4];
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[c][u] = 0.0f;
+            switch ((j + 1) >> 2) {
+#define LK_BT_DOT(G) \
+    case G: bt_dot<NC, G>(zr, v4, acc);
+                LK_GROUPS16(LK_BT_DOT)
+#undef LK_BT_DOT
+                default: break;
+            }
+            float beta[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                beta[c] = ((acc[c][0] + acc[c][1]) + (acc[c][2] + acc[c][3])) * tau;
+            switch ((j + 1) >> 2) {
+#define LK_BT_UPDATE(G) \
+    case G: bt_update<NC, G>(zr, v4, beta);
+                LK_GROUPS16(LK_BT_UPDATE)
+#undef LK_BT_UPDATE
+                default: break;
+            }
+        }
+        __syncwarp();  // every group has read vtmp before the next reflector is staged
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int col = lane + 32 * c;
+#pragma unroll
+        for (int t = 0; t < KM; ++t)
+            if (col < k && t < k) Z[col * ld + t] = zr[c][t];
+    }
+    __syncwarp();
+}
+#undef LK_GROUPS16
+#undef LK_G8
 
 // C = B V, mean increment, scaled perturbations, X^a written in place.
 template <int NC>
@@ -1257,10 +1374,10 @@ __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB_VEC)
     extern __shared__ float smem[];
     const int k = a.k, ld = k + 1;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    float *Z = smem + (size_t)wib * vec_smem_floats(k);
+    float *vtmp = smem + (size_t)wib * vec_smem_floats(k);
+    float *Z = vtmp + tri_vw(k);
     float *B = Z + k * ld;
     float *taus = B + kRows * ld;
-    float *vtmp = taus + k;
     const int warps_per_block = blockDim.x >> 5;
     const int nw = gridDim.x * warps_per_block;
     for (int lp = blockIdx.x * warps_per_block + wib; lp < a.npts; lp += nw) {
@@ -1326,7 +1443,10 @@ __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB_VEC)
             const int t = lane + 32 * c;
             dr[c] = t < k ? a.eigval[(size_t)lp * k + t] : 1.0f;
         }
-        back_transform<NC>(Ag, Z, taus, vtmp, k, ld, lane);
+        if constexpr (NC <= 2)
+            back_transform_registers<NC>(Ag, Z, taus, vtmp, k, ld, lane);
+        else
+            back_transform<NC>(Ag, Z, taus, vtmp, k, ld, lane);
         if (a.refine) {
             refine_clusters<NC>(Z, ld, Ag, a.diag, k, dr, lane, a.refine_tau);
 #pragma unroll
