@@ -55,11 +55,13 @@ __host__ __device__ inline int tri_vw(int k) { return (k + 31) & ~31; }
 __host__ __device__ inline int tri_smem_floats(int k) {
     return round4(k * (k + 1) + 2 * tri_vw(k) + 3 * k);
 }
-// split, vectors and update: vtmp (tri_vw(k): one reflector by absolute row, zero-padded to a
-// multiple of 32, first so that it is 16-byte aligned), Z (k x ld), B (kRows x ld), taus (k)
+// split, vectors and update: a staging area first (16-byte aligned; 2 tri_vw(k) + 8 floats:
+// the replay's (c, s) by row, rows 0..k+1, then one reflector by absolute row for the
+// back-transform, zero-padded to a multiple of 32), Z (k x ld), B (kRows x ld), taus (k)
+__host__ __device__ inline int vec_stage_floats(int k) { return 2 * tri_vw(k) + 8; }
 __host__ __device__ inline int vec_smem_floats(int k) {
     const int ld = k + 1;
-    return round4(tri_vw(k) + k * ld + kRows * ld + k);
+    return round4(vec_stage_floats(k) + k * ld + kRows * ld + k);
 }
 
 // Reflector j (m = k-1-j entries) is kept in row k-1-j of the point's Gram slot, columns
@@ -1267,45 +1269,59 @@ __global__ void __launch_bounds__(kQlThreads) eig_ql_kernel(EigArgs a, EigSplit 
     for (int t = 0; t < k; ++t) a.eigval[(size_t)lp * k + t] = D[t * L].x;
 }
 
-// One recorded rotation of the replay with the lane's entries of Z in registers: rows I and
-// I + 1 of Z (columns I, I + 1 of the eigenvector matrix) turned by (c, s) = g0 = cs[I].  The
-// pair two rows down is loaded here (g0, g1, g2 rotate), so a shared-memory load is in flight
-// for two rotation steps before it is used.
-template <int NC, int I>
-__device__ __forceinline__ void replay_rot(float (&z)[NC][32 * NC], float2 &g0, float2 &g1,
-                                           const float2 *cs) {
-    if constexpr (I + 1 < 32 * NC) {
-        const float2 g2 = cs[I > 1 ? I - 2 : 0];
+// One 4-row group of a replay sweep with the lane's entries of Z in registers: the rotations
+// of rows 4G+3, 4G+2, 4G+1, 4G in that order, row i turning rows i and i + 1 of Z (columns i,
+// i + 1 of the eigenvector matrix) by (c, s) of cs[i]; pa, pb hold the group's four pairs.
+// Rows of the group outside the sweep hold (1, 0), which leaves both rows exactly as they are.
+template <int NC, int R>
+__device__ __forceinline__ void replay_rot(float (&z)[NC][32 * NC], float co, float s) {
+    if constexpr (R + 1 < 32 * NC) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-            const float za = z[c][I], zb = z[c][I + 1];
-            z[c][I + 1] = fmaf(g0.y, za, g0.x * zb);
-            z[c][I] = fmaf(g0.x, za, -(g0.y * zb));
+            const float za = z[c][R], zb = z[c][R + 1];
+            z[c][R + 1] = fmaf(s, za, co * zb);
+            z[c][R] = fmaf(co, za, -(s * zb));
         }
-        g0 = g1;
-        g1 = g2;
+    }
+}
+
+template <int NC, int G>
+__device__ __forceinline__ void replay_group(float (&z)[NC][32 * NC], const float4 &pa,
+                                             const float4 &pb) {
+    if constexpr (4 * G < 32 * NC) {
+        replay_rot<NC, 4 * G + 3>(z, pb.z, pb.w);
+        replay_rot<NC, 4 * G + 2>(z, pb.x, pb.y);
+        replay_rot<NC, 4 * G + 1>(z, pa.z, pa.w);
+        replay_rot<NC, 4 * G>(z, pa.x, pa.y);
     }
 }
 
 // Replay of the recorded QL rotations onto Z = I with Z held in registers (k <= 64): the lane
 // keeps its NC columns of the shared-memory image of Z, all 32 NC rows, so a rotation costs
-// one broadcast load of (c, s) and four multiply-adds per column, with no shared-memory
-// traffic for Z.  A sweep's rotations act on rows m-1, m-2, ..., m-cnt in that order; the
-// sweep enters an unrolled chain of rotation steps at row m-1 (a jump table on m) and leaves
-// it after row m-cnt.  Each sweep's record (header and pairs, at most 32 NC entries) is read
-// as one window, one entry per lane and column, the next window's loads in flight while the
-// current sweep runs; its pairs are staged in shared memory at cs[row].  Z is written to
-// shared memory at the end (rows 0..k-1).
+// four multiply-adds per column and no shared-memory traffic for Z.  A sweep's rotations act
+// on rows m-1, m-2, ..., m-cnt in that order.  For 33 <= k <= 64 the sweep enters an unrolled
+// chain of 4-row groups at the group of row m-1 (a jump table) and leaves it after the group
+// of row m-cnt, the rows of those two groups outside the sweep padded with identity
+// rotations; the pairs are staged in shared memory by row (cs[row], rows 0..k+1) and read as
+// 16-byte broadcast loads, one group ahead.  For k <= 32 (one column per lane) the chain goes
+// row by row (GR = 1: no padding, an exit test per row, the pair two rows ahead in flight):
+// measured 3 % faster there than groups of 2 or 4, and 4 % slower at k = 64.  Each sweep's record (header and pairs, at most 32 NC
+// entries) is read as one window, one entry per lane and column, the next window's loads in
+// flight while the current sweep runs.  Z is written to shared memory at the end.
 template <int NC>
 __device__ __forceinline__ void replay_in_registers(const float2 *__restrict__ rec, int nrec,
                                                     float *Z, float2 *cs, int k, int ld,
                                                     int lane) {
     constexpr int KM = 32 * NC;
+    constexpr int GR = NC == 1 ? 1 : 4;   // rows per group
+    constexpr int LG = GR == 1 ? 0 : 2;   // log2 GR
+    static_assert(GR == 1 ? KM <= 64 : KM / GR <= 16, "the chains have 64 and 16 cases");
     float z[NC][KM];
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
         for (int i = 0; i < KM; ++i) z[c][i] = i == lane + 32 * c ? 1.0f : 0.0f;
+    const float4 *cs4 = reinterpret_cast<const float4 *>(cs);
     float2 win[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
@@ -1324,31 +1340,62 @@ __device__ __forceinline__ void replay_in_registers(const float2 *__restrict__ r
             nwin[c] = idx < nrec ? __ldcs(rec + idx) : make_float2(0.0f, 0.0f);
         }
         const bool valid = cnt > 0 && cnt <= m && m <= k - 1;  // as the QL kernel writes them
+        const int lo = m - cnt;
+        const int gt = (m - 1) >> LG, gb = lo >> LG;
         if (valid) {
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 const int r = lane + 32 * c - 1;  // window entry 1 + r is pair r
                 if (r >= 0 && r < cnt) cs[m - 1 - r] = win[c];
             }
+            // identity pads: rows GR gb .. lo-1 and m .. GR gt + GR - 1 (fewer than GR each)
+            const int row = lane < GR ? GR * gb + lane : m + lane - GR;
+            if ((lane < GR && row < lo) || (lane >= GR && lane < 2 * GR && row < GR * (gt + 1)))
+                cs[row] = make_float2(1.0f, 0.0f);
         }
         __syncwarp();
         if (valid) {
-            const int lo = m - cnt;
-            float2 g0 = cs[m - 1], g1 = cs[m > 1 ? m - 2 : 0];
-#define LK_REPLAY_CASE(i)                 \
-    case i:                               \
-        replay_rot<NC, i>(z, g0, g1, cs); \
-        if (i == lo) break;
-#define LK_REPLAY_CASE8(b)                                                                  \
-    LK_REPLAY_CASE(b + 7) LK_REPLAY_CASE(b + 6) LK_REPLAY_CASE(b + 5) LK_REPLAY_CASE(b + 4) \
-    LK_REPLAY_CASE(b + 3) LK_REPLAY_CASE(b + 2) LK_REPLAY_CASE(b + 1) LK_REPLAY_CASE(b)
-            switch (m - 1) {
-                LK_REPLAY_CASE8(56) LK_REPLAY_CASE8(48) LK_REPLAY_CASE8(40) LK_REPLAY_CASE8(32)
-                LK_REPLAY_CASE8(24) LK_REPLAY_CASE8(16) LK_REPLAY_CASE8(8) LK_REPLAY_CASE8(0)
-                default: break;
+            if constexpr (GR == 1) {
+                float2 g0 = cs[m - 1], g1 = cs[m > 1 ? m - 2 : 0];
+#define LK_REPLAY_ROW(i)                                  \
+    case i: {                                             \
+        const float2 g2 = cs[i > 1 ? i - 2 : 0];          \
+        replay_rot<NC, i>(z, g0.x, g0.y);                 \
+        if (i == lo) break;                               \
+        g0 = g1;                                          \
+        g1 = g2;                                          \
+    }
+#define LK_REPLAY_ROW8(b)                                                           \
+    LK_REPLAY_ROW(b + 7) LK_REPLAY_ROW(b + 6) LK_REPLAY_ROW(b + 5) LK_REPLAY_ROW(b + 4) \
+    LK_REPLAY_ROW(b + 3) LK_REPLAY_ROW(b + 2) LK_REPLAY_ROW(b + 1) LK_REPLAY_ROW(b)
+                switch (m - 1) {
+                    LK_REPLAY_ROW8(56) LK_REPLAY_ROW8(48) LK_REPLAY_ROW8(40) LK_REPLAY_ROW8(32)
+                    LK_REPLAY_ROW8(24) LK_REPLAY_ROW8(16) LK_REPLAY_ROW8(8) LK_REPLAY_ROW8(0)
+                    default: break;
+                }
+#undef LK_REPLAY_ROW8
+#undef LK_REPLAY_ROW
+            } else {
+                // group G's four pairs: float4 2 G and 2 G + 1
+                float4 pa = cs4[2 * gt], pb = cs4[2 * gt + 1];
+#define LK_REPLAY_GROUP(G)                          \
+    case G: {                                       \
+        const float4 na = cs4[G > 0 ? 2 * G - 2 : 0]; \
+        const float4 nb = cs4[G > 0 ? 2 * G - 1 : 1]; \
+        replay_group<NC, G>(z, pa, pb);             \
+        if (G == gb) break;                         \
+        pa = na;                                    \
+        pb = nb;                                    \
+    }
+                switch (gt) {
+                    LK_REPLAY_GROUP(15) LK_REPLAY_GROUP(14) LK_REPLAY_GROUP(13) LK_REPLAY_GROUP(12)
+                    LK_REPLAY_GROUP(11) LK_REPLAY_GROUP(10) LK_REPLAY_GROUP(9) LK_REPLAY_GROUP(8)
+                    LK_REPLAY_GROUP(7) LK_REPLAY_GROUP(6) LK_REPLAY_GROUP(5) LK_REPLAY_GROUP(4)
+                    LK_REPLAY_GROUP(3) LK_REPLAY_GROUP(2) LK_REPLAY_GROUP(1) LK_REPLAY_GROUP(0)
+                    default: break;
+                }
+#undef LK_REPLAY_GROUP
             }
-#undef LK_REPLAY_CASE8
-#undef LK_REPLAY_CASE
         }
         __syncwarp();
         pos = next;
@@ -1375,7 +1422,7 @@ __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB_VEC)
     const int k = a.k, ld = k + 1;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     float *vtmp = smem + (size_t)wib * vec_smem_floats(k);
-    float *Z = vtmp + tri_vw(k);
+    float *Z = vtmp + vec_stage_floats(k);
     float *B = Z + k * ld;
     float *taus = B + kRows * ld;
     const int warps_per_block = blockDim.x >> 5;
@@ -1389,8 +1436,7 @@ __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB_VEC)
         for (int t = lane; t < k; t += 32) taus[t] = sp.taus[(size_t)lp * k + t];
         const float2 *rec = sp.rot + (size_t)lp * sp.rcap;
         if constexpr (NC <= 2) {
-            // Z's shared memory is free until the replay ends: it holds the staged (c, s)
-            replay_in_registers<NC>(rec, nrec, Z, reinterpret_cast<float2 *>(Z), k, ld, lane);
+            replay_in_registers<NC>(rec, nrec, Z, reinterpret_cast<float2 *>(vtmp), k, ld, lane);
         } else {
             set_identity<NC>(Z, k, ld, lane);
             // replay: the record is read 32 entries at a time, one per lane, and each entry is
