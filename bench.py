@@ -56,6 +56,8 @@ def parse_args(argv=None):
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="turb256_k32")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--chunk-mb", type=float, default=0.0,
+                   help="Gram buffer per analysis chunk in MiB (0: the library default)")
     p.add_argument("--eig-schedule", choices=sorted(EIG_SCHEDULES), default="auto",
                    help="eigensolve schedule (auto: the handle's autotuner picks)")
     p.add_argument("--cpu-sample-seconds", type=float, default=12.0)
@@ -322,14 +324,14 @@ def spin_up(w, device):
     return spin, members, (net, var, kw)
 
 
-def make_experiment(w, members, setup, device, precision, eig_schedule=0):
+def make_experiment(w, members, setup, device, precision, eig_schedule=0, chunk_bytes=0):
     """A fresh experiment of the workload starting from the spun-up members."""
     import torch
 
     from paper_2308_03310_gb300 import letkf as L
     net, var, kw = setup
     exp = L.Experiment(w.nx, w.ny, w.k, w.tau, net, var, device=device, precision=precision,
-                       eig_schedule=eig_schedule, **kw)
+                       eig_schedule=eig_schedule, chunk_bytes=chunk_bytes, **kw)
     torch.cuda.synchronize(device)
     L.letkf_set_deviation(exp.h, members.data_ptr(), 0, w.k, L.LETKF_DEVICE)
     assert exp.sync() == 0
@@ -493,7 +495,8 @@ def main(argv=None):
     forms = {"fp32": [L.LETKF_FP32], "mixed": [L.LETKF_MIXED],
              "both": [L.LETKF_FP32, L.LETKF_MIXED]}[args.precision]
     sched = EIG_SCHEDULES[args.eig_schedule]
-    results = [measure(w, members, setup, yos, device, prec, steps, warm, world, sched)
+    chunk = int(args.chunk_mb * (1 << 20))
+    results = [measure(w, members, setup, yos, device, prec, steps, warm, world, sched, chunk)
                for prec in forms]
     head = results[0]
     line = {
@@ -504,6 +507,7 @@ def main(argv=None):
         "p50_cycle_ms": head["p50_cycle_ms"], "p99_cycle_ms": head["p99_cycle_ms"],
         "roofline": head["roofline"], "kernels": head["kernels"], "e2e": head["e2e"],
         "gpu_launches": head["gpu_launches"], "eig_schedule": head["eig_schedule"],
+        "chunks_per_analysis": head["chunks_per_analysis"],
         "lbm": head["lbm"],
         "clocks": head["clocks"],
         "local_obs": head["local_obs"],
@@ -712,7 +716,8 @@ def serve_main(args, device, rank, world):
     return 0
 
 
-def measure(w, members, setup, yos, device, precision, steps, warm, world, eig_schedule=0):
+def measure(w, members, setup, yos, device, precision, steps, warm, world, eig_schedule=0,
+            chunk_bytes=0):
     """Time `steps` cycles of one precision form (device-resident inputs), then the same
     through the public API with host buffers."""
     import numpy as np
@@ -720,7 +725,7 @@ def measure(w, members, setup, yos, device, precision, steps, warm, world, eig_s
 
     from paper_2308_03310_gb300 import letkf as L
 
-    exp = make_experiment(w, members, setup, device, precision, eig_schedule)
+    exp = make_experiment(w, members, setup, device, precision, eig_schedule, chunk_bytes)
     st = exp.stats()
     LV = exp.L * exp.V
     stream = exp.stream
@@ -823,6 +828,7 @@ def measure(w, members, setup, yos, device, precision, steps, warm, world, eig_s
                 "d2h_bytes_per_step": exp.nmem * LV * 4},
         "gpu_launches": cycle_kernels * steps,
         "eig_schedule": EIG_NAMES.get(st_end.eig_schedule, str(st_end.eig_schedule)),
+        "chunks_per_analysis": st_end.n_chunks,
         "lbm": lbm_rates(w, ms["lbm_step"], peaks),
         "clocks": clocks,
         "local_obs": {"mean": st.mean_local_obs, "max": st.max_local_obs,

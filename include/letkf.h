@@ -99,7 +99,8 @@ typedef struct letkf_config {
     int32_t precision;         /* LETKF_FP32 or LETKF_MIXED                             */
     int32_t eig_schedule;      /* LETKF_EIG_*; 0 (AUTO) lets the handle choose          */
     int64_t chunk_bytes;       /* device bytes for the per-point k x k Gram buffer;
-                                  0 = default (256 MiB)                                 */
+                                  0 = default (1 GiB; larger chunks give the
+                                  thread-per-matrix QL kernel more matrices per launch) */
     void   *stream;            /* cudaStream_t to run on; NULL = a stream the handle
                                   creates and owns                                       */
 } letkf_config;

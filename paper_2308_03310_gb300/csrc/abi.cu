@@ -27,7 +27,7 @@
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int64_t kDefaultChunkBytes = 256ll << 20;
+constexpr int64_t kDefaultChunkBytes = 1ll << 30;  // 1 GiB: 65,536 points at k = 64
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
