@@ -612,6 +612,7 @@ def group_main(args, device, rank, world):
                 stream.wait_event(done)
 
         g = timed(group_cycle)
+        picks = [EIG_NAMES.get(e.stats().eig_schedule, "auto") for e in exps]
         sep = timed(separate_cycles)
         for e in exps:
             rc = e.sync()
@@ -627,6 +628,7 @@ def group_main(args, device, rank, world):
             "separate_ms_per_cycle": statistics.mean(sep),
             "zero_obs_fraction": st.n_zero_obs / st.n_points,
             "max_local_obs": st.max_local_obs, "mean_local_obs": st.mean_local_obs,
+            "eig_schedules": dict(zip((str(k) for k in ks), picks)),
         }
         for e in exps:
             e.close()
@@ -642,7 +644,7 @@ def group_main(args, device, rank, world):
                    "network": "clustered: every 2nd point over 25 % of the domain, every 16th "
                               "elsewhere, an observation-free band", "loc_radius": r,
                    "steps_per_cycle": steps_cycle, "precision": "fp32",
-                   "parallelism": "one grouped launch per column class"},
+                   "parallelism": "one grouped launch per column class for the fused-schedule ensembles, split kernels for the others"},
         "p50_cycle_ms": head["p50_cycle_ms"], "p99_cycle_ms": head["p99_cycle_ms"],
         "group": head, "mixed": dict(out["mixed"],
                                      speedup_vs_fp32=out["mixed"]["value"] / head["value"]),

@@ -234,17 +234,19 @@ int letkf_cycle(letkf_handle *h, int32_t nsteps, const float *yo, int32_t where)
  * Several experiments (handles) of one device analysed as one batch, e.g. ensembles of
  * different sizes over the same or different grids and observation networks.  Per handle the
  * observation operator, the transposes and the localized Gram matrices run as in
- * letkf_analyze; the eigensolve, transform and update of the grid points of all handles run as
- * one persistent launch per column class (k <= 32, <= 64, <= 128) in which every warp takes the
- * next grid point from a global counter, so points with any number of local observations
- * (including none) and matrices of every order balance over the GPU.  The eigensolve is the
- * fused schedule of each point (the result of every handle equals its LETKF_EIG_FUSED
- * letkf_analyze bit for bit).
+ * letkf_analyze.  For the handles on the LETKF_EIG_FUSED schedule the eigensolve, transform
+ * and update of all their grid points run as one persistent launch per column class (k <= 32,
+ * <= 64, <= 128) in which every warp takes the next grid point from a global counter, so
+ * points with any number of local observations (including none) and matrices of every order
+ * balance over the GPU.  Handles on the split schedules run their own split kernels in the
+ * same stream.  Each handle's result equals its letkf_analyze on its schedule bit for bit.  A
+ * handle on LETKF_EIG_AUTO that has not picked yet picks at its first group analysis (as at
+ * its first letkf_analyze); a group cycle that contains such a handle runs without capture.
  *   hs     n distinct handles of one device, 1 <= n <= 8; the work runs on hs[0]'s stream,
  *          ordered after each handle's earlier work and before its later work
  *   yo     n observation vectors (where = LETKF_HOST/DEVICE), yo[i] of handle hs[i]
  * letkf_group_cycle(hs, n, nsteps, yo, where): every handle's lbm_forecast(nsteps) and the
- * group analysis, captured once per (membership, state buffers, nsteps) into a CUDA graph
+ * group analysis, captured once per (membership, schedules, state buffers, nsteps) into a CUDA graph
  * kept by hs[0] (at most 8 such graphs, the oldest dropped) and replayed.  Phase timing of the
  * handles is not recorded by group calls.  Device errors are reported by each handle's
  * letkf_sync. */

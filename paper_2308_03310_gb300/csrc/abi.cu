@@ -209,7 +209,7 @@ struct letkf_handle {
     unsigned long long serial = 0;  // unique per handle of the process (group graph keys)
     struct GroupGraph {             // captured group cycles led by this handle
         std::vector<unsigned long long> members;
-        std::vector<int> cur;
+        std::vector<int> cur, sched;
         int nsteps = -1;
         int kernels = 0;
         cudaGraphExec_t exec = nullptr;
@@ -605,8 +605,11 @@ int group_fence(letkf_handle *const *hs, int n, bool join) {
 }
 
 // The group's work on the group stream (inside a GroupScope): optional forecasts, then per
-// handle the observation operator and transpose; per chunk round every handle's Gram chunk and
-// one grouped eigen launch per column class over all of them; the transposes back.
+// handle the observation operator and transpose; per chunk round every handle's Gram chunk,
+// the split eigensolve of the handles on the SPLIT schedule, and one grouped eigen launch per
+// column class over the handles on the FUSED schedule; the transposes back.  A handle still on
+// AUTO picks its schedule at its first Gram chunk (eager calls only: the callers do not
+// capture while a handle has yet to pick).
 int enqueue_group(letkf_handle *const *hs, int n, int nsteps) {
     letkf_handle *h = hs[0];
     const int *blocks = nullptr;
@@ -632,9 +635,17 @@ int enqueue_group(letkf_handle *const *hs, int n, int nsteps) {
             if (y0 >= g->cfg.ny) continue;
             const int y1 = std::min(g->cfg.ny, y0 + g->plan.chunk_rows);
             if ((rc = enqueue_gram_chunk(g, r, y0, y1))) return rc;
-            segs[m++] = eig_args(g, y0, y1);
+            if (g->eig_schedule == LETKF_EIG_AUTO && (rc = tune_eig_schedule(g, y0, y1)))
+                return rc;
+            if (g->eig_schedule == LETKF_EIG_FUSED) {
+                segs[m++] = eig_args(g, y0, y1);
+            } else {
+                const cudaError_t e = lk::launch_eigen_split(eig_args(g, y0, y1), g->eig_split,
+                                                             h->stream);
+                if (e != cudaSuccess) return cuda_fail(g, e);
+            }
         }
-        CK(lk::launch_eigen_group(segs, m, h->status + 16, blocks, h->stream));
+        if (m > 0) CK(lk::launch_eigen_group(segs, m, h->status + 16, blocks, h->stream));
     }
     for (int i = 0; i < n; ++i) {
         letkf_handle *g = hs[i];
@@ -1128,16 +1139,25 @@ int letkf_group_cycle(letkf_handle *const *hs, int32_t n, int32_t nsteps, const 
         for (int i = 0; i < n && !rc; ++i)
             rc = copy_in(hs[i], hs[i]->yo, yo[i], (size_t)hs[i]->plan.LV * sizeof(float), where);
         if (rc) return rc;
-        // the captured graph of this membership, state buffers and step count
+        bool pending = false;  // a handle still picks its eigensolve schedule: no capture
+        for (int i = 0; i < n; ++i) pending |= hs[i]->eig_schedule == LETKF_EIG_AUTO;
+        if (pending) {
+            if ((rc = enqueue_group(hs, n, nsteps))) return rc;
+            h->stats.cycle_kernels = 0;
+            return group_fence(hs, n, true);
+        }
+        // the captured graph of this membership, schedules, state buffers and step count
         std::vector<unsigned long long> ids(n);
-        std::vector<int> cur(n);
+        std::vector<int> cur(n), sched(n);
         for (int i = 0; i < n; ++i) {
             ids[i] = hs[i]->serial;
             cur[i] = hs[i]->cur;
+            sched[i] = hs[i]->eig_schedule;
         }
         letkf_handle::GroupGraph *gg = nullptr;
         for (auto &e : h->group_graphs)
-            if (e.members == ids && e.cur == cur && e.nsteps == nsteps) gg = &e;
+            if (e.members == ids && e.cur == cur && e.sched == sched && e.nsteps == nsteps)
+                gg = &e;
         if (!gg) {
             if (h->group_graphs.size() >= 8) {  // bounded cache: drop the oldest
                 if (h->group_graphs.front().exec) cudaGraphExecDestroy(h->group_graphs.front().exec);
@@ -1156,6 +1176,7 @@ int letkf_group_cycle(letkf_handle *const *hs, int32_t n, int32_t nsteps, const 
             letkf_handle::GroupGraph e;
             e.members = ids;
             e.cur = cur;
+            e.sched = sched;
             e.nsteps = nsteps;
             e.kernels = graph_kernel_nodes(g);
             const cudaError_t ei = cudaGraphInstantiate(&e.exec, g, 0);
