@@ -23,30 +23,59 @@
 namespace lk {
 namespace {
 
+// c_q . v for a lattice direction known at compile time (no multiplications by 0 or +-1).
+template <int CX, int CY>
+__device__ __forceinline__ float cdot(float vx, float vy) {
+    if constexpr (CX == 0) return CY > 0 ? vy : -vy;
+    else if constexpr (CY == 0) return CX > 0 ? vx : -vx;
+    else return (CX > 0 ? vx : -vx) + (CY > 0 ? vy : -vy);
+}
+
+// Direction Q (0..3) and its opposite 8 - Q: the equilibrium of the pair from its symmetric
+// and antisymmetric parts, w (a +- b) with a = base + 4.5 rho (c.u)^2 and b = 3 rho c.u, then
+// the BGK relaxation and the force term +- 3 w c.F.
+template <bool kForce, int Q>
+__device__ __forceinline__ void collide_pair(const float (&g)[NV], float ux, float uy, float base,
+                                             float r3, float r45, float f3x, float f3y,
+                                             float omega, float (&out)[NV]) {
+    constexpr float w = wq(Q);
+    const float cu = cdot<cx(Q), cy(Q)>(ux, uy);
+    const float a = fmaf(r45 * cu, cu, base);
+    const float b = r3 * cu;
+    const float gp = w * (a + b), gm = w * (a - b);  // equilibria of Q and 8 - Q
+    float sp = fmaf(omega, gp - g[Q], g[Q]);
+    float sm = fmaf(omega, gm - g[8 - Q], g[8 - Q]);
+    if (kForce) {
+        const float fq = w * cdot<cx(Q), cy(Q)>(f3x, f3y);
+        sp += fq;
+        sm -= fq;
+    }
+    out[Q] = sp;
+    out[8 - Q] = sm;
+}
+
 // BGK collision with the body-force source for one node: post-collision populations out[q]
-// from the node's deviations g[q] (Eq. 1, Sec. II-A).
+// from the node's deviations g[q] (Eq. 1, Sec. II-A).  f^eq_q = w_q (rho + rho (3 c.u +
+// 4.5 (c.u)^2 - 1.5 |u|^2)) written for the deviations: geq_q = w_q (drho - 1.5 rho |u|^2 +
+// 4.5 rho (c.u)^2 + 3 rho c.u), evaluated per pair of opposite directions (q, 8 - q), whose
+// terms differ only in the sign of c.u.
 template <bool kForce>
 __device__ __forceinline__ void collide(const float (&g)[NV], float fx, float fy, float omega,
                                         float (&out)[NV]) {
-    float drho = 0.0f, jx = 0.0f, jy = 0.0f;
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-        drho += g[q];
-        if (cx(q) != 0) jx += cx(q) > 0 ? g[q] : -g[q];
-        if (cy(q) != 0) jy += cy(q) > 0 ? g[q] : -g[q];
-    }
+    const float drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+    const float jx = ((g[2] + g[5]) + g[8]) - ((g[0] + g[3]) + g[6]);
+    const float jy = ((g[6] + g[7]) + g[8]) - ((g[0] + g[1]) + g[2]);
     const float rho = 1.0f + drho;
-    const float rinv = 1.0f / rho;
+    const float rinv = __frcp_rn(rho);
     const float ux = jx * rinv, uy = jy * rinv;
-    const float usq = 1.5f * (ux * ux + uy * uy);
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-        const float cu = (float)cx(q) * ux + (float)cy(q) * uy;
-        const float geq = wq(q) * (drho + rho * (3.0f * cu + 4.5f * cu * cu - usq));
-        float gs = g[q] - omega * (g[q] - geq);
-        if (kForce) gs += 3.0f * wq(q) * ((float)cx(q) * fx + (float)cy(q) * fy);
-        out[q] = gs;
-    }
+    const float base = fmaf(-1.5f * rho, fmaf(ux, ux, uy * uy), drho);
+    const float r3 = 3.0f * rho, r45 = 4.5f * rho;
+    const float f3x = 3.0f * fx, f3y = 3.0f * fy;
+    collide_pair<kForce, 0>(g, ux, uy, base, r3, r45, f3x, f3y, omega, out);
+    collide_pair<kForce, 1>(g, ux, uy, base, r3, r45, f3x, f3y, omega, out);
+    collide_pair<kForce, 2>(g, ux, uy, base, r3, r45, f3x, f3y, omega, out);
+    collide_pair<kForce, 3>(g, ux, uy, base, r3, r45, f3x, f3y, omega, out);
+    out[4] = fmaf(omega, wq(4) * base - g[4], g[4]);
 }
 
 template <bool kForce>
@@ -166,13 +195,19 @@ __global__ void __launch_bounds__(NT, MINB) lbm_2step_kernel(const float *__rest
             fy = F.y;
         }
         collide<kForce>(g, fx, fy, omega, out);
+        // targets (bx - 1 + c_x, by - 1 + c_y): inside the tile and the grid per axis
+        const int tx0 = bx - 1, ty0 = by - 1;
+        bool vx[3], vy[3];
 #pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            const int tx = bx - 1 + cx(q), ty = by - 1 + cy(q);
-            const int gx = x0 + tx, gy = y0 + ty;
-            if (tx >= 0 && tx < TX && ty >= 0 && ty < TY && gx < nx && gy < ny)
-                __stcs(dst + q * npts + (size_t)gy * nx + gx, out[q]);
+        for (int c = 0; c < 3; ++c) {
+            vx[c] = (unsigned)(tx0 + c - 1) < (unsigned)TX && x0 + tx0 + c - 1 < nx;
+            vy[c] = (unsigned)(ty0 + c - 1) < (unsigned)TY && y0 + ty0 + c - 1 < ny;
         }
+        const long long at = (long long)(y0 + ty0) * nx + (x0 + tx0);
+#pragma unroll
+        for (int q = 0; q < NV; ++q)
+            if (vx[cx(q) + 1] && vy[cy(q) + 1])
+                __stcs(dst + at + (long long)q * (long long)npts + cy(q) * nx + cx(q), out[q]);
     }
 }
 
