@@ -311,6 +311,21 @@ int letkf_local_analysis_noalloc(int32_t npts, int32_t k, int32_t lmaxv, const f
 int letkf_eigh_batch(int32_t npts, int32_t k, float *q, float *eigval, float *evec,
                      int32_t refine, void *stream);
 
+/* letkf_eigh_batch on the split schedule (the analysis' LETKF_EIG_SPLIT: tridiagonalization one
+ * warp per matrix, the QL recurrence one thread per matrix with its rotations recorded, then
+ * the rotations replayed onto the eigenvectors and the back-transform one warp per matrix;
+ * a matrix whose record would overflow is recomputed by the one-warp schedule).  Same
+ * arguments, results and return codes as letkf_eigh_batch (the eigenpairs agree to FP32
+ * rounding), with the scratch in a caller-owned device workspace instead of the static array:
+ *   workspace        device buffer of at least letkf_eigh_workspace_bytes(npts, k) bytes,
+ *                    256-byte aligned; its contents on entry do not matter and are overwritten
+ *   workspace_bytes  its size
+ * Returns LETKF_ENOMEM when the workspace is too small or misaligned.  Calls that share a
+ * workspace race unless they are ordered on one stream. */
+size_t letkf_eigh_workspace_bytes(int32_t npts, int32_t k);
+int letkf_eigh_batch_ws(int32_t npts, int32_t k, float *q, float *eigval, float *evec,
+                        int32_t refine, void *workspace, size_t workspace_bytes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

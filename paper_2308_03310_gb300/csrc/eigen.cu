@@ -1104,7 +1104,7 @@ __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS) eig_tridiag_kernel(Eig
     const int warps_per_block = blockDim.x >> 5;
     const int nw = gridDim.x * warps_per_block;
     for (int lp = blockIdx.x * warps_per_block + wib; lp < a.npts; lp += nw) {
-        if (a.nloc[lp] == 0) continue;
+        if (a.nloc && a.nloc[lp] == 0) continue;
         float *Ag = a.gram + (size_t)lp * k * k;
         load_q<NC>(Ag, S, k, ld, lane, a.diag);
         if constexpr (NC == 1)  // at k <= 64 (212 registers) the shared-memory form is faster
@@ -1136,7 +1136,7 @@ __global__ void __launch_bounds__(kQlThreads) eig_ql_kernel(EigArgs a, EigSplit 
     }
     __syncthreads();
     if (lp >= a.npts) return;
-    if (a.nloc[lp] == 0) {
+    if (a.nloc && a.nloc[lp] == 0) {
         for (int t = 0; t < k; ++t) a.eigval[(size_t)lp * k + t] = a.diag;
         sp.nrot[lp] = 0;
         return;
@@ -1399,10 +1399,11 @@ __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB_VEC)
     const int nw = gridDim.x * warps_per_block;
     for (int lp = blockIdx.x * warps_per_block + wib; lp < a.npts; lp += nw) {
         const int nrec = sp.nrot[lp];
-        if (a.nloc[lp] == 0 || nrec < 0) continue;  // unchanged / recomputed by the fused kernel
+        // unchanged / recomputed by the fused kernel
+        if ((a.nloc && a.nloc[lp] == 0) || nrec < 0) continue;
         float *Ag = a.gram + (size_t)lp * k * k;
         float xbar[NV];
-        float *X = load_forecast<NC>(a, lp, B, k, ld, lane, xbar);
+        float *X = a.x ? load_forecast<NC>(a, lp, B, k, ld, lane, xbar) : nullptr;
         for (int t = lane; t < k; t += 32) taus[t] = sp.taus[(size_t)lp * k + t];
         const float2 *rec = sp.rot + (size_t)lp * sp.rcap;
         if constexpr (NC <= 2) {
@@ -1472,7 +1473,7 @@ __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB_VEC)
             }
         }
         if (a.evec) store_vectors<NC>(Z, ld, a.evec + (size_t)lp * k * k, k, lane);
-        transform_update<NC>(X, B, Z, dr, xbar, k, ld, lane, a.status);
+        if (X) transform_update<NC>(X, B, Z, dr, xbar, k, ld, lane, a.status);
     }
 }
 

@@ -236,3 +236,83 @@ extern "C" int letkf_eigh_batch(int32_t npts, int32_t k, float *q, float *eigval
     if (bits & lk::ST_NOTCONV) return LETKF_ENOTCONV;
     return LETKF_OK;
 }
+
+namespace {
+
+// Split-schedule scratch for npts matrices of order k, each array 256-byte aligned.
+struct EighLayout {
+    size_t de, taus, rot, nrot, list, count, status, total;
+    int rcap;
+};
+
+EighLayout eigh_layout(int32_t npts, int32_t k) {
+    EighLayout l{};
+    l.rcap = k * k + 4 * k;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return at;
+    };
+    const size_t n = (size_t)npts;
+    l.de = take(n * k * sizeof(float2));
+    l.taus = take(n * k * sizeof(float));
+    l.rot = take(n * (size_t)l.rcap * sizeof(float2));
+    l.nrot = take(n * sizeof(int));
+    l.list = take((n + 4) * sizeof(int));
+    l.count = take(sizeof(int));
+    l.status = take(sizeof(int));
+    l.total = off;
+    return l;
+}
+
+}  // namespace
+
+extern "C" size_t letkf_eigh_workspace_bytes(int32_t npts, int32_t k) {
+    if (npts < 0 || k < 2 || k > 128) return 0;
+    return eigh_layout(npts, k).total;
+}
+
+extern "C" int letkf_eigh_batch_ws(int32_t npts, int32_t k, float *q, float *eigval, float *evec,
+                                   int32_t refine, void *workspace, size_t workspace_bytes,
+                                   void *stream) {
+    if (npts < 0 || k < 2 || k > 128 || (refine != 0 && refine != 1)) return LETKF_EINVAL;
+    if (npts == 0) return LETKF_OK;
+    if (!q || !eigval) return LETKF_EINVAL;
+    const EighLayout l = eigh_layout(npts, k);
+    if (!workspace || workspace_bytes < l.total || ((uintptr_t)workspace & 255))
+        return LETKF_ENOMEM;
+    unsigned char *ws = static_cast<unsigned char *>(workspace);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    lk::EigSplit sp;
+    sp.de = reinterpret_cast<float2 *>(ws + l.de);
+    sp.taus = reinterpret_cast<float *>(ws + l.taus);
+    sp.rot = reinterpret_cast<float2 *>(ws + l.rot);
+    sp.nrot = reinterpret_cast<int *>(ws + l.nrot);
+    sp.list = reinterpret_cast<int *>(ws + l.list);
+    sp.list_count = reinterpret_cast<int *>(ws + l.count);
+    sp.rcap = l.rcap;
+    int *status = reinterpret_cast<int *>(ws + l.status);
+    if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return LETKF_ECUDA;
+    lk::EigArgs a;
+    a.k = k;
+    a.diag = 0.0f;           // the matrices are Q themselves
+    a.gram = q;
+    a.npts = npts;
+    a.eigval = eigval;
+    a.evec = evec;
+    a.refine = refine;
+    a.refine_tau = 1e-6f;
+    a.status = status;       // no counts, no forecast blocks: eigenpairs only
+    if (lk::eigen_prepare(k, &a.max_blocks) != cudaSuccess ||
+        lk::eigen_split_prepare(k, &sp) != cudaSuccess)
+        return LETKF_ECUDA;
+    if (lk::launch_eigen_split(a, sp, s) != cudaSuccess) return LETKF_ECUDA;
+    int bits = 0;
+    if (cudaMemcpyAsync(&bits, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return LETKF_ECUDA;
+    if (bits & lk::ST_NONFINITE) return LETKF_ENONFINITE;
+    if (bits & lk::ST_NOTCONV) return LETKF_ENOTCONV;
+    return LETKF_OK;
+}

@@ -46,8 +46,8 @@ EXPORTED = (
     "letkf_get_stats", "letkf_enable_timing", "letkf_get_timings", "letkf_set_state", "letkf_get_state", "letkf_set_deviation",
     "letkf_get_deviation", "letkf_set_macro", "lbm_forecast",
     "letkf_get_obs", "letkf_analyze", "letkf_analyze_probe", "letkf_cycle",
-    "letkf_local_analysis_noalloc", "letkf_eigh_batch", "letkf_group_analyze",
-    "letkf_group_cycle",
+    "letkf_local_analysis_noalloc", "letkf_eigh_batch", "letkf_eigh_workspace_bytes",
+    "letkf_eigh_batch_ws", "letkf_group_analyze", "letkf_group_cycle",
 )
 
 LETKF_NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -129,6 +129,9 @@ def load(path: str = LIB):
         "letkf_local_analysis_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, P, P,
                                                    C.c_float, P, P]),
         "letkf_eigh_batch": (C.c_int, [C.c_int32, C.c_int32, P, P, P, C.c_int32, P]),
+        "letkf_eigh_workspace_bytes": (C.c_size_t, [C.c_int32, C.c_int32]),
+        "letkf_eigh_batch_ws": (C.c_int, [C.c_int32, C.c_int32, P, P, P, C.c_int32, P,
+                                          C.c_size_t, P]),
         "letkf_group_analyze": (C.c_int, [P, P, C.c_int32, C.c_int32]),
         "letkf_group_cycle": (C.c_int, [P, C.c_int32, C.c_int32, P, C.c_int32]),
     }
@@ -246,6 +249,20 @@ def letkf_eigh_batch(npts, k, q_ptr, eigval_ptr, evec_ptr, refine, stream):
     return load().letkf_eigh_batch(int(npts), int(k), C.c_void_p(q_ptr), C.c_void_p(eigval_ptr),
                                    C.c_void_p(evec_ptr or None), int(refine),
                                    C.c_void_p(stream))
+
+
+def letkf_eigh_workspace_bytes(npts, k):
+    """Device bytes letkf_eigh_batch_ws needs for npts matrices of order k (0: invalid)."""
+    return int(load().letkf_eigh_workspace_bytes(int(npts), int(k)))
+
+
+def letkf_eigh_batch_ws(npts, k, q_ptr, eigval_ptr, evec_ptr, refine, ws_ptr, ws_bytes, stream):
+    """letkf_eigh_batch on the split schedule with a caller workspace (device pointers).
+    Returns the status code without raising."""
+    return load().letkf_eigh_batch_ws(int(npts), int(k), C.c_void_p(q_ptr),
+                                      C.c_void_p(eigval_ptr), C.c_void_p(evec_ptr or None),
+                                      int(refine), C.c_void_p(ws_ptr or None), int(ws_bytes),
+                                      C.c_void_p(stream))
 
 
 def _group_arrays(exps, yos):

@@ -1,4 +1,5 @@
-"""letkf_eigh_batch: the analysis' batched symmetric eigensolver against numpy.linalg.eigh.
+"""letkf_eigh_batch (one warp per matrix) and letkf_eigh_batch_ws (the split schedule, caller
+workspace): the analysis' batched symmetric eigensolver against numpy.linalg.eigh.
 
 Pins (FP64 eigh of the same FP32 matrices is the reference):
   * eigenvalues within 1e-5 of the largest magnitude, orthonormal eigenvectors (max entry of
@@ -39,7 +40,10 @@ def _from_spectrum(lams, seed):
     return ((Q + Q.T) / 2).astype(np.float32)
 
 
-def _solve(Q, refine):
+SOLVERS = ["fused", "split"]
+
+
+def _solve(Q, refine, solver="fused"):
     import torch
     n, k, _ = Q.shape
     dev = torch.device("cuda")
@@ -47,8 +51,16 @@ def _solve(Q, refine):
     lam = torch.empty((n, k), dtype=torch.float32, device=dev)
     vec = torch.empty((n, k, k), dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
-    rc = L.letkf_eigh_batch(n, k, tq.data_ptr(), lam.data_ptr(), vec.data_ptr(), refine,
-                            torch.cuda.current_stream().cuda_stream)
+    stream = torch.cuda.current_stream().cuda_stream
+    if solver == "fused":
+        rc = L.letkf_eigh_batch(n, k, tq.data_ptr(), lam.data_ptr(), vec.data_ptr(), refine,
+                                stream)
+    else:
+        nb = L.letkf_eigh_workspace_bytes(n, k)
+        ws = torch.empty(nb + 256, dtype=torch.uint8, device=dev)
+        base = (ws.data_ptr() + 255) // 256 * 256
+        rc = L.letkf_eigh_batch_ws(n, k, tq.data_ptr(), lam.data_ptr(), vec.data_ptr(), refine,
+                                   base, nb, stream)
     assert rc == L.LETKF_OK, L.strerror(rc)
     return tq.cpu().numpy(), lam.cpu().numpy().astype(np.float64), \
         vec.cpu().numpy().astype(np.float64)
@@ -85,23 +97,25 @@ def _matfun_errors(Q, lam, vec):
 
 @pytest.mark.parametrize("k", [2, 5, 31, 32, 33, 64, 100, 128])
 @pytest.mark.parametrize("refine", [0, 1])
-def test_eigenpairs_match_eigh(k, refine):
+@pytest.mark.parametrize("solver", SOLVERS)
+def test_eigenpairs_match_eigh(k, refine, solver):
     Q = _random_spd(24, k, 1000 + k)
-    Qout, lam, vec = _solve(Q, refine)
+    Qout, lam, vec = _solve(Q, refine, solver)
     _check_pairs(Q, lam, vec)
     iu = np.triu_indices(k)
     assert np.array_equal(Qout[:, iu[0], iu[1]], Q[:, iu[0], iu[1]])
 
 
 @pytest.mark.parametrize("k", [32, 64, 128])
-def test_degenerate_spectrum(k):
+@pytest.mark.parametrize("solver", SOLVERS)
+def test_degenerate_spectrum(k, solver):
     rng = np.random.default_rng(7 + k)
     Q = np.empty((8, k, k), np.float32)
     for p in range(8):
         Y = rng.standard_normal((k, 3)) * 0.5
         Q[p] = ((k - 1) * np.eye(k) + Y @ Y.T).astype(np.float32)
     for refine in (0, 1):
-        _, lam, vec = _solve(Q, refine)
+        _, lam, vec = _solve(Q, refine, solver)
         _check_pairs(Q, lam, vec)
 
 
@@ -127,7 +141,8 @@ def test_refinement_on_clustered_spectra(k):
 
 
 @pytest.mark.parametrize("k,rank,top", [(128, 84, 2000.0), (64, 40, 5000.0), (32, 20, 1e4)])
-def test_small_cluster_next_to_large_eigenvalues_converges(k, rank, top):
+@pytest.mark.parametrize("solver", SOLVERS)
+def test_small_cluster_next_to_large_eigenvalues_converges(k, rank, top, solver):
     # (k-1) I + a rank-r term with eigenvalues up to `top`: k - r equal eigenvalues beside
     # large ones.  QL must deflate the equal block although every sweep through the large
     # entries leaves rounding of order eps ||Q|| on its couplings (threshold eps ||T||).
@@ -138,5 +153,25 @@ def test_small_cluster_next_to_large_eigenvalues_converges(k, rank, top):
         lam = np.geomspace(1.0, top, rank)
         Q[p] = ((k - 1) * np.eye(k) + (U * lam) @ U.T).astype(np.float32)
     for refine in (0, 1):
-        _, lam, vec = _solve(Q, refine)                 # LETKF_OK, not ENOTCONV
+        _, lam, vec = _solve(Q, refine, solver)         # LETKF_OK, not ENOTCONV
         _check_pairs(Q, lam, vec)
+
+
+def test_split_solver_rejects_a_short_or_misaligned_workspace():
+    import torch
+    n, k = 8, 32
+    dev = torch.device("cuda")
+    q = torch.eye(k, device=dev).repeat(n, 1, 1).contiguous()
+    lam = torch.empty((n, k), device=dev)
+    nb = L.letkf_eigh_workspace_bytes(n, k)
+    assert nb > 8 * n * k * k
+    ws = torch.empty(nb + 512, dtype=torch.uint8, device=dev)
+    base = (ws.data_ptr() + 255) // 256 * 256
+    s = torch.cuda.current_stream().cuda_stream
+    assert L.letkf_eigh_batch_ws(n, k, q.data_ptr(), lam.data_ptr(), 0, 0, base, nb - 1, s) \
+        == L.LETKF_ENOMEM
+    assert L.letkf_eigh_batch_ws(n, k, q.data_ptr(), lam.data_ptr(), 0, 0, base + 4, nb, s) \
+        == L.LETKF_ENOMEM
+    assert L.letkf_eigh_batch_ws(n, k, q.data_ptr(), lam.data_ptr(), 0, 0, base, nb, s) \
+        == L.LETKF_OK
+    assert np.allclose(lam.cpu().numpy(), 1.0)
