@@ -1383,9 +1383,10 @@ __device__ __forceinline__ void replay_in_registers(const float2 *__restrict__ r
 }
 
 // (3) vectors, transform and update, warp per matrix: Z = I, the recorded rotations replayed
-// onto Z (each lane its own columns, the carried row in registers), V = H Z, then the
-// fused schedule's transform and update.
-template <int NC>
+// onto Z, V = H Z, then the fused schedule's transform and update (kUpdate; without it, the
+// eigenpairs only, for letkf_eigh_batch_ws: a separate instantiation, so that the analysis
+// path carries no extra registers).
+template <int NC, bool kUpdate>
 __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB_VEC)
     eig_vec_kernel(EigArgs a, EigSplit sp) {
     extern __shared__ float smem[];
@@ -1403,7 +1404,7 @@ __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB_VEC)
         if ((a.nloc && a.nloc[lp] == 0) || nrec < 0) continue;
         float *Ag = a.gram + (size_t)lp * k * k;
         float xbar[NV];
-        float *X = a.x ? load_forecast<NC>(a, lp, B, k, ld, lane, xbar) : nullptr;
+        float *X = kUpdate ? load_forecast<NC>(a, lp, B, k, ld, lane, xbar) : nullptr;
         for (int t = lane; t < k; t += 32) taus[t] = sp.taus[(size_t)lp * k + t];
         const float2 *rec = sp.rot + (size_t)lp * sp.rcap;
         if constexpr (NC <= 2) {
@@ -1473,7 +1474,7 @@ __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB_VEC)
             }
         }
         if (a.evec) store_vectors<NC>(Z, ld, a.evec + (size_t)lp * k * k, k, lane);
-        if (X) transform_update<NC>(X, B, Z, dr, xbar, k, ld, lane, a.status);
+        if constexpr (kUpdate) transform_update<NC>(X, B, Z, dr, xbar, k, ld, lane, a.status);
     }
 }
 
@@ -1516,10 +1517,15 @@ cudaError_t prepare_split_nc(int k, EigSplit *sp) {
                                   (size_t)tri_smem_floats(kmax_of(NC)) * sizeof(float) * warps,
                                   &sp->grid_tri);
     if (e != cudaSuccess) return e;
-    e = occupancy<NC>((const void *)eig_vec_kernel<NC>, warps,
+    e = occupancy<NC>((const void *)eig_vec_kernel<NC, true>, warps,
                       (size_t)vec_smem_floats(k) * sizeof(float) * warps,
                       (size_t)vec_smem_floats(kmax_of(NC)) * sizeof(float) * warps,
                       &sp->grid_vec);
+    if (e != cudaSuccess) return e;
+    int unused = 0;
+    e = occupancy<NC>((const void *)eig_vec_kernel<NC, false>, warps,
+                      (size_t)vec_smem_floats(k) * sizeof(float) * warps,
+                      (size_t)vec_smem_floats(kmax_of(NC)) * sizeof(float) * warps, &unused);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(eig_ql_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(128 * kQlThreads * sizeof(float2)));
@@ -1548,8 +1554,14 @@ cudaError_t launch_split_nc(const EigArgs &a, const EigSplit &sp, cudaStream_t s
                              (size_t)tri_smem_floats(a.k) * sizeof(float) * warps, s>>>(a, sp);
     eig_ql_kernel<<<(unsigned)((a.npts + kQlThreads - 1) / kQlThreads), kQlThreads,
                     (size_t)a.k * kQlThreads * sizeof(float2), s>>>(a, sp);
-    eig_vec_kernel<NC><<<grid_for(sp.grid_vec, a.npts, warps), 32 * warps,
-                         (size_t)vec_smem_floats(a.k) * sizeof(float) * warps, s>>>(a, sp);
+    if (a.x)
+        eig_vec_kernel<NC, true><<<grid_for(sp.grid_vec, a.npts, warps), 32 * warps,
+                                   (size_t)vec_smem_floats(a.k) * sizeof(float) * warps, s>>>(a,
+                                                                                         sp);
+    else
+        eig_vec_kernel<NC, false><<<grid_for(sp.grid_vec, a.npts, warps), 32 * warps,
+                                    (size_t)vec_smem_floats(a.k) * sizeof(float) * warps, s>>>(a,
+                                                                                          sp);
     // matrices whose rotation record overflowed: the fused kernel over the list
     EigArgs f = a;
     f.list = sp.list;
