@@ -319,9 +319,62 @@ def spin_up(w, device):
     members = torch.empty((w.k, 9, w.ny, w.nx), dtype=torch.float32, device=device)
     torch.cuda.synchronize(device)
     L.letkf_get_deviation(spin.h, members.data_ptr(), 0, w.k, L.LETKF_DEVICE)
+    truth = torch.empty((1, 9, w.ny, w.nx), dtype=torch.float32, device=device)
+    L.letkf_get_deviation(spin.h, truth.data_ptr(), w.k, 1, L.LETKF_DEVICE)
     torch.cuda.synchronize(device)
     assert spin.sync() == 0
-    return spin, members, (net, var, kw)
+    return spin, members, (net, var, kw), truth
+
+
+def rmse_run(w, members, truth, setup, device, precision, ncycles, seed_offset=0):
+    """Assimilation quality against the synthetic truth (OSSE, Sec. V): the spun-up ensemble and
+    its truth (an auxiliary member, advanced but never analysed) cycled ncycles times with
+    noisy observations of the truth.  Per cycle the velocity RMSE of the ensemble mean against
+    the truth over the whole grid, before (forecast) and after (analysis) the update, and the
+    ensemble spread.  Diagnostics only: the moments are formed with torch from the device
+    state after each phase."""
+    import numpy as np
+    import torch
+
+    from paper_2308_03310_gb300 import letkf as L
+    net, var, kw = setup
+    k = w.k
+    exp = L.Experiment(w.nx, w.ny, k, w.tau, net, var, n_aux=1, device=device,
+                       precision=precision, **kw)
+    torch.cuda.synchronize(device)
+    L.letkf_set_deviation(exp.h, members.data_ptr(), 0, k, L.LETKF_DEVICE)
+    L.letkf_set_deviation(exp.h, truth.data_ptr(), k, 1, L.LETKF_DEVICE)
+    buf = torch.empty((k + 1, 9, w.ny, w.nx), dtype=torch.float32, device=device)
+    LV = exp.L * exp.V
+
+    def diag():
+        L.letkf_get_deviation(exp.h, buf.data_ptr(), 0, k + 1, L.LETKF_DEVICE)
+        torch.cuda.synchronize(device)
+        g = buf.double()
+        rho = 1.0 + g.sum(1)
+        ux = (g[:, [2, 5, 8]].sum(1) - g[:, [0, 3, 6]].sum(1)) / rho
+        uy = (g[:, [6, 7, 8]].sum(1) - g[:, [0, 1, 2]].sum(1)) / rho
+        err = (ux[:k].mean(0) - ux[k]) ** 2 + (uy[:k].mean(0) - uy[k]) ** 2
+        spread = ux[:k].var(0) + uy[:k].var(0)
+        return float(err.mean().sqrt()), float(spread.mean().sqrt())
+
+    fc, an, sp = [], [], []
+    for c in range(ncycles):
+        exp.forecast(w.steps_per_cycle)
+        y = exp.get_obs()[k] + w.obs_noise(seed_offset + 5000 + c, LV)
+        e, s_ = diag()
+        fc.append(e)
+        sp.append(s_)
+        exp.analyze(y.astype(np.float32))
+        an.append(diag()[0])
+    rc = exp.sync()
+    exp.close()
+    if rc:
+        raise RuntimeError(f"RMSE cycles failed: {L.strerror(rc)}")
+    late = slice(ncycles // 2, ncycles)
+    return {"forecast_rmse": float(np.mean(fc[late])), "analysis_rmse": float(np.mean(an[late])),
+            "forecast_spread": float(np.mean(sp[late])), "first_forecast_rmse": fc[0],
+            "analysis_below_forecast_fraction": float(np.mean(np.array(an) < np.array(fc)))}
 
 
 def make_experiment(w, members, setup, device, precision, eig_schedule=0, chunk_bytes=0):
@@ -491,7 +544,7 @@ def main(argv=None):
     w = synth.WORKLOADS[args.workload]
     steps = args.steps if args.steps is not None else DEFAULT_STEPS.get(args.workload, 20)
     warm = max(3, args.warmup)
-    spin, members, setup = spin_up(w, device)
+    spin, members, setup, truth = spin_up(w, device)
     yos = nature_observations(spin, w, warm + 2 * steps, seed_offset=1000 * rank)
     spin.close()
     forms = {"fp32": [L.LETKF_FP32], "mixed": [L.LETKF_MIXED],
@@ -501,6 +554,13 @@ def main(argv=None):
     results = [measure(w, members, setup, yos, device, prec, steps, warm, world, sched, chunk)
                for prec in forms]
     head = results[0]
+    ncyc = 20
+    rmse = {"cycles": ncyc, "averaged_over": f"cycles {ncyc // 2}..{ncyc - 1}",
+            "unit": "lattice velocity", "field": "(u, v) of the ensemble mean vs the truth, all "
+                                                   "grid points"}
+    for prec in forms:
+        rmse["mixed" if prec == L.LETKF_MIXED else "fp32"] = rmse_run(
+            w, members, truth, setup, device, prec, ncyc, seed_offset=1000 * rank)
     line = {
         "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": steps,
         "warmup": warm, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
@@ -513,6 +573,7 @@ def main(argv=None):
         "lbm": head["lbm"],
         "clocks": head["clocks"],
         "local_obs": head["local_obs"],
+        "rmse_vs_truth": rmse,
         "mixed": None,
     }
     if len(results) > 1:
