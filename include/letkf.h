@@ -51,6 +51,11 @@ extern "C" {
 
 #define LETKF_LOC_NONE  0      /* G = 1 for every observation ("infinite")    */
 #define LETKF_LOC_GAUSS 1      /* G = exp(-d^2/(2 r^2)) for d^2 < cutoff^2    */
+#define LETKF_LOC_GC    2      /* G = GC(d / c), Gaspari & Cohn (1999) Eq. 4.10, the paper's
+                                  localization (Sec. II-B): the fifth-order piecewise rational
+                                  function, half-width c = sqrt(10/3) r, zero from d = 2c on
+                                  (the default cutoff of LETKF_LOC_GAUSS); the cutoff is
+                                  capped at 2c, so every local observation has G > 0   */
 
 #define LETKF_FP32  0          /* plain FP32 CUDA-core analysis                                */
 #define LETKF_MIXED 1          /* split-precision: for 33 <= k <= 128 the localized Gram runs on
@@ -91,7 +96,7 @@ typedef struct letkf_config {
     int32_t obs_vars;          /* LETKF_OBS_* bit mask, V = number of bits set (>= 1)   */
     const float *obs_err_var;  /* host [L*V] diagonal of R, index l*V + v, > 0          */
     int32_t loc_kind;          /* LETKF_LOC_*                                           */
-    float   loc_radius;        /* Gaussian radius r in cells (> 0 for LOC_GAUSS)        */
+    float   loc_radius;        /* radius r in cells (> 0 for LOC_GAUSS and LOC_GC)      */
     float   loc_cutoff2;       /* squared cutoff distance; <= 0 selects (40/3) r^2,
                                   i.e. cutoff 2 sqrt(10/3) r                            */
     float   infl;              /* multiplicative inflation rho: Q = (k-1)/rho I + ...;

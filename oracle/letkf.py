@@ -16,7 +16,10 @@ R-localization (Sec. II-B): R_loc^-1 = G o R^-1 with G diagonal.  Here G is
 a Gaussian exp(-d^2 / (2 r^2)) of the periodic minimum-image distance d
 from the grid point to the observation point, truncated where
 d^2 >= (2 sqrt(10/3) r)^2; distances are integers so the cutoff test is
-exact.  "No localization" uses G = 1 for every observation.
+exact.  "No localization" uses G = 1 for every observation.  The paper's own
+choice, Gaspari-Cohn (Sec. II-B), is the option kind="gc": G = GC(d / c), the
+fifth-order piecewise rational function of Gaspari & Cohn (1999, Eq. 4.10)
+with half-width c = sqrt(10/3) r, whose support d < 2c is the same cutoff.
 
 One local problem is solved per grid point and its transform is applied to
 all 9 populations of that point (Sec. II-B: the 9 velocities share the same
@@ -51,11 +54,31 @@ def local_obs(x, y, obs_xy, nx, ny, cutoff2):
     return sel, d2[sel]
 
 
-def localization_weight(d2, radius):
-    """Gaussian localization exp(-d^2 / (2 r^2)); radius = inf gives 1."""
+def gaspari_cohn(z):
+    """Gaspari-Cohn correlation function of the scaled distance z = d / c (Gaspari & Cohn
+    1999, Eq. 4.10): a fifth-order piecewise rational function, 1 at z = 0, 0 for z >= 2."""
+    z = np.abs(np.asarray(z, dtype=np.float64))
+    out = np.zeros_like(z)
+    a = z <= 1.0
+    za = z[a]
+    out[a] = (((-0.25 * za + 0.5) * za + 0.625) * za - 5.0 / 3.0) * za * za + 1.0
+    b = (z > 1.0) & (z < 2.0)
+    zb = z[b]
+    out[b] = ((((zb / 12.0 - 0.5) * zb + 0.625) * zb + 5.0 / 3.0) * zb - 5.0) * zb + 4.0 \
+        - 2.0 / (3.0 * zb)
+    return out
+
+
+def localization_weight(d2, radius, kind="gauss"):
+    """Localization weight G of squared distances d2: Gaussian exp(-d^2 / (2 r^2)), or
+    (kind="gc") Gaspari-Cohn GC(d / c) with c = sqrt(10/3) r; radius = inf gives 1."""
     d2 = np.asarray(d2, dtype=np.float64)
     if not math.isfinite(radius):
         return np.ones_like(d2)
+    if kind == "gc":
+        return gaspari_cohn(np.sqrt(d2) / (math.sqrt(10.0 / 3.0) * radius))
+    if kind != "gauss":
+        raise ValueError(f"unknown localization {kind!r}")
     return np.exp(-d2 / (2.0 * radius * radius))
 
 
@@ -89,13 +112,13 @@ def local_analysis(Xb, dY, d, rinv, infl=1.0, eigh=np.linalg.eigh):
 
 
 def point_inputs(x, y, Yf, yo, obs_xy, obs_err_var, nx, ny, radius, cutoff2, obs_vars,
-                 ybar=None, dY=None):
+                 ybar=None, dY=None, loc="gauss"):
     """Local obs-space inputs (dY_loc [p, k], d_loc [p], rinv [p], nloc) at (x, y)."""
     if ybar is None:
         ybar, dY = ensemble_obs(Yf)
     V = len(var_list(obs_vars))
     sel, d2 = local_obs(x, y, obs_xy, nx, ny, cutoff2)
-    g = localization_weight(d2, radius)
+    g = localization_weight(d2, radius, loc)
     idx = (sel[:, None] * V + np.arange(V)[None, :]).reshape(-1)
     gs = np.repeat(g, V)
     rinv = gs / np.asarray(obs_err_var, dtype=np.float64)[idx]
@@ -104,7 +127,7 @@ def point_inputs(x, y, Yf, yo, obs_xy, obs_err_var, nx, ny, radius, cutoff2, obs
 
 
 def analyze(f, Yf, yo, obs_xy, obs_err_var, radius, cutoff2, obs_vars, infl=1.0,
-            points=None):
+            points=None, loc="gauss"):
     """LETKF analysis of an ensemble (Algorithm 1), one local problem per point.
 
     f   [k, 9, ny, nx] forecast ensemble (member-major, post-streaming)
@@ -123,7 +146,7 @@ def analyze(f, Yf, yo, obs_xy, obs_err_var, radius, cutoff2, obs_vars, infl=1.0,
         points = [(x, y) for y in range(ny) for x in range(nx)]
     for (x, y) in points:
         dYl, dl, rl, nloc = point_inputs(x, y, Yf, yo, obs_xy, obs_err_var, nx, ny, radius,
-                                         cutoff2, obs_vars, ybar=ybar, dY=dY)
+                                         cutoff2, obs_vars, ybar=ybar, dY=dY, loc=loc)
         res = local_analysis(f[:, :, y, x].T, dYl, dl, rl, infl)
         res["nloc"] = nloc
         Xa[:, :, y, x] = res["Xa"].T

@@ -48,6 +48,7 @@ struct Plan {
     int cs = 8, ncx = 1, ncy = 1;
     int d2max = 0, cr = 0;
     float inv2r2 = 0.0f;
+    float inv_c = 0.0f;  // Gaspari-Cohn: 1 / (sqrt(10/3) r)
     // byte offsets inside the workspace
     size_t off_state[2], off_force, off_xg, off_obs_xy, off_cell_start, off_cell_obs, off_rinv,
         off_yf, off_yb, off_ybar, off_yo, off_orec, off_gram, off_cvec, off_nloc, off_nloc_all,
@@ -61,8 +62,10 @@ int validate(const letkf_config *c) {
     if (!(c->tau > 0.5f) || !isfinite(c->tau)) return LETKF_EINVAL;
     if (c->n_obs < 0 || (c->n_obs > 0 && (!c->obs_xy || !c->obs_err_var))) return LETKF_EINVAL;
     if (c->obs_vars < 1 || c->obs_vars > 7) return LETKF_EINVAL;
-    if (c->loc_kind != LETKF_LOC_NONE && c->loc_kind != LETKF_LOC_GAUSS) return LETKF_EINVAL;
-    if (c->loc_kind == LETKF_LOC_GAUSS && !(c->loc_radius > 0.0f && isfinite(c->loc_radius)))
+    if (c->loc_kind != LETKF_LOC_NONE && c->loc_kind != LETKF_LOC_GAUSS &&
+        c->loc_kind != LETKF_LOC_GC)
+        return LETKF_EINVAL;
+    if (c->loc_kind != LETKF_LOC_NONE && !(c->loc_radius > 0.0f && isfinite(c->loc_radius)))
         return LETKF_EINVAL;
     if (!(c->infl > 0.0f) || !isfinite(c->infl)) return LETKF_EINVAL;
     if (c->precision != LETKF_FP32 && c->precision != LETKF_MIXED) return LETKF_EINVAL;
@@ -100,10 +103,12 @@ int make_plan(const letkf_config *c, Plan *p) {
         p->tile_h = std::max(p->tile_h, lk::gram_tc_tile_height(p->kp));
     }
     // localization: integer threshold of the strict cutoff d^2 < c^2 (Sec. II-B)
-    if (c->loc_kind == LETKF_LOC_GAUSS) {
+    if (c->loc_kind != LETKF_LOC_NONE) {
         const double r = c->loc_radius;
         const double c2 = c->loc_cutoff2 > 0.0f ? (double)c->loc_cutoff2 : 40.0 * r * r / 3.0;
-        const double lim = ceil(c2) - 1.0;
+        // Gaspari-Cohn: the observations inside min(cutoff, its support 2c) count as local
+        const double c2e = c->loc_kind == LETKF_LOC_GC ? std::min(c2, 40.0 * r * r / 3.0) : c2;
+        const double lim = ceil(c2e) - 1.0;
         p->d2max = lim > 2.0e9 ? 2000000000 : (int)lim;
         if (p->d2max < 0) p->d2max = -1;
         int cr = (int)sqrt((double)std::max(p->d2max, 0));
@@ -111,6 +116,7 @@ int make_plan(const letkf_config *c, Plan *p) {
         while (cr > 0 && (long long)cr * cr > p->d2max) --cr;
         p->cr = p->d2max < 0 ? 0 : cr;
         p->inv2r2 = (float)(1.0 / (2.0 * r * r));
+        p->inv_c = (float)(1.0 / (sqrt(10.0 / 3.0) * r));
     }
     // bins: smallest power-of-two edge (>= 8) whose patch of one Gram tile fits the kernel
     const int maxc = lk::gram_max_cells();
@@ -824,6 +830,8 @@ int letkf_init(const letkf_config *cfg, void *workspace, size_t workspace_bytes,
     h->net.d2max = plan.d2max;
     h->net.cr = plan.cr;
     h->net.inv2r2 = plan.inv2r2;
+    h->net.loc_gc = cfg->loc_kind == LETKF_LOC_GC;
+    h->net.inv_c = plan.inv_c;
 
     if (lk::lbm_prepare() != cudaSuccess || lk::gram_prepare(plan.kp) != cudaSuccess ||
         lk::eigen_prepare(cfg->k, &h->eig_blocks) != cudaSuccess ||

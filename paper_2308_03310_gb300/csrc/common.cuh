@@ -27,6 +27,20 @@ __host__ __device__ constexpr float dwq(int q) {
                              : (float)(1.0 / 36.0 - (double)(1.0f / 36.0f)));
 }
 
+// Gaspari-Cohn correlation of the scaled distance z = d / c >= 0 inside its support (Gaspari
+// & Cohn 1999, Eq. 4.10): fifth-order piecewise rational, 1 at z = 0, zero at z = 2.  The
+// outer piece, z^5/12 - z^4/2 + 5 z^3/8 + 5 z^2/3 - 5 z + 4 - 2/(3 z), is evaluated in its
+// factored form (2 - z)^4 (2 z^2 + 4 z - 1) / (24 z): no cancellation near z = 2, and never
+// negative.  Callers pass points strictly inside the support; z is held below 2 so that a
+// rounding of z up to 2 still leaves a positive weight.
+__device__ __forceinline__ float gaspari_cohn(float z) {
+    if (z <= 1.0f)
+        return fmaf(fmaf(fmaf(fmaf(-0.25f, z, 0.5f), z, 0.625f), z, -5.0f / 3.0f), z * z, 1.0f);
+    z = fminf(z, 1.99999988f);  // the float below 2
+    const float t = 2.0f - z, t2 = t * t;
+    return t2 * t2 * fmaf(fmaf(2.0f, z, 4.0f), z, -1.0f) / (24.0f * z);
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -165,14 +165,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Square root of the Gaussian localization weight, exp(-d^2 / (4 r^2)), of an observation at
-// (ox, oy) seen from grid point (qx, qy); 0 beyond the cutoff.
+// Square root of the localization weight of an observation at (ox, oy) seen from grid point
+// (qx, qy): the Gaussian's exp(-d^2 / (4 r^2)) directly, or sqrt(GC(d / c)); 0 beyond the
+// cutoff.
 __device__ __forceinline__ float loc_weight_sqrt(const ObsNet &net, int ox, int oy, int qx,
                                                  int qy, int nx, int ny) {
     if (net.loc_none) return 1.0f;
     const int dx = min_image(ox - qx, nx), dy = min_image(oy - qy, ny);
     const int d2 = dx * dx + dy * dy;
-    return d2 <= net.d2max ? __expf(-0.5f * (float)d2 * net.inv2r2) : 0.0f;
+    if (d2 > net.d2max) return 0.0f;
+    return net.loc_gc ? sqrtf(fmaxf(gaspari_cohn(sqrtf((float)d2) * net.inv_c), 0.0f))
+                      : __expf(-0.5f * (float)d2 * net.inv2r2);
 }
 
 // A_p row `row` (accumulator values v[0..31] for columns c0..c0+31) to global memory.

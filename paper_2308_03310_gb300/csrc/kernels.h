@@ -26,6 +26,8 @@ struct ObsNet {
     int d2max;              // local iff integer squared periodic distance <= d2max
     int cr;                 // largest |dx| with dx^2 <= d2max (search half-width in cells)
     float inv2r2;           // 1 / (2 r^2) of the Gaussian weight
+    int loc_gc;             // 1: Gaspari-Cohn weight GC(d / c) instead of the Gaussian
+    float inv_c;            // 1 / c, c = sqrt(10/3) r (Gaspari-Cohn half-width)
 };
 
 // ---- lbm.cu -------------------------------------------------------------------

@@ -102,13 +102,16 @@ __device__ __forceinline__ int patch_obs(const ObsNet &net, const int *cell_base
     return net.cell_obs[cell_base[lo] + (j - cell_pre[lo])];
 }
 
-// Gaussian localization weight of observation point o seen from grid point (qx, qy).
+// Localization weight (Gaussian, or Gaspari-Cohn) of observation point o seen from grid
+// point (qx, qy).
 __device__ __forceinline__ float loc_weight(const ObsNet &net, int2 o, int qx, int qy, int nx,
                                             int ny) {
     if (net.loc_none) return 1.0f;
     const int dx = min_image(o.x - qx, nx), dy = min_image(o.y - qy, ny);
     const int d2 = dx * dx + dy * dy;
-    return d2 <= net.d2max ? expf(-(float)d2 * net.inv2r2) : 0.0f;
+    if (d2 > net.d2max) return 0.0f;
+    return net.loc_gc ? gaspari_cohn(sqrtf((float)d2) * net.inv_c)
+                      : expf(-(float)d2 * net.inv2r2);
 }
 
 }  // namespace lk

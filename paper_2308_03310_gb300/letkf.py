@@ -32,6 +32,7 @@ LETKF_OBS_V = 4
 
 LETKF_LOC_NONE = 0
 LETKF_LOC_GAUSS = 1
+LETKF_LOC_GC = 2
 
 LETKF_FP32 = 0
 LETKF_MIXED = 1
@@ -316,7 +317,7 @@ class Experiment:
     def __init__(self, nx, ny, k, tau, obs_xy, obs_err_var, obs_vars=LETKF_OBS_U | LETKF_OBS_V,
                  loc_radius=None, loc_cutoff2=0.0, force=None, n_aux=0, infl=1.0,
                  precision=LETKF_FP32, chunk_bytes=0, stream=None, device=None,
-                 eig_schedule=LETKF_EIG_AUTO):
+                 eig_schedule=LETKF_EIG_AUTO, loc_kind=LETKF_LOC_GAUSS):
         import torch
         self.torch = torch
         self.device = torch.device(device if device is not None else "cuda")
@@ -340,7 +341,7 @@ class Experiment:
         if loc_radius is None:
             cfg.loc_kind, cfg.loc_radius = LETKF_LOC_NONE, 0.0
         else:
-            cfg.loc_kind, cfg.loc_radius = LETKF_LOC_GAUSS, float(loc_radius)
+            cfg.loc_kind, cfg.loc_radius = int(loc_kind), float(loc_radius)
         cfg.loc_cutoff2 = float(loc_cutoff2)
         cfg.infl = float(infl)
         cfg.precision = int(precision)

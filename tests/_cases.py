@@ -64,13 +64,14 @@ def observations(f_truth, obs_xy, obs_vars, sigma, seed):
     return (y + synth.gaussian(y.shape, sigma, seed)).astype(np.float32)
 
 
-def oracle_analysis(f32, yo, obs_xy, obs_var, radius, obs_vars, points=None, infl=1.0):
+def oracle_analysis(f32, yo, obs_xy, obs_var, radius, obs_vars, points=None, infl=1.0,
+                    loc="gauss"):
     """Oracle analysis of the FP32 state f32 (as FP64)."""
     f = f32.astype(np.float64)
     Yf = oobs.observe(f, obs_xy, obs_vars)
     c2 = synth.loc_cutoff2(radius) if math.isfinite(radius) else math.inf
     return oletkf.analyze(f, Yf, yo.astype(np.float64), obs_xy, obs_var.astype(np.float64),
-                          radius, c2, obs_vars, infl=infl, points=points)
+                          radius, c2, obs_vars, infl=infl, points=points, loc=loc)
 
 
 def point_parity(xa_gpu, xa_orc, xf):

@@ -1,6 +1,7 @@
 """Pins of the FP64 LETKF oracle (Sec. II-B, Algorithm 1) against independent facts:
-brute-force Kalman filter, number-theoretic lattice counts, closed-form
-spectra, a hand-worked scalar case and the transform's algebraic identities."""
+brute-force Kalman filter, number-theoretic lattice counts, closed-form spectra, the 3D
+convolution behind the Gaspari-Cohn function, a hand-worked scalar case and the transform's
+algebraic identities."""
 import json
 import math
 import os
@@ -67,6 +68,55 @@ def test_gaussian_weight_values():
     assert w[1] == pytest.approx(math.exp(-0.5), rel=1e-15)
     assert w[2] == pytest.approx(math.exp(-20.0 / 3.0), rel=1e-14)
     assert (letkf.localization_weight(np.array([5.0, 1e9]), math.inf) == 1.0).all()
+
+
+def _cone_self_convolution(z):
+    """3D self-convolution of the radial cone (1 - s)_+ at distance z, normalized to 1 at 0:
+    the construction behind the Gaspari-Cohn function, evaluated by quadrature."""
+    from scipy import integrate
+
+    def cone(s):
+        return max(0.0, 1.0 - s)
+
+    def conv(r):
+        if r < 1e-12:
+            return 4.0 * math.pi * integrate.quad(lambda s: s * s * cone(s) ** 2, 0.0, 1.0,
+                                                  epsabs=1e-14, epsrel=1e-12)[0]
+
+        def inner(s):
+            lo, hi = abs(r - s), min(r + s, 1.0)
+            if hi <= lo:
+                return 0.0
+            return integrate.quad(lambda t: t * cone(t), lo, hi, epsabs=1e-14, epsrel=1e-12)[0]
+        return 2.0 * math.pi / r * integrate.quad(lambda s: s * cone(s) * inner(s), 0.0, 1.0,
+                                                  limit=200, epsabs=1e-14, epsrel=1e-12)[0]
+    return conv(z) / conv(0.0)
+
+
+@pytest.mark.parametrize("z", [0.05, 0.3, 0.7, 1.0, 1.2, 1.6, 1.9])
+def test_gaspari_cohn_is_the_self_convolution_of_a_cone(z):
+    # Gaspari & Cohn build their fifth-order function as a 3D convolution of compactly
+    # supported pieces; the normalized self-convolution of (1 - d/c)_+ reproduces it, which
+    # pins every coefficient and both branches of the oracle's piecewise formula.
+    pytest.importorskip("scipy")
+    assert letkf.gaspari_cohn(np.array([z]))[0] == pytest.approx(_cone_self_convolution(z),
+                                                                    abs=1e-9)
+
+
+def test_gaspari_cohn_weight_support_and_shape():
+    r = 3.0
+    c = math.sqrt(10.0 / 3.0) * r
+    d = np.linspace(0.0, 2.5 * c, 2001)
+    w = letkf.localization_weight(d * d, r, "gc")
+    assert w[0] == 1.0
+    assert (w[d >= 2.0 * c] == 0.0).all()          # zero from the default cutoff on
+    assert (np.diff(w[d < 2.0 * c]) < 0.0).all()   # strictly decreasing inside
+    # the two branches meet at d = c (value 5/24) without a jump in value or slope
+    assert letkf.gaspari_cohn(np.array([1.0]))[0] == pytest.approx(5.0 / 24.0, rel=1e-14)
+    g = letkf.gaspari_cohn(np.array([1.0 - 2e-6, 1.0 - 1e-6, 1.0 + 1e-6, 1.0 + 2e-6]))
+    assert (g[1] - g[0]) == pytest.approx(g[3] - g[2], rel=1e-4)
+    with pytest.raises(ValueError):
+        letkf.localization_weight(np.array([1.0]), r, "spline")
 
 
 # ---------------------------------------------------------------- observation operator
