@@ -53,7 +53,7 @@ __host__ __device__ inline int smem_floats(int k) {
 // 32, the rows the register chains of k <= 64 read), de (k float2), taus (k)
 __host__ __device__ inline int tri_vw(int k) { return (k + 31) & ~31; }
 __host__ __device__ inline int tri_smem_floats(int k) {
-    return round4(k * (k + 1) + 2 * tri_vw(k) + 3 * k);
+    return round4(round4(k * (k + 1)) + 2 * tri_vw(k) + 3 * k);  // vw 16-byte aligned
 }
 // split, vectors and update: a staging area first (16-byte aligned; 2 tri_vw(k) + 8 floats:
 // the replay's (c, s) by row, rows 0..k+1, then one reflector by absolute row for the
@@ -937,31 +937,43 @@ __device__ __forceinline__ void tri_pick(const float (&q)[NC][32 * NC], float (&
     for (int c = 0; c < NC; ++c) x[c] = q[c][I];
 }
 
-// p += Q'[s][t] v_s for row s = I + 1
-template <int NC, int I>
-__device__ __forceinline__ void tri_mv(const float (&q)[NC][32 * NC], const float2 *vw,
-                                       float (&p)[NC]) {
-    if constexpr (I + 1 < 32 * NC) {
-        const float vs = vw[I + 1].x;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) p[c] = fmaf(q[c][I + 1], vs, p[c]);
-    }
-}
-
-// Q'[s][t] -= v_s w_t + w_s v_t for row s = I + 1
-template <int NC, int I>
-__device__ __forceinline__ void tri_up(float (&q)[NC][32 * NC], const float2 *vw,
-                                       const float (&vt)[NC], const float (&wt)[NC]) {
-    if constexpr (I + 1 < 32 * NC) {
-        const float2 g = vw[I + 1];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) q[c][I + 1] -= fmaf(g.x, wt[c], g.y * vt[c]);
-    }
-}
-
 // Case labels 0..63 in increasing order: a chain entered at case j falls through the rows
 // above j + 1.
+// The same two row loops over 4-row groups: (v, w) of rows 4G..4G+3 come as two 16-byte
+// broadcast loads, the product keeps one accumulator per row mod 4 (four independent
+// multiply-add chains), and the rows of the first group below j + 1 hold v = w = 0.
+template <int NC, int G>
+__device__ __forceinline__ void tri_mv4(const float (&q)[NC][32 * NC], const float4 *vw4,
+                                        float (&p)[NC][4]) {
+    if constexpr (4 * G < 32 * NC) {
+        const float4 a = vw4[2 * G], b = vw4[2 * G + 1];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            p[c][0] = fmaf(q[c][4 * G], a.x, p[c][0]);
+            p[c][1] = fmaf(q[c][4 * G + 1], a.z, p[c][1]);
+            p[c][2] = fmaf(q[c][4 * G + 2], b.x, p[c][2]);
+            p[c][3] = fmaf(q[c][4 * G + 3], b.z, p[c][3]);
+        }
+    }
+}
+
+template <int NC, int G>
+__device__ __forceinline__ void tri_up4(float (&q)[NC][32 * NC], const float4 *vw4,
+                                        const float (&vt)[NC], const float (&wt)[NC]) {
+    if constexpr (4 * G < 32 * NC) {
+        const float4 a = vw4[2 * G], b = vw4[2 * G + 1];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            q[c][4 * G] -= fmaf(a.x, wt[c], a.y * vt[c]);
+            q[c][4 * G + 1] -= fmaf(a.z, wt[c], a.w * vt[c]);
+            q[c][4 * G + 2] -= fmaf(b.x, wt[c], b.y * vt[c]);
+            q[c][4 * G + 3] -= fmaf(b.z, wt[c], b.w * vt[c]);
+        }
+    }
+}
+
 #define LK_CASE8(M, b) M(b) M(b + 1) M(b + 2) M(b + 3) M(b + 4) M(b + 5) M(b + 6) M(b + 7)
+#define LK_GROUPS16(M) LK_CASE8(M, 0) LK_CASE8(M, 8)
 #define LK_CASES64(M)                                                                      \
     LK_CASE8(M, 0) LK_CASE8(M, 8) LK_CASE8(M, 16) LK_CASE8(M, 24) LK_CASE8(M, 32)         \
     LK_CASE8(M, 40) LK_CASE8(M, 48) LK_CASE8(M, 56)
@@ -1028,26 +1040,32 @@ __device__ __forceinline__ void tridiagonalize_registers(float *Ag, const float 
                 refl[t - j - 1] = vt[c];  // lower triangle of the slot
             }
         }
+        const int g0 = (j + 1) >> 2;  // the group of row j + 1
+        if (lane < 4 && 4 * g0 + lane <= j) vw[4 * g0 + lane] = make_float2(0.0f, 0.0f);
         if (lane == 0) {
             taus[j] = tau;
             de[j].y = beta;
         }
         __syncwarp();
         if (tau != 0.0f) {
-            float p[NC];
+            const float4 *vw4 = reinterpret_cast<const float4 *>(vw);
+            float p4[NC][4];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) p[c] = 0.0f;
-            switch (j) {
-#define LK_MV(i) \
-    case i: tri_mv<NC, i>(q, vw, p);
-                LK_CASES64(LK_MV)
-#undef LK_MV
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) p4[c][u] = 0.0f;
+            switch (g0) {
+#define LK_MV4(G) \
+    case G: tri_mv4<NC, G>(q, vw4, p4);
+                LK_GROUPS16(LK_MV4)
+#undef LK_MV4
                 default: break;
             }
+            float p[NC];
             float kk = 0.0f;
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                p[c] *= tau;
+                p[c] = ((p4[c][0] + p4[c][1]) + (p4[c][2] + p4[c][3])) * tau;
                 kk = fmaf(p[c], vt[c], kk);
             }
             const float K = 0.5f * tau * warp_sum(kk);
@@ -1059,11 +1077,11 @@ __device__ __forceinline__ void tridiagonalize_registers(float *Ag, const float 
                 if (t > j && t < k) vw[t].y = wt[c];
             }
             __syncwarp();
-            switch (j) {
-#define LK_UP(i) \
-    case i: tri_up<NC, i>(q, vw, vt, wt);
-                LK_CASES64(LK_UP)
-#undef LK_UP
+            switch (g0) {
+#define LK_UP4(G) \
+    case G: tri_up4<NC, G>(q, vw4, vt, wt);
+                LK_GROUPS16(LK_UP4)
+#undef LK_UP4
                 default: break;
             }
         }
@@ -1087,6 +1105,7 @@ __device__ __forceinline__ void tridiagonalize_registers(float *Ag, const float 
     }
     __syncwarp();
 }
+#undef LK_GROUPS16
 #undef LK_CASES64
 #undef LK_CASE8
 
@@ -1098,7 +1117,7 @@ __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS) eig_tridiag_kernel(Eig
     const int k = a.k, ld = k + 1;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     float *S = smem + (size_t)wib * tri_smem_floats(k);
-    float2 *vw = reinterpret_cast<float2 *>(S + k * ld);
+    float2 *vw = reinterpret_cast<float2 *>(S + round4(k * ld));
     float2 *de = vw + tri_vw(k);
     float *taus = reinterpret_cast<float *>(de + k);
     const int warps_per_block = blockDim.x >> 5;
