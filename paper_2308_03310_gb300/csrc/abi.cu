@@ -191,6 +191,9 @@ struct letkf_handle {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // the split eigensolve's second stream and its fork/join events (halves of a chunk overlap)
+    cudaStream_t stream2 = nullptr;
+    cudaEvent_t split_fork = nullptr, split_join = nullptr;
     unsigned char *ws = nullptr;
     bool own_ws = false;
     float *state[2] = {nullptr, nullptr};
@@ -453,7 +456,8 @@ int tune_eig_schedule(letkf_handle *h, int y0, int y1) {
             err = cudaEventRecord(t0, h->stream);
             if (err == cudaSuccess)
                 err = sch == 0 ? lk::launch_eigen_update(e, h->stream)
-                               : lk::launch_eigen_split(e, h->eig_split, h->stream);
+                               : lk::launch_eigen_split(e, h->eig_split, h->stream, h->stream2,
+                                                         h->split_fork, h->split_join);
             if (err == cudaSuccess) err = cudaEventRecord(t1, h->stream);
             if (err == cudaSuccess) err = cudaEventSynchronize(t1);
             float ms = 0.0f;
@@ -523,7 +527,8 @@ int enqueue_analysis(letkf_handle *h, letkf_probe *probe) {
             CK(lk::launch_eigen_update(e, h->stream));
         } else {
             e.eigval = h->eigval;
-            CK(lk::launch_eigen_split(e, h->eig_split, h->stream));
+            CK(lk::launch_eigen_split(e, h->eig_split, h->stream, h->stream2, h->split_fork,
+                                      h->split_join));
         }
         if ((rc = mark(h, 6 + 2 * chunk))) return rc;
         ++chunk;
@@ -646,8 +651,9 @@ int enqueue_group(letkf_handle *const *hs, int n, int nsteps) {
             if (g->eig_schedule == LETKF_EIG_FUSED) {
                 segs[m++] = eig_args(g, y0, y1);
             } else {
-                const cudaError_t e = lk::launch_eigen_split(eig_args(g, y0, y1), g->eig_split,
-                                                             h->stream);
+                const cudaError_t e =
+                    lk::launch_eigen_split(eig_args(g, y0, y1), g->eig_split, h->stream,
+                                           g->stream2, g->split_fork, g->split_join);
                 if (e != cudaSuccess) return cuda_fail(g, e);
             }
         }
@@ -744,6 +750,10 @@ int letkf_init(const letkf_config *cfg, void *workspace, size_t workspace_bytes,
             return fail(LETKF_ECUDA);
         h->own_stream = true;
     }
+    if (cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->split_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->split_join, cudaEventDisableTiming) != cudaSuccess)
+        return fail(LETKF_ECUDA);
     if (workspace) {
         h->ws = (unsigned char *)workspace;
     } else {
@@ -900,8 +910,12 @@ int letkf_destroy(letkf_handle *h) {
     cudaGetDevice(&dev);
     if (dev != h->device) cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->stream2) cudaStreamSynchronize(h->stream2);
     destroy_graphs(h);
     destroy_events(h);
+    if (h->split_fork) cudaEventDestroy(h->split_fork);
+    if (h->split_join) cudaEventDestroy(h->split_join);
+    if (h->stream2) cudaStreamDestroy(h->stream2);
     if (h->own_ws && h->ws) cudaFree(h->ws);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     if (dev >= 0 && dev != h->device) cudaSetDevice(dev);

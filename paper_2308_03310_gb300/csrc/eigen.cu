@@ -1251,7 +1251,7 @@ __global__ void __launch_bounds__(kQlThreads) eig_ql_kernel(EigArgs a, EigSplit 
     if (notconv) atomicOr(a.status, ST_NOTCONV);
     if (overflow) {  // handed to the fused kernel, which recomputes the point from A
         sp.nrot[lp] = -1;
-        sp.list[atomicAdd(sp.list_count, 1)] = lp;
+        sp.list[atomicAdd(sp.list_count, 1)] = lp + sp.list_offset;
         return;
     }
     sp.nrot[lp] = pos;
@@ -1564,15 +1564,40 @@ cudaError_t launch_nc(const EigArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// The points [p0, p0 + n) of a chunk as a chunk of their own (the same buffers, offset).
+void split_part(const EigArgs &a, const EigSplit &sp, int p0, int n, EigArgs *b, EigSplit *c) {
+    const size_t k = (size_t)a.k, o = (size_t)p0;
+    *b = a;
+    *c = sp;
+    b->npts = n;
+    b->pt0 = a.pt0 + p0;
+    b->gram = a.gram + o * k * k;
+    b->cvec = a.cvec ? a.cvec + o * k : nullptr;
+    b->nloc = a.nloc ? a.nloc + o : nullptr;
+    b->eigval = a.eigval + o * k;
+    b->evec = a.evec ? a.evec + o * k * k : nullptr;
+    c->de = sp.de + o * k;
+    c->taus = sp.taus + o * k;
+    c->rot = sp.rot + o * (size_t)sp.rcap;
+    c->nrot = sp.nrot + o;
+    c->list_offset = sp.list_offset + p0;
+}
+
 template <int NC>
-cudaError_t launch_split_nc(const EigArgs &a, const EigSplit &sp, cudaStream_t s) {
+void launch_tri(const EigArgs &a, const EigSplit &sp, cudaStream_t s) {
     const int warps = EigCfg<NC>::WARPS;
-    cudaError_t e = cudaMemsetAsync(sp.list_count, 0, sizeof(int), s);
-    if (e != cudaSuccess) return e;
     eig_tridiag_kernel<NC><<<grid_for(sp.grid_tri, a.npts, warps), 32 * warps,
                              (size_t)tri_smem_floats(a.k) * sizeof(float) * warps, s>>>(a, sp);
+}
+
+void launch_ql(const EigArgs &a, const EigSplit &sp, cudaStream_t s) {
     eig_ql_kernel<<<(unsigned)((a.npts + kQlThreads - 1) / kQlThreads), kQlThreads,
                     (size_t)a.k * kQlThreads * sizeof(float2), s>>>(a, sp);
+}
+
+template <int NC>
+void launch_vec(const EigArgs &a, const EigSplit &sp, cudaStream_t s) {
+    const int warps = EigCfg<NC>::WARPS;
     if (a.x)
         eig_vec_kernel<NC, true><<<grid_for(sp.grid_vec, a.npts, warps), 32 * warps,
                                    (size_t)vec_smem_floats(a.k) * sizeof(float) * warps, s>>>(a,
@@ -1581,6 +1606,40 @@ cudaError_t launch_split_nc(const EigArgs &a, const EigSplit &sp, cudaStream_t s
         eig_vec_kernel<NC, false><<<grid_for(sp.grid_vec, a.npts, warps), 32 * warps,
                                     (size_t)vec_smem_floats(a.k) * sizeof(float) * warps, s>>>(a,
                                                                                           sp);
+}
+
+// Chunks below this many points run on one stream: their halves would not fill the GPU.
+constexpr int kSplitOverlapMin = 16384;
+
+template <int NC>
+cudaError_t launch_split_nc(const EigArgs &a, const EigSplit &sp, cudaStream_t s,
+                            cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join) {
+    const int warps = EigCfg<NC>::WARPS;
+    cudaError_t e = cudaMemsetAsync(sp.list_count, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    if (s2 && fork && join && a.npts >= kSplitOverlapMin) {
+        // halves h0, h1: s runs tri(h0), QL(h0), vec(h0); s2 starts after tri(h0) and runs
+        // tri(h1), QL(h1), vec(h1); s waits for s2 before the hand-off kernel
+        const int n0 = (a.npts / 2 + kQlThreads - 1) / kQlThreads * kQlThreads;
+        EigArgs a0, a1;
+        EigSplit p0, p1;
+        split_part(a, sp, 0, n0, &a0, &p0);
+        split_part(a, sp, n0, a.npts - n0, &a1, &p1);
+        launch_tri<NC>(a0, p0, s);
+        if ((e = cudaEventRecord(fork, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s2, fork, 0)) != cudaSuccess) return e;
+        launch_ql(a0, p0, s);
+        launch_tri<NC>(a1, p1, s2);
+        launch_ql(a1, p1, s2);
+        launch_vec<NC>(a0, p0, s);
+        launch_vec<NC>(a1, p1, s2);
+        if ((e = cudaEventRecord(join, s2)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s, join, 0)) != cudaSuccess) return e;
+    } else {
+        launch_tri<NC>(a, sp, s);
+        launch_ql(a, sp, s);
+        launch_vec<NC>(a, sp, s);
+    }
     // matrices whose rotation record overflowed: the fused kernel over the list
     EigArgs f = a;
     f.list = sp.list;
@@ -1676,13 +1735,14 @@ cudaError_t eigen_group_prepare(int *max_blocks) {
     return e;
 }
 
-cudaError_t launch_eigen_split(const EigArgs &a, const EigSplit &sp, cudaStream_t s) {
+cudaError_t launch_eigen_split(const EigArgs &a, const EigSplit &sp, cudaStream_t s,
+                               cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join) {
     if (a.npts <= 0) return cudaSuccess;
     if (!a.eigval || !sp.de || !sp.taus || !sp.rot || !sp.nrot || !sp.list || !sp.list_count)
         return cudaErrorInvalidValue;
-    if (a.k <= 32) return launch_split_nc<1>(a, sp, s);
-    if (a.k <= 64) return launch_split_nc<2>(a, sp, s);
-    if (a.k <= 128) return launch_split_nc<4>(a, sp, s);
+    if (a.k <= 32) return launch_split_nc<1>(a, sp, s, s2, fork, join);
+    if (a.k <= 64) return launch_split_nc<2>(a, sp, s, s2, fork, join);
+    if (a.k <= 128) return launch_split_nc<4>(a, sp, s, s2, fork, join);
     return cudaErrorInvalidValue;
 }
 

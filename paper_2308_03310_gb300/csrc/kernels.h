@@ -117,6 +117,7 @@ struct EigSplit {
     int *nrot = nullptr;            // [npts] record length, -1: handed to the fused kernel
     int *list = nullptr;            // [npts] points handed to the fused kernel
     int *list_count = nullptr;      // [1]
+    int list_offset = 0;            // added to a point's index when it is listed
     int rcap = 0;                   // record capacity per point (entries)
     int grid_tri = 0, grid_vec = 0; // resident grids (eigen_split_prepare)
 };
@@ -137,7 +138,12 @@ cudaError_t launch_eigen_group(const EigArgs *segs, int n, int *counters, const 
 cudaError_t eigen_prepare(int k, int *max_blocks);  // once per process and k
 cudaError_t eigen_split_prepare(int k, EigSplit *sp);
 cudaError_t launch_eigen_update(const EigArgs &a, cudaStream_t s);
-cudaError_t launch_eigen_split(const EigArgs &a, const EigSplit &sp, cudaStream_t s);
+// With a second stream s2 and two events (all non-null) a large chunk runs as two halves whose
+// kernels overlap: the second half's tridiagonalization with the first half's QL, the first
+// half's vectors with the second half's QL.  Same results as the one-stream order.
+cudaError_t launch_eigen_split(const EigArgs &a, const EigSplit &sp, cudaStream_t s,
+                               cudaStream_t s2 = nullptr, cudaEvent_t fork = nullptr,
+                               cudaEvent_t join = nullptr);
 size_t eigen_smem_per_warp(int k);
 
 }  // namespace lk

@@ -79,6 +79,43 @@ def test_schedules_match_oracle_and_each_other(k, nx, ny, stride, radius):
     assert np.abs(lf - ls).max() <= 1e-6 * np.abs(lf).max()
 
 
+@pytest.mark.parametrize("k,n,precision", [(32, 136, L.LETKF_FP32), (64, 128, L.LETKF_MIXED)])
+def test_split_schedule_on_two_streams_matches_fused_and_oracle(k, n, precision):
+    # chunks of >= 16384 points run the split kernels as two overlapping halves on two
+    # streams (the second half's points listed at their chunk index); the analysis must equal
+    # the fused schedule to FP32 rounding and the oracle at sampled points, including the
+    # points at the seam between the halves
+    net = synth.regular_obs_network(n, n, 4)
+    var = np.full(len(net) * 2, 1e-4, dtype=np.float32)
+    f0 = C.big_ensemble_state(k, n, n, seed=961 + k)
+    Yf = C.observe_at_points(f0, net, UV)
+    yo = (Yf.mean(0) + synth.gaussian(Yf.shape[1], 0.01, 962)).astype(np.float32)
+    outs = {}
+    for sch in (L.LETKF_EIG_SPLIT, L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT_CHECK):
+        exp = L.Experiment(n, n, k, 0.6, net, var, loc_radius=3.0, precision=precision,
+                           eig_schedule=sch)
+        exp.set_state(f0)
+        exp.analyze(yo)
+        outs[sch] = C.dev64(exp.get_deviation())
+        assert exp.sync() == 0
+    Wb = lbm.W[None, :, None, None]
+    fb = _flat(f0.astype(np.float64) - Wb)
+    for sch in (L.LETKF_EIG_SPLIT, L.LETKF_EIG_SPLIT_CHECK):
+        errs = C.point_parity(_flat(outs[sch]), _flat(outs[L.LETKF_EIG_FUSED]), fb)
+        assert max(errs) < 2e-6, (sch, errs)
+    half = (n * n // 2 + 63) // 64 * 64
+    pts = sorted({0, half - 1, half, half + 1, n * n - 1, n * n // 3})
+    ref = C.oracle_points(f0, Yf, yo, net, var, 3.0, UV, [(p % n, p // n) for p in pts])
+    bg, bo, bf = [], [], []
+    for p in pts:
+        x, y = p % n, p // n
+        bg.append(outs[L.LETKF_EIG_SPLIT][:, :, y, x])
+        bo.append(ref[(x, y)]["Xa"].T - lbm.W[None, :])
+        bf.append(f0[:, :, y, x].astype(np.float64) - lbm.W[None, :])
+    errs = C.point_parity(np.concatenate(bg, 1), np.concatenate(bo, 1), np.concatenate(bf, 1))
+    assert max(errs) < 1e-5, errs
+
+
 def test_split_schedule_in_mixed_precision_matches_oracle():
     f0, yo, net, var, dev, _, _ = _run(64, 16, 16, 2, 3.0, 951, L.LETKF_EIG_SPLIT,
                                        precision=L.LETKF_MIXED)
