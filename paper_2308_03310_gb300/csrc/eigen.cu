@@ -1608,7 +1608,10 @@ void launch_vec(const EigArgs &a, const EigSplit &sp, cudaStream_t s) {
                                                                                           sp);
 }
 
-// Chunks below this many points run on one stream: their halves would not fill the GPU.
+// Chunks below this many points run on one stream: their halves would not fill the GPU.  The
+// overlap is used for k <= 32, where it measured 11 % faster (256^2); at k = 64 (1024^2) it
+// measured 1 % slower: there the vector kernel is limited by shared memory and shares the SMs
+// with the QL blocks.
 constexpr int kSplitOverlapMin = 16384;
 
 template <int NC>
@@ -1617,7 +1620,7 @@ cudaError_t launch_split_nc(const EigArgs &a, const EigSplit &sp, cudaStream_t s
     const int warps = EigCfg<NC>::WARPS;
     cudaError_t e = cudaMemsetAsync(sp.list_count, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    if (s2 && fork && join && a.npts >= kSplitOverlapMin) {
+    if (NC == 1 && s2 && fork && join && a.npts >= kSplitOverlapMin) {
         // halves h0, h1: s runs tri(h0), QL(h0), vec(h0); s2 starts after tri(h0) and runs
         // tri(h1), QL(h1), vec(h1); s waits for s2 before the hand-off kernel
         const int n0 = (a.npts / 2 + kQlThreads - 1) / kQlThreads * kQlThreads;

@@ -138,9 +138,9 @@ cudaError_t launch_eigen_group(const EigArgs *segs, int n, int *counters, const 
 cudaError_t eigen_prepare(int k, int *max_blocks);  // once per process and k
 cudaError_t eigen_split_prepare(int k, EigSplit *sp);
 cudaError_t launch_eigen_update(const EigArgs &a, cudaStream_t s);
-// With a second stream s2 and two events (all non-null) a large chunk runs as two halves whose
-// kernels overlap: the second half's tridiagonalization with the first half's QL, the first
-// half's vectors with the second half's QL.  Same results as the one-stream order.
+// With a second stream s2 and two events (all non-null) a large chunk (k <= 32) runs as two
+// halves whose kernels overlap: the second half's tridiagonalization with the first half's QL,
+// the first half's vectors with the second half's QL.  Same results as the one-stream order.
 cudaError_t launch_eigen_split(const EigArgs &a, const EigSplit &sp, cudaStream_t s,
                                cudaStream_t s2 = nullptr, cudaEvent_t fork = nullptr,
                                cudaEvent_t join = nullptr);

@@ -79,9 +79,10 @@ def test_schedules_match_oracle_and_each_other(k, nx, ny, stride, radius):
     assert np.abs(lf - ls).max() <= 1e-6 * np.abs(lf).max()
 
 
-@pytest.mark.parametrize("k,n,precision", [(32, 136, L.LETKF_FP32), (64, 128, L.LETKF_MIXED)])
+@pytest.mark.parametrize("k,n,precision", [(32, 136, L.LETKF_FP32), (24, 128, L.LETKF_MIXED),
+                                         (64, 128, L.LETKF_MIXED)])
 def test_split_schedule_on_two_streams_matches_fused_and_oracle(k, n, precision):
-    # chunks of >= 16384 points run the split kernels as two overlapping halves on two
+    # chunks of >= 16384 points (k <= 32) run the split kernels as two overlapping halves on two
     # streams (the second half's points listed at their chunk index); the analysis must equal
     # the fused schedule to FP32 rounding and the oracle at sampled points, including the
     # points at the seam between the halves
