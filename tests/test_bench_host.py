@@ -1,5 +1,6 @@
-"""Host-side logic of bench.py, on CPU: clock parsing, roofline arithmetic, the
-multi-rank reductions (world size 2 over gloo) and the reference (oracle) arm."""
+"""Host-side logic of bench.py, on CPU: clock parsing, roofline and D2Q9 rate arithmetic, the
+multi-rank reductions (world size 2 over gloo), the all-core oracle baseline and the reference
+(oracle) arm."""
 import json
 import os
 import socket
@@ -85,3 +86,41 @@ def test_reference_arm_other_ranks_exit_without_work():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference"],
                        capture_output=True, text=True, timeout=60, env=env)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_lbm_rates_count_updates_and_single_step_bytes():
+    import synth
+    w = synth.WORKLOADS["turb256_k32"]
+    r = bench.lbm_rates(w, 2.0, {"hbm_gbs": 6800.0})
+    updates = 256 * 256 * 32 * 100
+    assert r["mlups"] == pytest.approx(updates / 2e-3 / 1e6)
+    assert r["mlups_per_member"] == pytest.approx(r["mlups"] / 32)
+    gbs = (72.0 * updates + 8.0 * 256 * 256 * 100) / 2e-3 / 1e9
+    assert r["single_step_equivalent_gbs"] == pytest.approx(gbs)
+    assert r["single_step_equivalent_frac"] == pytest.approx(gbs / 6800.0)
+
+
+def test_kernel_work_counts_two_step_launches():
+    import synth
+    w = synth.WORKLOADS["turb256_k32"]
+    work = bench.kernel_work(w, 32, 65536, 42.0, 2, 1024, 1, 100)
+    unit, amount, launches = work["lbm_step"]
+    assert launches == 50                       # two steps per launch
+    assert amount == pytest.approx((72.0 * 65536 * 32 + 8.0 * 65536) * 50 / 1e9)
+    # 99 steps: 49 two-step launches and one single step, the same launch count and bytes
+    assert bench.kernel_work(w, 32, 65536, 42.0, 2, 1024, 1, 99)["lbm_step"] == work["lbm_step"]
+
+
+def test_all_core_oracle_baseline_sums_concurrent_samples(monkeypatch):
+    calls = []
+
+    def fake(wname, seconds):
+        calls.append((wname, seconds))
+        return {"value": 10.0, "unit": bench.UNIT, "cores": 1, "kind": "oracle",
+                "sample": "s"}
+    monkeypatch.setattr(bench, "run_oracle_subprocess", fake)
+    monkeypatch.setattr(bench.os, "cpu_count", lambda: 6)
+    r = bench.run_oracle_all_cores("tgv32_k8", 1.5)
+    assert r["cores"] == 6 and r["value"] == pytest.approx(60.0)
+    assert calls == [("tgv32_k8", 1.5)] * 6
+    assert r["sample"].startswith("6 concurrent single-threaded samples")
