@@ -451,9 +451,11 @@ def oracle_sample(wname: str, seconds: float) -> dict:
     t_pt = (time.perf_counter() - t0) / npt
     t_cycle = w.steps_per_cycle * t_lbm + t_obs + npts * t_pt
     return {"value": npts / t_cycle, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"{nl} LBM step(s) of the full {k}-member {nx}x{ny} ensemble and {npt} of "
-                       f"{npts} grid-point analyses (FP64 NumPy, one thread), extrapolated to one "
-                       f"cycle of {w.steps_per_cycle} steps + {npts} analyses"),
+            "sample": (f"{nl} LBM step(s) of the full {k}-member {nx}x{ny} ensemble and {npt} "
+                       f"grid-point analyses at random points of the {npts} (FP64 NumPy, one "
+                       f"thread), extrapolated to one cycle of {w.steps_per_cycle} steps + "
+                       f"{npts} analyses"),
+            "lbm_mlups_per_member": npts / t_lbm / 1e6,
             "seconds_per_cycle": t_cycle}
 
 
