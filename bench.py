@@ -40,8 +40,9 @@ FLUSH_BYTES = 256 << 20
 FP32_LANES_PER_SM = 128
 SMS = 152
 
-# Algorithmic work per unit (stated with the derivations in the design doc):
-#   lbm_step      72 B per lattice update (9 loads + 9 stores of FP32) + 8 B per node of force
+# Algorithmic work per unit:
+#   lbm_step      72 B per node and member per launch (one FP32 read and one write of the nine
+#                 populations; two time steps per launch) + 8 B per node of force
 #   transpose     2 x 36 k B per grid point (read + write of the 9 x k block)
 #   obs_operator  36 B per (observation point, member) read + 4 V B per (point, member) written x2
 #   gram          2 k^2 flops per local observed scalar per grid point

@@ -8,7 +8,7 @@ with (i, j) in {-1, 0, 1}^2 (D2Q9), lattice units c = dx = dt = 1, the
 lattice-BGK collision Omega = -(f - f^eq) / tau and a body force F, and the
 moments of Eqs. 2-5: rho = sum f, u = (1/rho) sum c f.
 
-Readings where the paper is silent (listed in the design doc):
+Readings where the paper is silent:
   * population index q = 3 (j + 1) + (i + 1) for c_q = (i, j);
   * f^eq is the standard second-order D2Q9 equilibrium
     w_q rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u), weights 4/9, 1/9, 1/36;
