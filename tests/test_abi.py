@@ -100,3 +100,46 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.letkf_destroy(None) == L.LETKF_OK
     assert lib.lbm_forecast(None, 1) == L.LETKF_EINVAL
     assert lib.letkf_analyze(None, None, 0) == L.LETKF_EINVAL
+
+
+def test_header_constants_match_the_binding():
+    src = open(os.path.join(ROOT, "include", "letkf.h")).read()
+    defines = dict(re.findall(r"^#define\s+(LETKF_\w+)\s+\(?(-?\d+)\)?\s*(?:/\*|$)", src,
+                              flags=re.M))
+    checked = 0
+    for name, value in defines.items():
+        if hasattr(L, name):
+            assert getattr(L, name) == int(value), name
+            checked += 1
+    for name in ("LETKF_LOC_GC", "LETKF_EIG_SPLIT", "LETKF_MIXED", "LETKF_ENOMEM"):
+        assert name in defines and hasattr(L, name), name
+    assert checked >= 20
+    scratch = re.search(r"#define\s+LETKF_NOALLOC_SCRATCH_BYTES\s+\((\d+)u\s*<<\s*(\d+)\)", src)
+    assert int(scratch.group(1)) << int(scratch.group(2)) == L.LETKF_NOALLOC_SCRATCH_BYTES
+
+
+def test_gaspari_cohn_localization_needs_a_radius(lib):
+    assert L.letkf_workspace_size(_cfg(loc_kind=L.LETKF_LOC_GC)) > 0
+    with pytest.raises(L.LetkfError):
+        L.letkf_workspace_size(_cfg(loc_kind=L.LETKF_LOC_GC, loc_radius=0.0))
+
+
+def test_eigensolver_workspace_query_and_argument_checks(lib):
+    # host-side checks only: none of these calls reaches the device
+    small = L.letkf_eigh_workspace_bytes(1000, 32)
+    assert small > 1000 * (32 * 32 + 4 * 32) * 8
+    assert L.letkf_eigh_workspace_bytes(4000, 32) > 3 * small
+    assert L.letkf_eigh_workspace_bytes(-1, 32) == 0
+    assert L.letkf_eigh_workspace_bytes(10, 1) == 0
+    assert L.letkf_eigh_workspace_bytes(10, 129) == 0
+    fake = 1 << 20                                    # never dereferenced by these calls
+    assert L.letkf_eigh_batch_ws(0, 32, fake, fake, 0, 0, 0, 0, None) == L.LETKF_OK
+    assert L.letkf_eigh_batch_ws(4, 1, fake, fake, 0, 0, fake, 1 << 20, None) == L.LETKF_EINVAL
+    assert L.letkf_eigh_batch_ws(4, 32, fake, fake, 0, 2, fake, 1 << 20, None) == L.LETKF_EINVAL
+    assert L.letkf_eigh_batch_ws(4, 32, 0, fake, 0, 0, fake, 1 << 20, None) == L.LETKF_EINVAL
+    need = L.letkf_eigh_workspace_bytes(4, 32)
+    assert L.letkf_eigh_batch_ws(4, 32, fake, fake, 0, 0, fake, need - 1, None) \
+        == L.LETKF_ENOMEM
+    assert L.letkf_eigh_batch_ws(4, 32, fake, fake, 0, 0, fake + 8, need, None) \
+        == L.LETKF_ENOMEM
+    assert L.letkf_eigh_batch_ws(4, 32, fake, fake, 0, 0, 0, need, None) == L.LETKF_ENOMEM
