@@ -312,7 +312,19 @@ def _ptr_where(t):
 
 
 class Experiment:
-    """One DA experiment: owns a libletkf handle, its torch-allocated workspace and stream."""
+    """One DA experiment: owns a libletkf handle, its torch-allocated workspace and stream.
+
+    nx, ny, k, tau          periodic grid, ensemble size, BGK relaxation time
+    obs_xy, obs_err_var     [L][2] observation points and the [L*V] diagonal of R
+    obs_vars                LETKF_OBS_* bits (rho, u, v)
+    loc_radius, loc_kind    radius r and LETKF_LOC_GAUSS / LETKF_LOC_GC; loc_radius=None
+                            means no localization; loc_cutoff2 overrides the default cutoff
+                            (40/3) r^2
+    force, n_aux, infl      [2][ny][nx] body force, auxiliary members (never analysed, e.g. a
+                            nature run), multiplicative inflation
+    precision, eig_schedule LETKF_FP32 / LETKF_MIXED, LETKF_EIG_*
+    chunk_bytes, stream, device   Gram chunk budget (0: library default), torch stream, device
+    """
 
     def __init__(self, nx, ny, k, tau, obs_xy, obs_err_var, obs_vars=LETKF_OBS_U | LETKF_OBS_V,
                  loc_radius=None, loc_cutoff2=0.0, force=None, n_aux=0, infl=1.0,
