@@ -259,6 +259,36 @@ def test_infinite_localization_equals_brute_force_kalman_filter(k):
     assert all(np.allclose(W, Ws[0], atol=1e-12) for W in Ws)
 
 
+@pytest.mark.parametrize("k,rho", [(4, 1.1), (6, 1.5), (8, 1.1), (8, 1.5)])
+def test_inflated_analysis_equals_kalman_filter_on_inflated_covariance(k, rho):
+    # Multiplicative inflation rho scales the background covariance: Pf = rho dX dX^T / (k-1)
+    # (Eq. enkf_p times rho).  With a linear H and no localization, the LETKF's
+    # Q = (k-1)/rho I + dY^T R^-1 dY must then give the KF's mean x^f + K (yo - H x^f) and the
+    # KF's covariance (I - K H) rho Pb (Eqs. kfx, kfp, kfk with rho Pb).  A mistaken
+    # (k-1) rho, or an inflation of only one of the mean and the perturbations, fails here.
+    nx = ny = 4
+    f = _small_ensemble(k, nx, ny, 700 + k)
+    net = np.array([[1, 0], [3, 2], [0, 3]], dtype=np.int32)
+    H = _linear_h(net, nx, ny)
+    X = f.reshape(k, -1).T
+    Yf = (H @ X).T
+    rvar = np.array([2e-4, 1e-4, 1e-4, 5e-4, 3e-4, 2e-4])
+    yo = H @ X.mean(axis=1) + gaussian((6,), 0.01, 17)
+    Xa, _ = letkf.analyze(f, Yf, yo, net, rvar, math.inf, math.inf,
+                          obs.VAR_RHO | obs.VAR_U, infl=rho)
+    Pb = kalman.ensemble_covariance(X)
+    xa_kf, Pa_kf, _ = kalman.kalman_analysis(X.mean(axis=1), rho * Pb, H, np.diag(rvar), yo)
+    Xa_flat = Xa.reshape(k, -1).T
+    incr = xa_kf - X.mean(axis=1)
+    assert np.allclose(Xa_flat.mean(axis=1) - X.mean(axis=1), incr,
+                       atol=1e-10 * np.abs(incr).max())
+    Pa = kalman.ensemble_covariance(Xa_flat)
+    assert np.allclose(Pa, Pa_kf, atol=1e-10 * np.abs(Pa_kf).max())
+    # and it differs from the uninflated analysis by more than rounding
+    _, Pa_1, _ = kalman.kalman_analysis(X.mean(axis=1), Pb, H, np.diag(rvar), yo)
+    assert np.abs(Pa_kf - Pa_1).max() > 1e-3 * np.abs(Pa_kf).max()
+
+
 def test_infinite_localization_equals_global_etkf():
     k, nx, ny = 8, 5, 4
     f = _small_ensemble(k, nx, ny, 300)
