@@ -55,7 +55,7 @@ def parse_args(argv=None):
     p.add_argument("--steps", type=int, default=None, help="timed cycles (default per workload)")
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", default="turb256_k32")
+    p.add_argument("--workload", default="turb1024_k64")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--chunk-mb", type=float, default=0.0,
                    help="Gram buffer per analysis chunk in MiB (0: the library default)")
@@ -74,7 +74,11 @@ def parse_args(argv=None):
                    help="serve_cfg5: HBM budget for resident experiments")
     p.add_argument("--serve-max-active", type=int, default=8,
                    help="serve_cfg5: most experiments on the GPU at once")
+    p.add_argument("--no-error-check", action="store_true",
+                   help="skip the error measurement against the FP64 oracle")
     p.add_argument("--_oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--_oracle-steps", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--_oracle-error-prep", default=None, help=argparse.SUPPRESS)
     return p.parse_args(argv)
 
 
@@ -209,7 +213,7 @@ def measured_peaks():
 
 EIG_SCHEDULES = {"auto": 0, "fused": 1, "split": 2}
 EIG_NAMES = {1: "fused", 2: "split", 3: "split_check"}
-PEAK_NAMES = {"hbm": "hbm_gbs", "alu": "FP32 FMA at max SM clock",
+PEAK_NAMES = {"hbm": "hbm_gbs", "alu": "FP32 FMA peak from the unit counts at max SM clock",
               "tensor": "bf16_tflops_sustained (FP16 operands, same nominal rate)"}
 
 
@@ -268,7 +272,7 @@ def roofline_table(work, ms, peaks, sm_mhz, tensor_gram=False):
                          "unit": "TFLOP/s", "frac": achieved / peak}
         else:
             achieved = amount / (t / 1e3)
-            peak = fp32_peak_tflops(sm_mhz)
+            peak = peaks.get("fp32_tflops") or fp32_peak_tflops(sm_mhz)
             out[name] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak}
         out[name].update({"ms_per_cycle": t, "share": t / total, "launches_per_cycle": launches,
@@ -406,77 +410,134 @@ def nature_observations(spin, w, ncycles, seed_offset=0):
 
 
 # ----------------------------------------------------------------------------- CPU oracle leg
+#
+# Everything below that touches oracle/ runs in a CPU subprocess of this script (the CPU
+# baseline, the reference arm and the oracle side of the error measurement); the GPU process
+# never imports the oracle.
+
+SUB_EDGE = 256          # the oracle's D2Q9 step and moments are timed on a sub-block this wide
+
+
+class OracleSample:
+    """The FP64 oracle, as it stands, on a bounded sample of one cycle of a workload.
+
+    One cycle = steps_per_cycle D2Q9 steps of the k members, the observation operator and one
+    local analysis per grid point.  Sampled: the oracle's D2Q9 step and its moments on a
+    periodic sub-block of at most 256 x 256 nodes (the cost per node is the same on any grid),
+    scaled by the node count; the oracle's local analysis (local observation search over the
+    full network, Gram matrix, eigendecomposition, transform, update) at random grid points of
+    the full grid, scaled by the point count."""
+
+    def __init__(self, wname: str):
+        import numpy as np
+
+        import synth
+        from oracle import lbm, obs as oobs
+        self.np, self.lbm, self.oobs = np, lbm, oobs
+        w = self.w = synth.WORKLOADS[wname]
+        k = w.k
+        sx, sy = min(w.nx, SUB_EDGE), min(w.ny, SUB_EDGE)
+        self.sub = (sx, sy)
+        self.scale = w.n_points / (sx * sy)
+        ux0, uy0 = synth.taylor_green_velocity(sx, sy, 0.05)
+        self.f = np.empty((k, 9, sy, sx))
+        for m in range(k):
+            self.f[m] = lbm.equilibrium(np.ones((sy, sx)), ux0 + synth.gaussian((sy, sx), 5e-3, m),
+                                        uy0 + synth.gaussian((sy, sx), 5e-3, 1000 + m))
+        fx, fy = w.force()
+        self.fx, self.fy = fx[:sy, :sx], fy[:sy, :sx]
+        self.net_sub = synth.regular_obs_network(sx, sy, w.obs_stride)
+        # forecast observations of the full network (a random flow's equilibria at the
+        # observation points), for the local analyses
+        self.net = w.obs_network()
+        L = len(self.net)
+        rx = synth.gaussian((k, 1, L), 0.02, 21)
+        ry = synth.gaussian((k, 1, L), 0.02, 22)
+        strip = lbm.equilibrium(np.ones((k, 1, L)), rx, ry)
+        strip_xy = np.stack([np.arange(L), np.zeros(L, dtype=np.int64)], axis=1)
+        self.Yf = oobs.observe(strip, strip_xy, oobs.VAR_U | oobs.VAR_V)
+        self.yo = self.Yf.mean(0) + synth.gaussian(self.Yf.shape[1], w.obs_sigma, 7)
+        self.var = w.obs_error_var(self.Yf.shape[1])
+        self.ybar, self.dY = oobs.ensemble_obs(self.Yf)
+        self.c2 = synth.loc_cutoff2(w.loc_radius)
+        self.rng = synth.generator(11)
+
+    def step(self, seconds: float) -> dict:
+        """One sample of about `seconds` of CPU work, extrapolated to one cycle."""
+        from oracle import letkf as oletkf
+        np, lbm, oobs, w = self.np, self.lbm, self.oobs, self.w
+        sx, sy = self.sub
+        t0 = time.perf_counter()
+        nl = 0
+        while nl < 1 or (time.perf_counter() - t0 < 0.2 * seconds and nl < 5):
+            self.f = lbm.step(self.f, w.tau, self.fx, self.fy)
+            nl += 1
+        t_lbm = (time.perf_counter() - t0) / nl * self.scale
+        t0 = time.perf_counter()
+        oobs.observe(self.f, self.net_sub, oobs.VAR_U | oobs.VAR_V)
+        t_obs = (time.perf_counter() - t0) * self.scale
+        t0 = time.perf_counter()
+        npt = 0
+        while npt < 8 or time.perf_counter() - t0 < 0.7 * seconds:
+            x, y = int(self.rng.integers(w.nx)), int(self.rng.integers(w.ny))
+            dYl, dl, rl, _ = oletkf.point_inputs(x, y, self.Yf, self.yo, self.net, self.var,
+                                                 w.nx, w.ny, w.loc_radius, self.c2,
+                                                 oobs.VAR_U | oobs.VAR_V, ybar=self.ybar,
+                                                 dY=self.dY)
+            oletkf.local_analysis(self.f[:, :, y % sy, x % sx].T, dYl, dl, rl)
+            npt += 1
+        t_pt = (time.perf_counter() - t0) / npt
+        t_cycle = w.steps_per_cycle * t_lbm + t_obs + w.n_points * t_pt
+        return {"value": w.n_points / t_cycle, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": (f"{nl} D2Q9 step(s) and the moments of the {w.k} members on a "
+                           f"{sx}x{sy} periodic sub-block (x{self.scale:g} nodes to the "
+                           f"{w.nx}x{w.ny} grid) and {npt} local analyses at random points of "
+                           f"the {w.n_points} (FP64 NumPy, one thread), extrapolated to one "
+                           f"cycle of {w.steps_per_cycle} steps + {w.n_points} analyses"),
+                "lbm_mlups_per_member": w.n_points / t_lbm / 1e6,
+                "seconds_per_cycle": t_cycle}
+
 
 def oracle_sample(wname: str, seconds: float) -> dict:
-    """Time the FP64 oracle on a bounded sample of one cycle of the workload.
-
-    The cycle is extrapolated from (a) LBM steps of the full ensemble and (b) as many
-    grid-point analyses as fit in the time budget."""
-    import numpy as np
-
-    import synth
-    from oracle import lbm, obs as oobs, letkf as oletkf
-
-    w = synth.WORKLOADS[wname]
-    k, nx, ny = w.k, w.nx, w.ny
-    npts = nx * ny
-    ux0, uy0 = synth.taylor_green_velocity(nx, ny, 0.05)
-    f = np.empty((k, 9, ny, nx))
-    for m in range(k):
-        f[m] = lbm.equilibrium(np.ones((ny, nx)), ux0 + synth.gaussian((ny, nx), 5e-3, m),
-                               uy0 + synth.gaussian((ny, nx), 5e-3, 1000 + m))
-    fx, fy = w.force()
-    t0 = time.perf_counter()
-    nl = 0
-    while nl < 1 or (time.perf_counter() - t0 < 0.25 * seconds and nl < 5):
-        f = lbm.step(f, w.tau, fx, fy)
-        nl += 1
-    t_lbm = (time.perf_counter() - t0) / nl
-    net = w.obs_network()
-    t0 = time.perf_counter()
-    Yf = oobs.observe(f, net, oobs.VAR_U | oobs.VAR_V)
-    t_obs = time.perf_counter() - t0
-    yo = Yf.mean(0) + synth.gaussian(Yf.shape[1], w.obs_sigma, 7)
-    var = w.obs_error_var(Yf.shape[1])
-    ybar, dY = oobs.ensemble_obs(Yf)
-    c2 = synth.loc_cutoff2(w.loc_radius)
-    rng = synth.generator(11)
-    t0 = time.perf_counter()
-    npt = 0
-    while npt < 16 or time.perf_counter() - t0 < 0.7 * seconds:
-        x, y = int(rng.integers(nx)), int(rng.integers(ny))
-        dYl, dl, rl, _ = oletkf.point_inputs(x, y, Yf, yo, net, var, nx, ny, w.loc_radius, c2,
-                                             oobs.VAR_U | oobs.VAR_V, ybar=ybar, dY=dY)
-        oletkf.local_analysis(f[:, :, y, x].T, dYl, dl, rl)
-        npt += 1
-    t_pt = (time.perf_counter() - t0) / npt
-    t_cycle = w.steps_per_cycle * t_lbm + t_obs + npts * t_pt
-    return {"value": npts / t_cycle, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"{nl} LBM step(s) of the full {k}-member {nx}x{ny} ensemble and {npt} "
-                       f"grid-point analyses at random points of the {npts} (FP64 NumPy, one "
-                       f"thread), extrapolated to one cycle of {w.steps_per_cycle} steps + "
-                       f"{npts} analyses"),
-            "lbm_mlups_per_member": npts / t_lbm / 1e6,
-            "seconds_per_cycle": t_cycle}
+    return OracleSample(wname).step(seconds)
 
 
-def run_oracle_subprocess(wname: str, seconds: float) -> dict:
+def oracle_steps(wname: str, steps: int, warmup: int, seconds: float) -> dict:
+    """The reference arm's steps in one process: the set-up once, then warmup + steps bounded
+    samples of one cycle each."""
+    s = OracleSample(wname)
+    for _ in range(warmup):
+        s.step(seconds)
+    runs = [s.step(seconds) for _ in range(steps)]
+    return {"seconds_per_cycle": [r["seconds_per_cycle"] for r in runs],
+            "sample": runs[-1]["sample"]}
+
+
+def _oracle_env():
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     for key in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT"):
         env.pop(key, None)
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--_oracle-sample", "--workload",
-                        wname, "--cpu-sample-seconds", str(seconds)], capture_output=True,
-                       text=True, env=env, timeout=600)
+    return env
+
+
+def _run_self(extra, timeout=900):
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), *extra], capture_output=True,
+                       text=True, env=_oracle_env(), timeout=timeout)
     if r.returncode != 0:
-        raise RuntimeError(f"oracle sample failed: {r.stderr[-2000:]}")
+        raise RuntimeError(f"oracle subprocess {extra[:2]} failed: {r.stderr[-2000:]}")
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def run_oracle_subprocess(wname: str, seconds: float) -> dict:
+    return _run_self(["--_oracle-sample", "--workload", wname, "--cpu-sample-seconds",
+                      str(seconds)])
 
 
 def run_oracle_all_cores(wname: str, seconds: float) -> dict:
     """The oracle on every host core at once: one single-threaded sample process per core
     (grid points are independent), the aggregate rate their sum.  The process count is
-    capped so that the samples' FP64 ensembles take at most half the host memory."""
+    capped so that the samples' FP64 arrays take at most half the host memory."""
     import concurrent.futures as cf
 
     import synth
@@ -486,7 +547,9 @@ def run_oracle_all_cores(wname: str, seconds: float) -> dict:
         mem = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
     except (ValueError, OSError, AttributeError):
         mem = 0
-    per_proc = 3 * 8 * 9 * (w.k + 1) * w.n_points  # the FP64 ensemble and its LBM copies
+    sub = min(w.nx, SUB_EDGE) * min(w.ny, SUB_EDGE)
+    # the sub-block ensemble and its D2Q9 temporaries, plus the full network's observations
+    per_proc = 6 * 8 * 9 * w.k * sub + 4 * 8 * 9 * w.k * len(w.obs_network())
     n = cores if mem <= 0 else max(1, min(cores, int(0.5 * mem // per_proc)))
     with cf.ThreadPoolExecutor(max_workers=n) as ex:
         runs = list(ex.map(lambda _: run_oracle_subprocess(wname, seconds), range(n)))
@@ -501,15 +564,10 @@ def reference_main(args):
         return 0
     wname = args.workload
     steps = args.steps if args.steps is not None else 3
-    per = max(2.0, min(args.cpu_sample_seconds, 150.0 / max(1, steps + args.warmup)))
-    for _ in range(args.warmup):
-        run_oracle_subprocess(wname, per)
-    vals, secs = [], []
-    for _ in range(steps):
-        s = run_oracle_subprocess(wname, per)
-        vals.append(s["value"])
-        secs.append(s["seconds_per_cycle"])
-        sample = s["sample"]
+    per = max(1.0, min(args.cpu_sample_seconds, 150.0 / max(1, steps + args.warmup)))
+    r = _run_self(["--_oracle-steps", "--workload", wname, "--steps", str(steps), "--warmup",
+                   str(args.warmup), "--cpu-sample-seconds", str(per)], timeout=1800)
+    secs = r["seconds_per_cycle"]
     import synth
     w = synth.WORKLOADS[wname]
     value = w.n_points * steps / sum(secs)
@@ -518,11 +576,103 @@ def reference_main(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(w),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": (f"each step a bounded sample of about {per:g} s, "
+                                        "extrapolated to one cycle (ms_per_step is that "
+                                        "extrapolated cycle time, not wall time): " +
+                                        r["sample"])},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+# ----------------------------------------------------------------------------- error vs oracle
+
+ERR_POINTS = 32
+
+
+def oracle_error_prep(wname: str, outdir: str, npoints: int = ERR_POINTS) -> dict:
+    """Oracle side of the error measurement (CPU subprocess).  Writes to outdir:
+      f0.npy      FP32 [k, 9, ny, nx] forecast ensemble: the oracle's equilibria of a seeded
+                  band-limited flow (RMS 0.05, wavenumbers 2-6) plus N(0, member_sigma^2)
+                  velocity perturbations per member and node; the GPU's input
+      yo.npy      FP32 [L*V] observations: the flow's (u, v) at the observation points plus
+                  N(0, obs_sigma^2)
+      points.npy  [n, 2] sampled grid points (the four corners, the centre, seeded others)
+      ref.npy     [n, k, 9] the oracle's analysis blocks there (Algorithm 1 per point, FP64,
+                  as deviations f - w from rest)
+      xf.npy      [n, k, 9] the forecast blocks there (f0 - w, FP64)
+      nloc.npy    [n] local observation points"""
+    import numpy as np
+
+    import synth
+    from oracle import lbm, obs as oobs, letkf as oletkf
+    w = synth.WORKLOADS[wname]
+    k, nx, ny = w.k, w.nx, w.ny
+    tx, ty = synth.band_limited_force(nx, ny, 2.0, 6.0, 0.05, w.seed + 71)
+    f0 = np.lib.format.open_memmap(os.path.join(outdir, "f0.npy"), mode="w+", dtype=np.float32,
+                                   shape=(k, 9, ny, nx))
+    for m in range(k):
+        ux = tx + synth.gaussian((ny, nx), w.member_sigma, w.seed + 100 + 2 * m)
+        uy = ty + synth.gaussian((ny, nx), w.member_sigma, w.seed + 101 + 2 * m)
+        f0[m] = lbm.equilibrium(np.ones((ny, nx)), ux, uy)
+    f0.flush()
+    net = w.obs_network()
+    L = len(net)
+    xs, ys = net[:, 0], net[:, 1]
+    strip_xy = np.stack([np.arange(L), np.zeros(L, dtype=np.int64)], axis=1)
+    truth = lbm.equilibrium(np.ones((1, L)), tx[ys, xs][None], ty[ys, xs][None])
+    uv = oobs.VAR_U | oobs.VAR_V
+    yo = (oobs.observe(truth, strip_xy, uv) + synth.gaussian(2 * L, w.obs_sigma, w.seed + 72))
+    yo = yo.astype(np.float32)
+    np.save(os.path.join(outdir, "yo.npy"), yo)
+    Yf = oobs.observe(np.asarray(f0[:, :, ys, xs], np.float64)[:, :, None, :], strip_xy, uv)
+    ybar, dY = oobs.ensemble_obs(Yf)
+    var = w.obs_error_var(2 * L)
+    c2 = synth.loc_cutoff2(w.loc_radius)
+    rng = synth.generator(w.seed + 73)
+    pts = {(0, 0), (nx - 1, ny - 1), (0, ny - 1), (nx - 1, 0), (nx // 2, ny // 2)}
+    while len(pts) < npoints:
+        pts.add((int(rng.integers(nx)), int(rng.integers(ny))))
+    pts = sorted(pts)
+    ref, xf, nloc = [], [], []
+    for (x, y) in pts:
+        dYl, dl, rl, n = oletkf.point_inputs(x, y, Yf, yo.astype(np.float64), net, var, nx, ny,
+                                             w.loc_radius, c2, uv, ybar=ybar, dY=dY)
+        xb = np.asarray(f0[:, :, y, x], np.float64)          # [k, 9]
+        res = oletkf.local_analysis(xb.T, dYl, dl, rl)
+        ref.append(res["Xa"].T - lbm.W[None, :])
+        xf.append(xb - lbm.W[None, :])
+        nloc.append(n)
+    np.save(os.path.join(outdir, "points.npy"), np.asarray(pts, dtype=np.int64))
+    np.save(os.path.join(outdir, "ref.npy"), np.stack(ref))
+    np.save(os.path.join(outdir, "xf.npy"), np.stack(xf))
+    np.save(os.path.join(outdir, "nloc.npy"), np.asarray(nloc, dtype=np.int64))
+    return {"points": len(pts), "mean_local_obs": float(np.mean(nloc))}
+
+
+def block_errors(got, ref, xf):
+    """Relative L2 errors of analysis blocks [n, k, 9] against the reference: the ensemble mean
+    (over all sampled points and populations), the mean increment (mean - forecast mean), the
+    perturbations about the mean; and the worst single point of each."""
+    import numpy as np
+
+    def rel(a, b):
+        d = np.linalg.norm(b)
+        return float(np.linalg.norm(a - b) / (d if d > 0 else 1.0))
+
+    got, ref, xf = (np.asarray(a, np.float64) for a in (got, ref, xf))
+    mg, mo, mf = got.mean(1), ref.mean(1), xf.mean(1)         # [n, 9]
+    out = {"mean": rel(mg, mo), "increment": rel(mg - mf, mo - mf),
+           "perturbations": rel(got - mg[:, None], ref - mo[:, None])}
+    worst = [0.0, 0.0, 0.0]
+    for i in range(got.shape[0]):
+        e = (rel(mg[i], mo[i]), rel(mg[i] - mf[i], mo[i] - mf[i]),
+             rel(got[i] - mg[i], ref[i] - mo[i]))
+        worst = [max(a, b) for a, b in zip(worst, e)]
+    out.update({"worst_point_mean": worst[0], "worst_point_increment": worst[1],
+                "worst_point_perturbations": worst[2]})
+    return out
 
 
 def workload_config(w, precision="fp32"):
@@ -539,6 +689,13 @@ def main(argv=None):
     args = parse_args(argv)
     if args._oracle_sample:
         print(json.dumps(oracle_sample(args.workload, args.cpu_sample_seconds)))
+        return 0
+    if args._oracle_steps:
+        print(json.dumps(oracle_steps(args.workload, args.steps, args.warmup,
+                                      args.cpu_sample_seconds)))
+        return 0
+    if args._oracle_error_prep:
+        print(json.dumps(oracle_error_prep(args.workload, args._oracle_error_prep)))
         return 0
     if args.impl == "reference":
         return reference_main(args)
@@ -576,8 +733,9 @@ def main(argv=None):
              "both": [L.LETKF_FP32, L.LETKF_MIXED]}[args.precision]
     sched = EIG_SCHEDULES[args.eig_schedule]
     chunk = int(args.chunk_mb * (1 << 20))
-    results = [measure(w, members, setup, yos, device, prec, steps, warm, world, sched, chunk)
-               for prec in forms]
+    peak32 = measure_fp32_peak(device)
+    results = [measure(w, members, setup, yos, device, prec, steps, warm, world, sched, chunk,
+                       peak32) for prec in forms]
     head = results[0]
     ncyc = 20
     rmse = {"cycles": ncyc, "averaged_over": f"cycles {ncyc // 2}..{ncyc - 1}",
@@ -609,9 +767,17 @@ def main(argv=None):
         line["mixed"]["kernels"] = {n: {"ms_per_cycle": d["ms_per_cycle"], "frac": d["frac"],
                                          "unit": d["unit"]} for n, d in mx["kernels"].items()}
         line["mixed"]["speedup_vs_fp32"] = mx["value"] / head["value"]
-        line["mixed"]["error"] = ("analysis vs the FP64 oracle, relative L2 (tests): "
-                                  "same bar as FP32 (1e-5); measured 0.9e-6 mean, 2.9e-6 "
-                                  "increment, 2.8e-6 perturbations at 1024^2, k = 64")
+    line["fp32_peak"] = peak32
+    if rank == 0 and world == 1 and not args.no_error_check:
+        # outside the timed region: one analysis of each form on a seeded synthetic ensemble
+        # of the workload's shape, compared with the FP64 oracle at sampled grid points
+        try:
+            err = measure_error(w, setup, device, forms, sched, chunk)
+        except Exception as e:  # the timing stands; say why the error is missing
+            err = {"error": str(e)[-300:]}
+        line["error_vs_oracle"] = err
+        if line["mixed"] is not None:
+            line["mixed"]["error"] = err.get("mixed", err.get("error"))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = run_oracle_subprocess(args.workload, args.cpu_sample_seconds)
@@ -918,8 +1084,83 @@ def serve_main(args, device, rank, world):
     return 0
 
 
+def measure_fp32_peak(device, iters=8192, reps=100):
+    """FP32 FMA peak of this GPU, measured by the library's microbenchmark kernel (independent
+    FMA chains filling every SM), timed with CUDA events on the launching stream; the median
+    over reps launches, clocks sampled while they run."""
+    import torch
+
+    from paper_2308_03310_gb300 import letkf as L
+    blocks, threads = L.letkf_fp32_peak_grid()
+    out = torch.empty(blocks * threads, dtype=torch.float32, device=device)
+    stream = torch.cuda.current_stream(device)
+    for _ in range(3):
+        L.letkf_fp32_peak_run(iters, out.data_ptr(), stream.cuda_stream)
+    torch.cuda.synchronize(device)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    with ClockSampler(device.index) as clk:
+        for a, b in ev:
+            a.record(stream)
+            flops = L.letkf_fp32_peak_run(iters, out.data_ptr(), stream.cuda_stream)
+            b.record(stream)
+        torch.cuda.synchronize(device)
+    rates = sorted(flops / (a.elapsed_time(b) * 1e-3) / 1e12 for a, b in ev)
+    assert torch.isfinite(out).all()
+    return {"tflops": statistics.median(rates), "best_tflops": rates[-1],
+            "launch": f"{blocks} x {threads} threads, 16 FMA chains x {8 * iters} rounds each",
+            "clocks": clk.summary()}
+
+
+def measure_error(w, setup, device, forms, eig_schedule=0, chunk_bytes=0):
+    """Error of each form against the FP64 oracle at the workload's full size: the oracle
+    subprocess writes a seeded synthetic ensemble of the workload's shape, observations and
+    its own local analyses at sampled grid points; here each form analyses that ensemble once
+    (the same handle configuration as the timed cycles) and its analysis blocks at the sampled
+    points are compared with the oracle's."""
+    import numpy as np
+    import torch
+
+    from paper_2308_03310_gb300 import letkf as L
+    net, var, kw = setup
+    out = {}
+    with tempfile.TemporaryDirectory(prefix="letkf_err_") as d:
+        info = _run_self(["--_oracle-error-prep", d, "--workload", w.name], timeout=1800)
+        f0 = np.load(os.path.join(d, "f0.npy"), mmap_mode="r")
+        yo = np.load(os.path.join(d, "yo.npy"))
+        pts = np.load(os.path.join(d, "points.npy"))
+        ref = np.load(os.path.join(d, "ref.npy"))
+        xf = np.load(os.path.join(d, "xf.npy"))
+        xs = torch.as_tensor(pts[:, 0], device=device)
+        ys = torch.as_tensor(pts[:, 1], device=device)
+        for prec in forms:
+            exp = L.Experiment(w.nx, w.ny, w.k, w.tau, net, var, device=device, precision=prec,
+                               eig_schedule=eig_schedule, chunk_bytes=chunk_bytes, **kw)
+            exp.set_state(f0)
+            exp.analyze(yo)
+            buf = torch.empty((w.k, 9, w.ny, w.nx), dtype=torch.float32, device=device)
+            torch.cuda.synchronize(device)
+            L.letkf_get_deviation(exp.h, buf.data_ptr(), 0, w.k, L.LETKF_DEVICE)
+            torch.cuda.synchronize(device)
+            rc = exp.sync()
+            if rc:
+                raise RuntimeError(f"error-check analysis failed: {L.strerror(rc)}")
+            got = buf[:, :, ys, xs].permute(2, 0, 1).double().cpu().numpy()   # [n, k, 9]
+            out["mixed" if prec == L.LETKF_MIXED else "fp32"] = block_errors(got, ref, xf)
+            exp.close()
+            del buf
+            torch.cuda.empty_cache()
+    out.update({"points": int(len(pts)), "mean_local_obs_at_points": info["mean_local_obs"],
+                "bar": 1e-5, "reference": "FP64 oracle (oracle.letkf.local_analysis)",
+                "unit": "relative L2 over the sampled points' 9 x k blocks, in f - w",
+                "input": ("a seeded band-limited flow (RMS 0.05) + N(0, member_sigma^2) member "
+                          "perturbations, equilibria by the oracle, FP32; the workload's "
+                          "network, R and localization")})
+    return out
+
+
 def measure(w, members, setup, yos, device, precision, steps, warm, world, eig_schedule=0,
-            chunk_bytes=0):
+            chunk_bytes=0, peak32=None):
     """Time `steps` cycles of one precision form (device-resident inputs), then the same
     through the public API with host buffers."""
     import numpy as np
@@ -978,6 +1219,8 @@ def measure(w, members, setup, yos, device, precision, steps, warm, world, eig_s
         "transpose_out": statistics.mean(p["transpose_out_ms"] for p in phase),
     }
     peaks = measured_peaks()
+    if peak32:
+        peaks["fp32_tflops"] = peak32["tflops"]
     sm_mhz = peaks["sm_max_mhz"] or 2070.0
     work = kernel_work(w, w.k, w.n_points, st.mean_local_obs, exp.V, exp.L, st.n_chunks,
                        w.steps_per_cycle)
@@ -989,7 +1232,11 @@ def measure(w, members, setup, yos, device, precision, steps, warm, world, eig_s
     roofline = {"kernel": top, "bound": t["bound"], "achieved": t["achieved"], "peak": t["peak"],
                 "unit": t["unit"], "frac": t["frac"],
                 "traffic": traffic_for(top, w.name),
-                "peak_source": f"{peaks['source']} ({PEAK_NAMES[t['bound']]})",
+                "peak_source": (f"{peaks['source']} ({PEAK_NAMES[t['bound']]})"
+                                if t["bound"] != "alu" or not peak32 else
+                                "measured in this run: FP32 FMA microbenchmark "
+                                "(letkf_fp32_peak_run, median of 100 launches; "
+                                f"{peak32['launch']})"),
                 "algorithmic_per_launch": amount / launches,
                 "algorithmic_unit": "GB" if unit == "GB" else "TFLOP",
                 "ms_per_launch": t["ms_per_launch"]}

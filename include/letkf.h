@@ -267,28 +267,33 @@ int letkf_group_cycle(letkf_handle *const *hs, int32_t n, int32_t nsteps,
  * processes whose device memory is all reserved by another allocator, or loops in which an
  * allocation, and the device synchronisation it can imply, is not allowed.
  *
- * It runs the analysis steps of Algorithm 1 for npts independent local problems given in the
- * paper's padded local layout, and allocates nothing: its only scratch (the k x k Gram
- * matrices, the c vectors, the local counts and a status word) sits in one static device array
- * of LETKF_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until exit.
+ * It solves npts independent local analyses (Gram matrix, eigensolve, transform and update
+ * of each point's forecast block) given in a padded per-point layout, and allocates nothing:
+ * its only scratch (the k x k Gram matrices, the c vectors, the local counts and a status
+ * word) sits in one static device array of LETKF_NOALLOC_SCRATCH_BYTES that every GPU loading
+ * this library holds until exit.
  *   npts       number of grid points (local problems), >= 0
  *   k          ensemble size, 2..128
- *   lmaxv      padded local observed scalars per point (l_max V), >= 0
- *   dy_loc     device [npts][lmaxv][k] obs-space perturbations of the local observations
- *   d_loc      device [npts][lmaxv]    innovations yo - ybar
+ *   lmaxv      rows per point in the padded layout (the largest number of local observed
+ *              scalars over the points), >= 0
+ *   dy_loc     device [npts][lmaxv][k] obs-space perturbations of each point's local observed
+ *              scalars, one row per scalar, padded to lmaxv rows
+ *   d_loc      device [npts][lmaxv]    innovations yo - ybar of those scalars
  *   rinv_loc   device [npts][lmaxv]    localized inverse error variances G / sigma^2; 0 marks a
  *                                      padding row (its dy_loc/d_loc entries are ignored)
  *   infl       multiplicative inflation (1 = none): Q = (k-1)/infl I + dY^T R_loc^-1 dY
  *   x          device [npts][9][k] forecast blocks (grid-point-major, any fixed reference such
  *              as f or f - w), overwritten with the analysis blocks
  *   stream     cudaStream_t (NULL = legacy default stream)
- * Returns after the work has finished, with LETKF_OK, LETKF_ENOTCONV or LETKF_ENONFINITE from
- * the device status; LETKF_EINVAL when npts * (k*k + k + 1) + 64 floats exceed the scratch
- * (e.g. at most 15,858 points for k = 32, 4,033 for k = 64) or an argument is invalid.
+ * The call synchronizes its stream (it reads the status word back before returning), so it
+ * must not be called while that stream is being captured into a CUDA graph.  It returns after
+ * the work has finished, with LETKF_OK, LETKF_ENOTCONV or LETKF_ENONFINITE from the device
+ * status; LETKF_EINVAL, before any launch, when npts * (k*k + k + 1) + 64 floats exceed the
+ * scratch (at most 15,872 points for k = 32, 4,032 for k = 64) or an argument is invalid.
  * Every call shares the one scratch array: calls that overlap on the GPU (different streams
  * or threads) race; calls ordered on one stream do not.  Each call clears the status word and
- * overwrites the scratch of the points it processes.  The first call on a device looks up the
- * array's device address and prepares the kernels; make it before any stream capture. */
+ * overwrites the scratch of the points it processes.  The first call on a device also looks
+ * up the array's device address and prepares the kernels. */
 #define LETKF_NOALLOC_SCRATCH_BYTES (64u << 20)
 int letkf_local_analysis_noalloc(int32_t npts, int32_t k, int32_t lmaxv, const float *dy_loc,
                                  const float *d_loc, const float *rinv_loc, float infl, float *x,
@@ -311,8 +316,10 @@ int letkf_local_analysis_noalloc(int32_t npts, int32_t k, int32_t lmaxv, const f
  *           only
  *   stream  cudaStream_t (NULL = legacy default stream)
  * Allocates nothing.  Returns after the work has finished: LETKF_OK, LETKF_ENOTCONV (some QL
- * iteration cap was hit) or LETKF_ENONFINITE; LETKF_EINVAL for bad arguments.  The status
- * word shares the static scratch of letkf_local_analysis_noalloc: the same overlap rule holds. */
+ * iteration cap was hit) or LETKF_ENONFINITE; LETKF_EINVAL for bad arguments.  It
+ * synchronizes its stream, so it must not be called while that stream is being captured.  The
+ * status word shares the static scratch of letkf_local_analysis_noalloc: the same overlap rule
+ * holds. */
 int letkf_eigh_batch(int32_t npts, int32_t k, float *q, float *eigval, float *evec,
                      int32_t refine, void *stream);
 
@@ -325,11 +332,23 @@ int letkf_eigh_batch(int32_t npts, int32_t k, float *q, float *eigval, float *ev
  *   workspace        device buffer of at least letkf_eigh_workspace_bytes(npts, k) bytes,
  *                    256-byte aligned; its contents on entry do not matter and are overwritten
  *   workspace_bytes  its size
- * Returns LETKF_ENOMEM when the workspace is too small or misaligned.  Calls that share a
- * workspace race unless they are ordered on one stream. */
+ * Returns LETKF_ENOMEM when the workspace is too small or misaligned.  Like letkf_eigh_batch it
+ * synchronizes its stream (not callable during stream capture).  Calls that share a workspace
+ * race unless they are ordered on one stream. */
 size_t letkf_eigh_workspace_bytes(int32_t npts, int32_t k);
 int letkf_eigh_batch_ws(int32_t npts, int32_t k, float *q, float *eigval, float *evec,
                         int32_t refine, void *workspace, size_t workspace_bytes, void *stream);
+
+/* ---- diagnostics ------------------------------------------------------------
+ * FP32 FMA throughput microbenchmark: the measured peak that the ALU-bound kernels (the
+ * eigensolve, the plain FP32 Gram) are reported against.  Not part of the method.
+ * letkf_fp32_peak_grid: the launch's blocks (every SM filled with resident blocks) and threads.
+ * letkf_fp32_peak_run: one launch on stream in which every thread runs 16 independent chains
+ *   x <- fma(x, a, b) for iters x 8 rounds; out: device buffer of blocks * threads floats (the
+ *   chains' sums); *flops = 2 x the FMAs executed.  The caller times the launch (CUDA events on
+ *   the stream).  LETKF_EINVAL for iters < 1 or NULL pointers. */
+int letkf_fp32_peak_grid(int32_t *blocks, int32_t *threads);
+int letkf_fp32_peak_run(int32_t iters, float *out, int64_t *flops, void *stream);
 
 #ifdef __cplusplus
 }

@@ -14,8 +14,9 @@
 // streams, two threads) race; calls ordered on one stream do not.  Each call overwrites the
 // Gram matrices, c vectors and counts of the points it processes and clears the status word
 // before its kernels run.  The first call on a device looks up the array's device address
-// (cudaGetSymbolAddress) and prepares the kernels; make that first call before any stream
-// capture.  Larger problems than the scratch holds are rejected with LETKF_EINVAL.
+// (cudaGetSymbolAddress) and prepares the kernels.  Every call reads the status word back and
+// synchronizes its stream, so none may run while that stream is being captured.  Larger
+// problems than the scratch holds are rejected with LETKF_EINVAL before any launch.
 #include <mutex>
 
 #include "common.cuh"

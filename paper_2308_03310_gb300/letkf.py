@@ -49,6 +49,7 @@ EXPORTED = (
     "letkf_get_obs", "letkf_analyze", "letkf_analyze_probe", "letkf_cycle",
     "letkf_local_analysis_noalloc", "letkf_eigh_batch", "letkf_eigh_workspace_bytes",
     "letkf_eigh_batch_ws", "letkf_group_analyze", "letkf_group_cycle",
+    "letkf_fp32_peak_grid", "letkf_fp32_peak_run",
 )
 
 LETKF_NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -135,6 +136,8 @@ def load(path: str = LIB):
                                           C.c_size_t, P]),
         "letkf_group_analyze": (C.c_int, [P, P, C.c_int32, C.c_int32]),
         "letkf_group_cycle": (C.c_int, [P, C.c_int32, C.c_int32, P, C.c_int32]),
+        "letkf_fp32_peak_grid": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+        "letkf_fp32_peak_run": (C.c_int, [C.c_int32, P, C.POINTER(C.c_int64), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -264,6 +267,21 @@ def letkf_eigh_batch_ws(npts, k, q_ptr, eigval_ptr, evec_ptr, refine, ws_ptr, ws
                                       C.c_void_p(eigval_ptr), C.c_void_p(evec_ptr or None),
                                       int(refine), C.c_void_p(ws_ptr or None), int(ws_bytes),
                                       C.c_void_p(stream))
+
+
+def letkf_fp32_peak_grid():
+    """(blocks, threads) of the FP32 FMA microbenchmark launch on the current device."""
+    b, t = C.c_int32(0), C.c_int32(0)
+    _check(load().letkf_fp32_peak_grid(C.byref(b), C.byref(t)), "letkf_fp32_peak_grid")
+    return b.value, t.value
+
+
+def letkf_fp32_peak_run(iters, out_ptr, stream):
+    """Launch the FP32 FMA microbenchmark on stream; returns the flops it executes."""
+    n = C.c_int64(0)
+    _check(load().letkf_fp32_peak_run(int(iters), C.c_void_p(out_ptr), C.byref(n),
+                                      C.c_void_p(stream)), "letkf_fp32_peak_run")
+    return n.value
 
 
 def _group_arrays(exps, yos):

@@ -7,6 +7,9 @@ observation): local observation counts range from 0 to a few hundred scalars.  O
 analysis runs the eigensolve of the points of the ensembles on the fused schedule in one
 persistent launch per column class, and the split kernels of those on a split schedule.
 Checked:
+  * each ensemble's grouped result matches the FP64 oracle's local analyses at sampled points
+    (the densest, points without observations, random ones), FP32 and mixed, with every
+    ensemble in the persistent launch and with a mix of fused and split ensembles;
   * each ensemble's grouped result is bit for bit its own letkf_analyze on the same schedule
     (which the parity tests pin to the oracle), in FP32 and in the mixed form, with every
     ensemble fused, every one split, a mix, and AUTO (each picks at the first group analysis);
@@ -81,6 +84,61 @@ def test_group_analysis_equals_each_alone_analysis(precision, schedule):
         assert np.array_equal(got, ref)
         # points without local observations keep their forecast
         assert not np.array_equal(got, C.to_deviation32(f0))
+
+
+def _oracle_sample_points(net, n=32, seed=1600):
+    """Sampled grid points for the oracle check: the densest local networks, points without
+    local observations and seeded random ones."""
+    from oracle import letkf as oletkf
+    c2 = synth.loc_cutoff2(2.0)
+    counts = {(x, y): len(oletkf.local_obs(x, y, net, NX, NY, c2)[0])
+              for y in range(NY) for x in range(NX)}
+    order = sorted(counts, key=lambda p: (-counts[p], p))
+    pts = set(order[:8]) | set([p for p in order if counts[p] == 0][:6])
+    rng = synth.generator(seed)
+    while len(pts) < n:
+        pts.add((int(rng.integers(NX)), int(rng.integers(NY))))
+    return sorted(pts), counts
+
+
+@pytest.mark.parametrize("precision", [L.LETKF_FP32, L.LETKF_MIXED])
+@pytest.mark.parametrize("schedule", ["fused", "mix"])
+def test_group_analysis_matches_oracle_at_sampled_points(precision, schedule):
+    # The grouped analysis (the persistent launch over all fused-schedule ensembles, split
+    # kernels for the others) of the k = 16/32/64/128 ensembles on the clustered network,
+    # each checked against the FP64 oracle's local analyses (Algorithm 1 per point) at the
+    # densest points, at points without observations and at random points, to the parity
+    # tests' 1e-5 relative L2 on the mean, the mean increment and the perturbations.
+    from oracle import lbm, obs as oobs
+    scheds = {"fused": (L.LETKF_EIG_FUSED,) * 4, "mix": MIX}[schedule]
+    grouped, f0s, yos = _ensembles(precision, scheds)
+    L.letkf_group_analyze(grouped, yos)
+    net = _network()
+    var = np.full(len(net) * 2, 1e-4, dtype=np.float32)
+    pts, counts = _oracle_sample_points(net)
+    assert max(counts.values()) > 40 and min(counts[p] for p in pts) == 0
+    for g, f0, yo in zip(grouped, f0s, yos):
+        got = g.get_deviation()
+        assert g.sync() == 0
+        Yf = oobs.observe(f0.astype(np.float64), net, UV)
+        ref = C.oracle_points(f0, Yf, yo, net, var, 2.0, UV, pts)
+        bg, bo, bf, worst = [], [], [], [0.0, 0.0, 0.0]
+        for (x, y) in pts:
+            r = ref[(x, y)]
+            b_g = C.dev64(got[:, :, y, x])
+            b_o = r["Xa"].T - lbm.W[None, :]
+            b_f = f0[:, :, y, x].astype(np.float64) - lbm.W[None, :]
+            if r["nloc"] == 0:
+                assert np.array_equal(got[:, :, y, x],
+                                      C.to_deviation32(f0[:, :, y, x][:, :, None, None])[:, :, 0, 0])
+                continue
+            bg.append(b_g)
+            bo.append(b_o)
+            bf.append(b_f)
+            worst = [max(a, b) for a, b in zip(worst, C.point_parity(b_g, b_o, b_f))]
+        errs = C.point_parity(np.concatenate(bg, 1), np.concatenate(bo, 1), np.concatenate(bf, 1))
+        assert max(errs) < 1e-5, (g.k, errs)
+        assert max(worst) < 5e-5, (g.k, worst)
 
 
 def test_points_without_observations_are_untouched_in_the_group():
