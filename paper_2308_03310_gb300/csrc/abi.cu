@@ -383,6 +383,7 @@ lk::EigArgs eig_args(letkf_handle *h, int y0, int y1) {
     lk::EigArgs e;
     e.k = k;
     e.diag = (float)((double)(k - 1) / (double)h->cfg.infl);
+    e.sqrt_infl = (float)sqrt((double)h->cfg.infl);
     e.gram = h->gram;
     e.cvec = h->cvec;
     e.nloc = h->nloc;

@@ -822,6 +822,22 @@ __device__ __forceinline__ void store_vectors(const float *Z, int ld, float *out
         }
 }
 
+// A point without local observations: Q = (k-1)/rho I, so wbar = 0 and dW = sqrt(rho) I; the
+// members keep their mean and their perturbations are scaled by sqrt(rho).  With rho = 1 the
+// point is left exactly as it is.
+__device__ __forceinline__ void inflate_point(const EigArgs &a, long long lp, int lane) {
+    if (a.sqrt_infl == 1.0f || !a.x) return;
+    const int k = a.k;
+    float *X = a.x + (size_t)(a.pt0 + lp) * NV * k;
+    for (int q = 0; q < NV; ++q) {
+        float sum = 0.0f;
+        for (int t = lane; t < k; t += 32) sum += X[q * k + t];
+        const float xbar = warp_sum(sum) / (float)k;
+        for (int t = lane; t < k; t += 32) X[q * k + t] = fmaf(a.sqrt_infl, X[q * k + t] - xbar, xbar);
+    }
+    __syncwarp();
+}
+
 // ---- fused schedule -----------------------------------------------------------------------
 
 // The whole analysis of grid point lp of a (fused schedule) by one warp, in its slice W of
@@ -839,9 +855,10 @@ __device__ __forceinline__ void analyze_point(const EigArgs &a, int lp, float *W
     float2 *de = vw + k;                    // tridiagonal (d_t, e_t), e_t couples t and t+1
     float *taus = reinterpret_cast<float *>(de + k);  // reflector scalars
     float *vtmp = taus + k;                 // one reflector, back in shared memory
-    if (a.nloc && a.nloc[lp] == 0) {  // no local observation: Q = (k-1)/rho I, X^a = X^f
+    if (a.nloc && a.nloc[lp] == 0) {  // no local observation: Q = (k-1)/rho I
         if (a.eigval)
             for (int t = lane; t < k; t += 32) a.eigval[(size_t)lp * k + t] = a.diag;
+        inflate_point(a, lp, lane);
         return;
     }
     float *Ag = a.gram + (size_t)lp * k * k;
@@ -1419,8 +1436,11 @@ __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS, EigCfg<NC>::MINB_VEC)
     const int nw = gridDim.x * warps_per_block;
     for (int lp = blockIdx.x * warps_per_block + wib; lp < a.npts; lp += nw) {
         const int nrec = sp.nrot[lp];
-        // unchanged / recomputed by the fused kernel
-        if ((a.nloc && a.nloc[lp] == 0) || nrec < 0) continue;
+        if (a.nloc && a.nloc[lp] == 0) {  // no local observation: Q = (k-1)/rho I
+            if constexpr (kUpdate) inflate_point(a, lp, lane);
+            continue;
+        }
+        if (nrec < 0) continue;  // recomputed by the fused kernel
         float *Ag = a.gram + (size_t)lp * k * k;
         float xbar[NV];
         float *X = kUpdate ? load_forecast<NC>(a, lp, B, k, ld, lane, xbar) : nullptr;

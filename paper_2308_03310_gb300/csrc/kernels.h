@@ -93,6 +93,8 @@ int gram_max_cells();
 struct EigArgs {
     int k = 0;
     float diag = 0.0f;              // (k - 1) / rho_infl
+    float sqrt_infl = 1.0f;         // sqrt(rho_infl): a point without local observations keeps
+                                    // its mean and has its perturbations scaled by it
     float *gram = nullptr;          // [npts][k][k]; Q is read from the upper triangle and the
                                     // diagonal, the Householder vectors go to the lower one
     const float *cvec = nullptr;    // [npts][k]

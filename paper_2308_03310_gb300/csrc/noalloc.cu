@@ -188,6 +188,7 @@ extern "C" int letkf_local_analysis_noalloc(int32_t npts, int32_t k, int32_t lma
     lk::EigArgs a;
     a.k = k;
     a.diag = (float)((double)(k - 1) / (double)infl);
+    a.sqrt_infl = (float)sqrt((double)infl);
     a.gram = gram;
     a.cvec = cvec;
     a.nloc = nloc;

@@ -229,6 +229,24 @@ def test_analysis_edge_cases_match_oracle(k, nx, ny, stride, radius, obs_vars, i
     _full_parity(exp, f0, yo, net, var, radius=radius, obs_vars=obs_vars, infl=infl)
 
 
+@pytest.mark.parametrize("k", [8, 48])
+@pytest.mark.parametrize("schedule", [L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT])
+def test_inflation_at_points_without_local_observations_matches_oracle(k, schedule):
+    # with inflation rho a point without local observations keeps its mean and has its
+    # perturbations scaled by sqrt(rho); observed points follow the inflated Q
+    nx = ny = 32
+    infl = 1.3
+    net = np.array([[3, 3], [20, 5], [9, 27]], dtype=np.int32)
+    f0 = C.perturb_nonequilibrium(C.ensemble_state(k, nx, ny, seed=95), 1e-4, 96)
+    var = np.full(len(net) * 2, 1e-4, dtype=np.float32)
+    exp = L.Experiment(nx, ny, k, 0.6, net, var, loc_radius=2.0, infl=infl,
+                       eig_schedule=schedule)
+    exp.set_state(f0)
+    yo = C.observations(C.ensemble_state(1, nx, ny, seed=97), net, UV, 0.01, 98)[0]
+    assert exp.stats().n_zero_obs > 0.5 * nx * ny
+    _full_parity(exp, f0, yo, net, var, radius=2.0, infl=infl)
+
+
 def test_points_without_local_observations_are_unchanged():
     nx = ny = 32
     k = 8

@@ -199,6 +199,17 @@ def test_no_local_observation_is_identity():
     assert np.allclose(r["Xa"], Xb, atol=1e-15)
 
 
+@pytest.mark.parametrize("rho", [1.0, 1.3])
+def test_no_local_observation_with_inflation_scales_perturbations(rho):
+    # With no observation Q = (k-1)/rho I, so wbar = 0 and dW = sqrt(k-1) Q^-1/2 = sqrt(rho) I:
+    # the mean is kept and every perturbation is scaled by sqrt(rho) (Eqs. letkf_q ..
+    # letkf_xa with the inflated Q).
+    Xb, _, _, _ = _random_local_problem(12, 1, seed=33)
+    r = letkf.local_analysis(Xb, np.zeros((0, 12)), np.zeros(0), np.zeros(0), rho)
+    xbar = Xb.mean(axis=1, keepdims=True)
+    assert np.allclose(r["Xa"], xbar + math.sqrt(rho) * (Xb - xbar), atol=1e-15)
+
+
 def test_scalar_two_member_case_matches_hand_worked_kalman():
     g = json.load(open(os.path.join(GOLDEN, "scalar_kalman_k2.json")))
     x = np.array([g["members"]])

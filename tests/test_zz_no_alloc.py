@@ -120,7 +120,7 @@ def _block_parity(got, ref, xf):
 
 @pytest.mark.parametrize("k,infl", [(5, 1.0), (16, 1.0), (32, 1.1), (64, 1.0), (128, 1.1)])
 def test_noalloc_matches_handle_analysis_on_two_calls_in_a_row(k, infl):
-    nx = ny = 32
+    nx = ny = 32 if k <= 64 else 24           # 24^2 points at k = 128 fit the scratch
     radius = 3.0
     f0 = C.perturb_nonequilibrium(C.ensemble_state(k, nx, ny, seed=501), 1e-4, 502)
     net = synth.regular_obs_network(nx, ny, 4)
@@ -157,7 +157,9 @@ def test_noalloc_matches_oracle_local_analysis(k, infl, lmaxv):
         errs = _block_parity(got, ref, x)
         assert max(errs) < 1e-5, (call, errs)
         empty = counts == 0
-        assert empty.any() and np.array_equal(got[empty], x[empty])
+        assert empty.any()
+        if infl == 1.0:                      # without inflation such points stay as they are
+            assert np.array_equal(got[empty], x[empty])
 
 
 def test_noalloc_accepts_the_largest_problem_and_rejects_one_point_more():
