@@ -211,8 +211,8 @@ def measured_peaks():
             "source": "fallback"}
 
 
-EIG_SCHEDULES = {"auto": 0, "fused": 1, "split": 2}
-EIG_NAMES = {1: "fused", 2: "split", 3: "split_check"}
+EIG_SCHEDULES = {"auto": 0, "fused": 1, "split": 2, "rational": 4}
+EIG_NAMES = {1: "fused", 2: "split", 3: "split_check", 4: "rational"}
 PEAK_NAMES = {"hbm": "hbm_gbs", "alu": "FP32 FMA peak from the unit counts at max SM clock",
               "tensor": "bf16_tflops_sustained (FP16 operands, same nominal rate)"}
 

@@ -63,8 +63,9 @@ extern "C" {
                                   accumulation); for k <= 32 it stays on CUDA cores         */
 
 /* Eigensolve schedules (same results up to rounding; see letkf_config.eig_schedule). */
-#define LETKF_EIG_AUTO        0  /* the handle picks one: at its first analysis both schedules
-                                    are timed on that analysis' first chunk of Gram matrices
+#define LETKF_EIG_AUTO        0  /* the handle picks one: at its first analysis the schedules
+                                    (FUSED, SPLIT and, for k <= 64, RATIONAL) are timed on
+                                    that analysis' first chunk of Gram matrices
                                     (applied to a scratch copy of the forecast, so the analysis
                                     itself is unaffected; one host synchronisation), and the
                                     faster is kept.  The pick is cached per (device, k, chunk
@@ -77,6 +78,15 @@ extern "C" {
 #define LETKF_EIG_SPLIT_CHECK 3  /* SPLIT with a record of one sweep per point, so that nearly
                                     every point is handed back to the fused kernel: exercises
                                     the hand-off; for tests and diagnosis, not for speed      */
+#define LETKF_EIG_RATIONAL    4  /* EVD-free transform, k <= 64 (the paper's future work,
+                                    Sec. III): the same Householder tridiagonalization
+                                    Q = H T H^T, then Q^-1 c by one tridiagonal solve and
+                                    Q^-1/2 applied to the perturbations through Zolotarev's
+                                    best rational approximation of t^-1/2 (shifted L D L^T
+                                    solves of T, relative error ~1e-8); no eigenvalues or
+                                    eigenvectors are formed.  A point whose condition bound
+                                    exceeds 1e6 is solved by the fused schedule instead.  A
+                                    probe's eigenvalues come from an extra eigenvalue-only QL. */
 
 /* ---- problem statement --------------------------------------------------
  * Follows the paper's statement of the problem (Sec. II-B): the grid, the
@@ -349,6 +359,14 @@ int letkf_eigh_batch_ws(int32_t npts, int32_t k, float *q, float *eigval, float 
  *   the stream).  LETKF_EINVAL for iters < 1 or NULL pointers. */
 int letkf_fp32_peak_grid(int32_t *blocks, int32_t *threads);
 int letkf_fp32_peak_run(int32_t iters, float *out, int64_t *flops, void *stream);
+
+/* The coefficients of LETKF_EIG_RATIONAL (host computation, FP64): Zolotarev's best n-term
+ * rational approximation t^-1/2 ~ sum_l residues[l] / (t + poles[l]) on [1/kappa_max, 1]
+ * (poles and residues: caller arrays of n doubles, 1 <= n <= 16, 1 < kappa_max < 1e12).
+ * Returns the largest relative error found on a fine logarithmic grid of the interval, or -1
+ * for invalid arguments. */
+double letkf_rational_coefficients(double kappa_max, int32_t n, double *poles,
+                                   double *residues);
 
 #ifdef __cplusplus
 }

@@ -69,8 +69,9 @@ int validate(const letkf_config *c) {
         return LETKF_EINVAL;
     if (!(c->infl > 0.0f) || !isfinite(c->infl)) return LETKF_EINVAL;
     if (c->precision != LETKF_FP32 && c->precision != LETKF_MIXED) return LETKF_EINVAL;
-    if (c->eig_schedule < LETKF_EIG_AUTO || c->eig_schedule > LETKF_EIG_SPLIT_CHECK)
+    if (c->eig_schedule < LETKF_EIG_AUTO || c->eig_schedule > LETKF_EIG_RATIONAL)
         return LETKF_EINVAL;
+    if (c->eig_schedule == LETKF_EIG_RATIONAL && c->k > lk::kRationalMaxK) return LETKF_EINVAL;
     if (c->chunk_bytes < 0) return LETKF_EINVAL;
     const int V = popcount3(c->obs_vars);
     for (int l = 0; l < c->n_obs; ++l) {
@@ -171,12 +172,16 @@ int make_plan(const letkf_config *c, Plan *p) {
     // split eigensolve: the schedule, and a record of about twice the rotations that the
     // implicit QL needs on these matrices (~k^2 / 2; overflowing points go to the fused kernel)
     p->eig_schedule = c->eig_schedule;
+    // (d, e), reflector scalars and the hand-off list: every schedule but FUSED; the rotation
+    // record: the split schedules (and AUTO, which may pick one)
     const bool split = p->eig_schedule != LETKF_EIG_FUSED;
-    p->rcap = p->eig_schedule == LETKF_EIG_SPLIT_CHECK ? c->k : c->k * c->k + 4 * c->k;
+    const bool record = split && p->eig_schedule != LETKF_EIG_RATIONAL;
+    p->rcap = !record ? 0
+              : p->eig_schedule == LETKF_EIG_SPLIT_CHECK ? c->k : c->k * c->k + 4 * c->k;
     p->off_de = take(split ? p->chunk_pts * c->k * sizeof(float2) : 0);
     p->off_taus = take(split ? p->chunk_pts * c->k * sizeof(float) : 0);
-    p->off_rot = take(split ? p->chunk_pts * (size_t)p->rcap * sizeof(float2) : 0);
-    p->off_nrot = take(split ? p->chunk_pts * sizeof(int) : 0);
+    p->off_rot = take(record ? p->chunk_pts * (size_t)p->rcap * sizeof(float2) : 0);
+    p->off_nrot = take(record ? p->chunk_pts * sizeof(int) : 0);
     p->off_list = take(split ? (p->chunk_pts + 4) * sizeof(int) : 0);
     p->off_status = take(kAlign);
     p->total = align_up(off, kAlign);
@@ -209,7 +214,8 @@ struct letkf_handle {
     float yref[3] = {0, 0, 0};
     int eig_blocks = 0;
     lk::EigSplit eig_split;
-    int eig_schedule = LETKF_EIG_FUSED;  // resolved: FUSED, SPLIT or SPLIT_CHECK
+    int eig_schedule = LETKF_EIG_FUSED;  // resolved: FUSED, SPLIT, SPLIT_CHECK or RATIONAL
+    int rat_grid = 0;                    // resident grid of the EVD-free transform kernel
     int tc_ctas = 0;
     letkf_stats stats;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -398,6 +404,27 @@ lk::EigArgs eig_args(letkf_handle *h, int y0, int y1) {
     return e;
 }
 
+// The EVD-free schedule serves k <= kRationalMaxK; AUTO considers it there.
+bool rational_candidate(int schedule, int k) {
+    return (schedule == LETKF_EIG_RATIONAL || schedule == LETKF_EIG_AUTO) &&
+           k <= lk::kRationalMaxK;
+}
+
+// The chunk's eigensolve, transform and update on the handle's resolved schedule.
+cudaError_t launch_eig_schedule(letkf_handle *h, int schedule, lk::EigArgs e, cudaStream_t s,
+                                bool want_eigval) {
+    if (schedule == LETKF_EIG_FUSED) {
+        e.eigval = want_eigval ? h->eigval : nullptr;
+        return lk::launch_eigen_update(e, s);
+    }
+    if (schedule == LETKF_EIG_RATIONAL) {
+        e.eigval = want_eigval ? h->eigval : nullptr;
+        return lk::launch_eigen_rational(e, h->eig_split, h->rat_grid, s);
+    }
+    e.eigval = h->eigval;
+    return lk::launch_eigen_split(e, h->eig_split, s, h->stream2, h->split_fork, h->split_join);
+}
+
 // ---- AUTO eigensolve schedule ----------------------------------------------------------
 // Both schedules are timed on the handle's first analysis, on the Gram matrices of its first
 // chunk (at most 16384 points), just before that chunk's eigensolve: each runs the full
@@ -449,16 +476,15 @@ int tune_eig_schedule(letkf_handle *h, int y0, int y1) {
     CK(cudaStreamSynchronize(h->stream));
     CK(cudaMemcpy(&saved, h->status, sizeof(int), cudaMemcpyDeviceToHost));
     cudaEvent_t t0 = nullptr, t1 = nullptr;
-    float best[2] = {0.0f, 0.0f};
+    const int cand[3] = {LETKF_EIG_FUSED, LETKF_EIG_SPLIT, LETKF_EIG_RATIONAL};
+    const int ncand = rational_candidate(LETKF_EIG_AUTO, k) ? 3 : 2;
+    float best[3] = {0.0f, 0.0f, 0.0f};
     cudaError_t err = cudaEventCreate(&t0);
     if (err == cudaSuccess) err = cudaEventCreate(&t1);
-    for (int sch = 0; sch < 2 && err == cudaSuccess; ++sch) {
+    for (int sch = 0; sch < ncand && err == cudaSuccess; ++sch) {
         for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
             err = cudaEventRecord(t0, h->stream);
-            if (err == cudaSuccess)
-                err = sch == 0 ? lk::launch_eigen_update(e, h->stream)
-                               : lk::launch_eigen_split(e, h->eig_split, h->stream, h->stream2,
-                                                         h->split_fork, h->split_join);
+            if (err == cudaSuccess) err = launch_eig_schedule(h, cand[sch], e, h->stream, false);
             if (err == cudaSuccess) err = cudaEventRecord(t1, h->stream);
             if (err == cudaSuccess) err = cudaEventSynchronize(t1);
             float ms = 0.0f;
@@ -472,7 +498,10 @@ int tune_eig_schedule(letkf_handle *h, int y0, int y1) {
         err = cudaMemcpyAsync(h->status, &saved, sizeof(int), cudaMemcpyHostToDevice, h->stream);
     if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
     if (err != cudaSuccess) return cuda_fail(h, err);
-    const int pick = best[1] < best[0] ? LETKF_EIG_SPLIT : LETKF_EIG_FUSED;
+    int ib = 0;
+    for (int sch = 1; sch < ncand; ++sch)
+        if (best[sch] < best[ib]) ib = sch;
+    const int pick = cand[ib];
     {
         EigTuneCache &c = eig_tune_cache();
         std::lock_guard<std::mutex> lock(c.mu);
@@ -522,15 +551,8 @@ int enqueue_analysis(letkf_handle *h, letkf_probe *probe) {
             }
         }
         if (h->eig_schedule == LETKF_EIG_AUTO && (rc = tune_eig_schedule(h, y0, y1))) return rc;
-        lk::EigArgs e = eig_args(h, y0, y1);
-        if (h->eig_schedule == LETKF_EIG_FUSED) {
-            e.eigval = (probe && probe->eigval) ? h->eigval : nullptr;
-            CK(lk::launch_eigen_update(e, h->stream));
-        } else {
-            e.eigval = h->eigval;
-            CK(lk::launch_eigen_split(e, h->eig_split, h->stream, h->stream2, h->split_fork,
-                                      h->split_join));
-        }
+        CK(launch_eig_schedule(h, h->eig_schedule, eig_args(h, y0, y1), h->stream,
+                               probe && probe->eigval));
         if ((rc = mark(h, 6 + 2 * chunk))) return rc;
         ++chunk;
         if (probe && probe->eigval)
@@ -653,8 +675,7 @@ int enqueue_group(letkf_handle *const *hs, int n, int nsteps) {
                 segs[m++] = eig_args(g, y0, y1);
             } else {
                 const cudaError_t e =
-                    lk::launch_eigen_split(eig_args(g, y0, y1), g->eig_split, h->stream,
-                                           g->stream2, g->split_fork, g->split_join);
+                    launch_eig_schedule(g, g->eig_schedule, eig_args(g, y0, y1), h->stream, false);
                 if (e != cudaSuccess) return cuda_fail(g, e);
             }
         }
@@ -786,8 +807,8 @@ int letkf_init(const letkf_config *cfg, void *workspace, size_t workspace_bytes,
     if (plan.eig_schedule != LETKF_EIG_FUSED) {
         h->eig_split.de = (float2 *)(w + plan.off_de);
         h->eig_split.taus = (float *)(w + plan.off_taus);
-        h->eig_split.rot = (float2 *)(w + plan.off_rot);
-        h->eig_split.nrot = (int *)(w + plan.off_nrot);
+        h->eig_split.rot = plan.rcap > 0 ? (float2 *)(w + plan.off_rot) : nullptr;
+        h->eig_split.nrot = plan.rcap > 0 ? (int *)(w + plan.off_nrot) : nullptr;
         h->eig_split.list = (int *)(w + plan.off_list);
         h->eig_split.list_count = h->eig_split.list + plan.chunk_pts;
         h->eig_split.rcap = plan.rcap;
@@ -847,7 +868,9 @@ int letkf_init(const letkf_config *cfg, void *workspace, size_t workspace_bytes,
     if (lk::lbm_prepare() != cudaSuccess || lk::gram_prepare(plan.kp) != cudaSuccess ||
         lk::eigen_prepare(cfg->k, &h->eig_blocks) != cudaSuccess ||
         (plan.eig_schedule != LETKF_EIG_FUSED &&
-         lk::eigen_split_prepare(cfg->k, &h->eig_split) != cudaSuccess))
+         lk::eigen_split_prepare(cfg->k, &h->eig_split) != cudaSuccess) ||
+        (rational_candidate(plan.eig_schedule, cfg->k) &&
+         lk::eigen_rational_prepare(cfg->k, &h->rat_grid) != cudaSuccess))
         return fail(LETKF_ECUDA);
     if (plan.tensor_gram) {
         int sms = 0;

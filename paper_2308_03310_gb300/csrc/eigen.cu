@@ -1174,12 +1174,14 @@ __global__ void __launch_bounds__(kQlThreads) eig_ql_kernel(EigArgs a, EigSplit 
     if (lp >= a.npts) return;
     if (a.nloc && a.nloc[lp] == 0) {
         for (int t = 0; t < k; ++t) a.eigval[(size_t)lp * k + t] = a.diag;
-        sp.nrot[lp] = 0;
+        if (sp.nrot) sp.nrot[lp] = 0;
         return;
     }
     float2 *D = des + tid;  // D[i * kQlThreads] = (d_i, e_i)
     constexpr int L = kQlThreads;
-    float2 *rec = sp.rot + (size_t)lp * sp.rcap;
+    // without a record buffer the kernel computes eigenvalues only (no record, no hand-off)
+    const bool record = sp.rot != nullptr;
+    float2 *rec = record ? sp.rot + (size_t)lp * sp.rcap : nullptr;
     const float eps = FLT_EPSILON;
     float tn = 0.0f;  // deflation threshold eps ||T||, as in the fused schedule
     for (int t = 0; t < k; ++t)
@@ -1207,7 +1209,7 @@ __global__ void __launch_bounds__(kQlThreads) eig_ql_kernel(EigArgs a, EigSplit 
                 notconv = true;
                 break;
             }
-            if (pos + 1 + (m - l) > sp.rcap) {
+            if (record && pos + 1 + (m - l) > sp.rcap) {
                 overflow = true;
                 break;
             }
@@ -1245,12 +1247,13 @@ __global__ void __launch_bounds__(kQlThreads) eig_ql_kernel(EigArgs a, EigSplit 
                 D[(i + 1) * L] = make_float2(g + pacc, enew);
                 if (i + 1 < m && fabsf(enew) <= tol) sm = i + 1;
                 g = co * r - b;
-                rec[pos++] = make_float2(co, s);
+                if (record) rec[pos] = make_float2(co, s);
+                ++pos;
                 di1 = di;
                 ei = dnext.y;
                 di = dnext.x;
             }
-            rec[hdr] = make_float2(__int_as_float(m), __int_as_float(pos - hdr - 1));
+            if (record) rec[hdr] = make_float2(__int_as_float(m), __int_as_float(pos - hdr - 1));
             if (next >= 0) {
                 m = next;
             } else {
@@ -1271,7 +1274,7 @@ __global__ void __launch_bounds__(kQlThreads) eig_ql_kernel(EigArgs a, EigSplit 
         sp.list[atomicAdd(sp.list_count, 1)] = lp + sp.list_offset;
         return;
     }
-    sp.nrot[lp] = pos;
+    if (sp.nrot) sp.nrot[lp] = pos;
     for (int t = 0; t < k; ++t) a.eigval[(size_t)lp * k + t] = D[t * L].x;
 }
 
@@ -1756,6 +1759,37 @@ cudaError_t eigen_group_prepare(int *max_blocks) {
                          (size_t)smem_floats(128) * sizeof(float) * EigCfg<4>::WARPS,
                          &max_blocks[2]);
     return e;
+}
+
+template <int NC>
+cudaError_t launch_rational_nc(const EigArgs &a, const EigSplit &sp, int grid, cudaStream_t s) {
+    const int warps = EigCfg<NC>::WARPS;
+    cudaError_t e = cudaMemsetAsync(sp.list_count, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    launch_tri<NC>(a, sp, s);
+    if (a.eigval) {  // eigenvalues for a caller that asked for them: the QL without a record
+        EigSplit v = sp;
+        v.rot = nullptr;
+        v.nrot = nullptr;
+        launch_ql(a, v, s);
+    }
+    if ((e = launch_eigen_rational_transform(a, sp, grid, s)) != cudaSuccess) return e;
+    EigArgs f = a;  // points beyond the approximations' range: the fused kernel
+    f.list = sp.list;
+    f.list_count = sp.list_count;
+    eigen_update_kernel<NC><<<grid_for(a.max_blocks, a.npts, warps), 32 * warps,
+                              (size_t)smem_floats(a.k) * sizeof(float) * warps, s>>>(f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eigen_rational(const EigArgs &a, const EigSplit &sp, int grid,
+                                  cudaStream_t s) {
+    if (a.npts <= 0) return cudaSuccess;
+    if (!sp.de || !sp.taus || !sp.list || !sp.list_count || !a.x || !a.cvec)
+        return cudaErrorInvalidValue;
+    if (a.k <= 32) return launch_rational_nc<1>(a, sp, grid, s);
+    if (a.k <= kRationalMaxK) return launch_rational_nc<2>(a, sp, grid, s);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_eigen_split(const EigArgs &a, const EigSplit &sp, cudaStream_t s,

@@ -137,6 +137,30 @@ cudaError_t eigen_group_prepare(int *max_blocks);  // max_blocks[3], once per pr
 // segs: up to 3 kMaxGroupSeg chunks; counters: 3 device ints; max_blocks from the prepare
 cudaError_t launch_eigen_group(const EigArgs *segs, int n, int *counters, const int *max_blocks,
                                cudaStream_t s);
+// EVD-free transform (LETKF_EIG_RATIONAL, k <= kRationalMaxK): Zolotarev's rational
+// approximations of t^-1/2 on [1/kappa_max, 1], FP32 copies of the FP64 coefficients.
+constexpr int kZoloSets = 5;
+constexpr int kMaxZoloPoles = 16;
+constexpr int kRationalMaxK = 64;
+struct ZoloTable {
+    float kappa_max[kZoloSets];
+    int n[kZoloSets];
+    float pole[kZoloSets][kMaxZoloPoles];   // t^-1/2 ~ sum_l res_l / (t + pole_l)
+    float res[kZoloSets][kMaxZoloPoles];
+};
+const ZoloTable &zolo_table();              // computed once per process (zolotarev.cu)
+double zolotarev_rsqrt(double kappa, int n, double *poles, double *residues);
+cudaError_t eigen_rational_prepare(int k, int *grid);
+// the transform kernel alone (after the tridiagonalization); hands points beyond the largest
+// approximation's range to the fused kernel through sp.list
+cudaError_t launch_eigen_rational_transform(const EigArgs &a, const EigSplit &sp, int grid,
+                                            cudaStream_t s);
+// the whole schedule: tridiagonalization, eigenvalues if a.eigval (values-only QL), the
+// transform, then the fused kernel over the handed-off points; sp needs de, taus, list and
+// list_count (no rotation record)
+cudaError_t launch_eigen_rational(const EigArgs &a, const EigSplit &sp, int grid,
+                                  cudaStream_t s);
+
 cudaError_t eigen_prepare(int k, int *max_blocks);  // once per process and k
 cudaError_t eigen_split_prepare(int k, EigSplit *sp);
 cudaError_t launch_eigen_update(const EigArgs &a, cudaStream_t s);

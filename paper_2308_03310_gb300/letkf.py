@@ -40,6 +40,7 @@ LETKF_EIG_AUTO = 0
 LETKF_EIG_FUSED = 1
 LETKF_EIG_SPLIT = 2
 LETKF_EIG_SPLIT_CHECK = 3
+LETKF_EIG_RATIONAL = 4
 
 # Every symbol include/letkf.h declares, in declaration order.
 EXPORTED = (
@@ -49,7 +50,7 @@ EXPORTED = (
     "letkf_get_obs", "letkf_analyze", "letkf_analyze_probe", "letkf_cycle",
     "letkf_local_analysis_noalloc", "letkf_eigh_batch", "letkf_eigh_workspace_bytes",
     "letkf_eigh_batch_ws", "letkf_group_analyze", "letkf_group_cycle",
-    "letkf_fp32_peak_grid", "letkf_fp32_peak_run",
+    "letkf_fp32_peak_grid", "letkf_fp32_peak_run", "letkf_rational_coefficients",
 )
 
 LETKF_NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -138,6 +139,9 @@ def load(path: str = LIB):
         "letkf_group_cycle": (C.c_int, [P, C.c_int32, C.c_int32, P, C.c_int32]),
         "letkf_fp32_peak_grid": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
         "letkf_fp32_peak_run": (C.c_int, [C.c_int32, P, C.POINTER(C.c_int64), P]),
+        "letkf_rational_coefficients": (C.c_double, [C.c_double, C.c_int32,
+                                                     C.POINTER(C.c_double),
+                                                     C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -282,6 +286,17 @@ def letkf_fp32_peak_run(iters, out_ptr, stream):
     _check(load().letkf_fp32_peak_run(int(iters), C.c_void_p(out_ptr), C.byref(n),
                                       C.c_void_p(stream)), "letkf_fp32_peak_run")
     return n.value
+
+
+def letkf_rational_coefficients(kappa_max, n):
+    """(poles, residues, max relative error) of the library's n-term rational approximation
+    of t^-1/2 on [1/kappa_max, 1] (host computation, no GPU needed)."""
+    p = (C.c_double * int(n))()
+    r = (C.c_double * int(n))()
+    err = load().letkf_rational_coefficients(float(kappa_max), int(n), p, r)
+    if err < 0:
+        raise LetkfError(LETKF_EINVAL, "letkf_rational_coefficients")
+    return np.array(p[:]), np.array(r[:]), float(err)
 
 
 def _group_arrays(exps, yos):

@@ -143,3 +143,34 @@ def test_eigensolver_workspace_query_and_argument_checks(lib):
     assert L.letkf_eigh_batch_ws(4, 32, fake, fake, 0, 0, fake + 8, need, None) \
         == L.LETKF_ENOMEM
     assert L.letkf_eigh_batch_ws(4, 32, fake, fake, 0, 0, 0, need, None) == L.LETKF_ENOMEM
+
+
+@pytest.mark.parametrize("kappa,n,bound", [(1e2, 8, 5e-9), (1e3, 10, 1e-8), (1e4, 12, 2e-8),
+                                           (1e5, 14, 3e-8), (1e6, 16, 4e-8)])
+def test_rational_coefficients_are_zolotarevs(lib, kappa, n, bound):
+    # The EVD-free schedule's coefficients (host code in the library): poles and residues of
+    # the n-term approximation of t^-1/2 on [1/kappa, 1].  Checked against Zolotarev's
+    # construction evaluated with scipy's Jacobi elliptic functions (poles c_{2l-1} =
+    # delta^2 sn^2 / cn^2 at u = (2l-1) K'/(2n), parameter 1 - delta^2) and against the
+    # approximation error measured here on a finer grid.
+    scipy_special = pytest.importorskip("scipy.special")
+    poles, res, err = L.letkf_rational_coefficients(kappa, n)
+    d2 = 1.0 / kappa
+    m = 1.0 - d2
+    Kp = scipy_special.ellipk(m)
+    sn, cn, _, _ = scipy_special.ellipj(np.arange(1, 2 * n, 2) * Kp / (2 * n), m)
+    assert np.allclose(poles, d2 * sn ** 2 / cn ** 2, rtol=1e-10, atol=0)
+    assert (poles > 0).all() and (res > 0).all()
+    t = np.logspace(-np.log10(kappa), 0, 300001)
+    approx = (res[None, :] / (t[:, None] + poles[None, :])).sum(1)
+    measured = np.abs(np.sqrt(t) * approx - 1.0).max()
+    assert measured < bound and abs(measured - err) < 0.05 * measured + 1e-12
+    # equioscillation: the error reaches +-max at both ends of the interval
+    ends = np.sqrt(t[[0, -1]]) * approx[[0, -1]] - 1.0
+    assert np.allclose(np.abs(ends), measured, rtol=0.05)
+
+
+def test_rational_coefficients_reject_bad_arguments(lib):
+    for kappa, n in [(1.0, 8), (1e13, 8), (100.0, 0), (100.0, 17)]:
+        with pytest.raises(L.LetkfError):
+            L.letkf_rational_coefficients(kappa, n)

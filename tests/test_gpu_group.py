@@ -60,13 +60,15 @@ def _ensembles(precision, schedules=(L.LETKF_EIG_AUTO,) * 4, nx=NX, ny=NY):
 
 
 MIX = (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT, L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT)
+# the EVD-free schedule serves k <= 64
+RAT = (L.LETKF_EIG_RATIONAL, L.LETKF_EIG_RATIONAL, L.LETKF_EIG_RATIONAL, L.LETKF_EIG_FUSED)
 
 
 @pytest.mark.parametrize("precision", [L.LETKF_FP32, L.LETKF_MIXED])
-@pytest.mark.parametrize("schedule", ["fused", "split", "mix", "auto"])
+@pytest.mark.parametrize("schedule", ["fused", "split", "mix", "rational", "auto"])
 def test_group_analysis_equals_each_alone_analysis(precision, schedule):
     scheds = {"fused": (L.LETKF_EIG_FUSED,) * 4, "split": (L.LETKF_EIG_SPLIT,) * 4,
-              "mix": MIX, "auto": (L.LETKF_EIG_AUTO,) * 4}[schedule]
+              "mix": MIX, "rational": RAT, "auto": (L.LETKF_EIG_AUTO,) * 4}[schedule]
     grouped, f0s, yos = _ensembles(precision, scheds)
     st = grouped[0].stats()
     assert 0.15 < st.n_zero_obs / st.n_points < 0.5          # a share of points sees nothing
@@ -102,7 +104,7 @@ def _oracle_sample_points(net, n=32, seed=1600):
 
 
 @pytest.mark.parametrize("precision", [L.LETKF_FP32, L.LETKF_MIXED])
-@pytest.mark.parametrize("schedule", ["fused", "mix"])
+@pytest.mark.parametrize("schedule", ["fused", "mix", "rational"])
 def test_group_analysis_matches_oracle_at_sampled_points(precision, schedule):
     # The grouped analysis (the persistent launch over all fused-schedule ensembles, split
     # kernels for the others) of the k = 16/32/64/128 ensembles on the clustered network,
@@ -110,7 +112,7 @@ def test_group_analysis_matches_oracle_at_sampled_points(precision, schedule):
     # densest points, at points without observations and at random points, to the parity
     # tests' 1e-5 relative L2 on the mean, the mean increment and the perturbations.
     from oracle import lbm, obs as oobs
-    scheds = {"fused": (L.LETKF_EIG_FUSED,) * 4, "mix": MIX}[schedule]
+    scheds = {"fused": (L.LETKF_EIG_FUSED,) * 4, "mix": MIX, "rational": RAT}[schedule]
     grouped, f0s, yos = _ensembles(precision, scheds)
     L.letkf_group_analyze(grouped, yos)
     net = _network()
