@@ -156,7 +156,8 @@ typedef struct letkf_probe {
     int32_t n_points;          /* sampled points                                        */
     const int32_t *points;     /* [n_points] linear grid index y*nx + x                 */
     int32_t *nloc;             /* [n_points] local observation points                   */
-    float   *gram;             /* [n_points][k][k] dY^T R_loc^-1 dY (Eq. letkf_q)        */
+    float   *gram;             /* [n_points][k][k] dY^T R_loc^-1 dY (Eq. letkf_q); the
+                                  kernels form its upper triangle, the probe mirrors it  */
     float   *cvec;             /* [n_points][k]    dY^T R_loc^-1 (yo - ybar) (Eq. letkf_wa) */
     float   *eigval;           /* [n_points][k]    eigenvalues of Q, ascending          */
     float   *xf;               /* [n_points][9][k] forecast block, grid-point-major     */

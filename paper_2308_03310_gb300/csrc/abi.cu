@@ -1101,6 +1101,14 @@ int letkf_analyze_probe(letkf_handle *h, const float *yo, int32_t where, letkf_p
     if ((rc = copy_in(h, h->yo, yo, (size_t)h->plan.LV * sizeof(float), where))) return rc;
     if ((rc = enqueue_analysis(h, probe))) return rc;
     if (probe) CK(cudaStreamSynchronize(h->stream));
+    if (probe && probe->gram) {  // the Gram kernels form the upper triangle: mirror it
+        const int k = h->cfg.k;
+        for (int i = 0; i < probe->n_points; ++i) {
+            float *A = probe->gram + (size_t)i * k * k;
+            for (int r = 0; r < k; ++r)
+                for (int c = r + 1; c < k; ++c) A[c * k + r] = A[r * k + c];
+        }
+    }
     if (probe && probe->eigval)  // ascending order per point
         for (int i = 0; i < probe->n_points; ++i)
             std::sort(probe->eigval + (size_t)i * h->cfg.k, probe->eigval + (size_t)(i + 1) * h->cfg.k);

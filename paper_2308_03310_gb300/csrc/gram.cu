@@ -5,17 +5,19 @@
 //     c_p = sum_o G_po / sigma_o^2  dy_o (yo_o - ybar_o) (the vector of Eq. letkf_wa)
 // with G_po = exp(-d^2 / (2 r^2)) for integer periodic d^2 <= d2max, else 0.
 //
-// Design (GB300): a CTA owns a TW x TH tile of grid points and a team of
-// (KP/8)^2 threads per point, each thread accumulating one 8 x 8 block of A_p in
-// registers.  The CTA gathers the observation patch of its tile once -- the
-// observations of every bin (cs x cs cell) that the tile's cutoff disks touch --
-// and stages it through shared memory 32 observation points at a time: their
-// perturbation rows dy_o (k floats each, read from L2, where the whole dY lives),
-// innovations and inverse variances.  The weight of each (point, observation)
-// pair is computed once per chunk into shared memory; a team skips observations
-// outside its point's cutoff.  Nothing per-point is materialized in HBM except the
-// k x k result (the paper's padded Y_loc[M, N_x, l_max V] array is never formed).
-// Summation order is fixed by the bin order, so results are bitwise reproducible.
+// Design (GB300): a CTA owns a TW x TH tile of grid points and a team of KB (KB + 1) / 2
+// threads per point (KB = KP / 8), each thread accumulating one 8 x 8 block (ti, tj), ti <= tj,
+// of A_p in registers: A is symmetric and the eigensolve reads only its upper triangle and
+// diagonal, so only the upper blocks are formed (36 of 64 at KP = 64; the diagonal blocks'
+// threads also accumulate c).  The CTA gathers the observation patch of its tile once -- the
+// observations of every bin (cs x cs cell) that the tile's cutoff disks touch -- and stages it
+// through shared memory 32 observation points at a time: their perturbation rows dy_o (k
+// floats each, read from L2, where the whole dY lives), innovations and inverse variances.
+// The weight of each (point, observation) pair is computed once per chunk into shared memory;
+// a team skips observations outside its point's cutoff.  Nothing per-point is materialized in
+// HBM except the upper triangle of the k x k result (the paper's padded Y_loc[M, N_x, l_max V]
+// array is never formed).  Summation order is fixed by the bin order, so results are bitwise
+// reproducible.
 #include "common.cuh"
 #include "kernels.h"
 #include "patch.cuh"
@@ -23,26 +25,41 @@
 namespace lk {
 namespace {
 
-constexpr int kThreads = 256;
 constexpr int kChunk = 32;  // observation points per staged chunk
 
 template <int KP>
 struct GramShape {
     static constexpr int KB = KP / 8;
-    static constexpr int T = KB * KB;         // threads per grid point
-    static constexpr int P = kThreads / T;    // grid points per CTA
-    static constexpr int TW = P >= 256 ? 16 : P >= 64 ? 8 : P >= 16 ? 4 : P >= 4 ? 2 : 1;
+    static constexpr int T = KB * (KB + 1) / 2;   // threads per grid point (upper blocks)
+    // grid points per CTA: about 256-320 threads, a rectangle of points
+    static constexpr int P = KP == 8 ? 256 : KP == 16 ? 64 : KP == 32 ? 32 : KP == 64 ? 8 : 2;
+    static constexpr int TW = KP == 8 ? 16 : KP == 16 ? 8 : KP == 32 ? 8 : KP == 64 ? 4 : 2;
     static constexpr int TH = P / TW;
+    static constexpr int NT = (P * T + 31) / 32 * 32;   // threads per CTA, whole warps (two
+                                                        // CTAs resident per SM)
+    static_assert(TW * TH == P, "tile");
 };
 
+// (ti, tj) of upper block r, row-major over ti <= tj < KB
+template <int KB>
+__device__ __forceinline__ void upper_block(int r, int &ti, int &tj) {
+    int i = 0, rem = r;
+    while (rem >= KB - i) {
+        rem -= KB - i;
+        ++i;
+    }
+    ti = i;
+    tj = i + rem;
+}
+
 template <int KP>
-__global__ void __launch_bounds__(kThreads) gram_kernel(GramArgs a) {
+__global__ void __launch_bounds__(GramShape<KP>::NT, 2) gram_kernel(GramArgs a) {
     using S = GramShape<KP>;
-    constexpr int KB = S::KB, T = S::T, P = S::P, TW = S::TW, TH = S::TH;
+    constexpr int KB = S::KB, T = S::T, P = S::P, TW = S::TW, TH = S::TH, NT = S::NT;
 
     __shared__ int cell_base[kMaxPatchCells];
     __shared__ int cell_pre[kMaxPatchCells + 1];
-    __shared__ int warp_tot[kThreads / 32];
+    __shared__ int warp_tot[NT / 32];
     __shared__ int2 opos[kChunk];
     __shared__ int oidx[kChunk];
     __shared__ float dv[kChunk * 3];
@@ -58,14 +75,17 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(GramArgs a) {
     const int ty0 = a.y_begin + blockIdx.y * TH;
 
     // ---- the tile's observation patch: bins touched by any cutoff disk of the tile
-    const int nc = build_patch<kThreads>(net, a.nx, a.ny, tx0, ty0, TW, TH, cell_base, cell_pre,
-                                         warp_tot);
+    const int nc = build_patch<NT>(net, a.nx, a.ny, tx0, ty0, TW, TH, cell_base, cell_pre,
+                                   warp_tot);
     const int total = cell_pre[nc];
 
-    // ---- this thread's role: point p of the tile, 8 x 8 block (ti, tj) of A_p
-    const int p = tid / T, r = tid % T, ti = r / KB, tj = r % KB;
+    // ---- this thread's role: point p of the tile, upper 8 x 8 block (ti, tj) of A_p
+    const int p = tid / T, r = tid - (tid / T) * T;
+    int ti = 0, tj = 0;
+    upper_block<KB>(r, ti, tj);
     const int px = tx0 + p % TW, py = ty0 + p / TW;
     const bool valid = p < P && px < a.nx && py < a.y_end;
+    const bool diag_block = ti == tj;
 
     float acc[8][8];
     float cacc[8];
@@ -92,14 +112,14 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(GramArgs a) {
         __syncthreads();
         // perturbation rows of the chunk: nch * V rows of KP floats, 16-byte copies
         constexpr int Q4 = KP / 4;
-        for (int e = tid; e < nch * V * Q4; e += kThreads) {
+        for (int e = tid; e < nch * V * Q4; e += NT) {
             const int row = e / Q4, c4 = e % Q4;
             const int s = oidx[row / V] * V + row % V;
             reinterpret_cast<float4 *>(ys + row * KP)[c4] =
                 __ldg(reinterpret_cast<const float4 *>(a.yb + (size_t)s * KP) + c4);
         }
         // localization weights of every (point, observation) pair of the chunk
-        for (int e = tid; e < P * nch; e += kThreads) {
+        for (int e = tid; e < P * nch; e += NT) {
             const int pp = e / nch, t = e % nch;
             const int qx = tx0 + pp % TW, qy = ty0 + pp / TW;
             const float w = (qx < a.nx && qy < a.y_end) ? loc_weight(net, opos[t], qx, qy, a.nx, a.ny)
@@ -127,7 +147,7 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(GramArgs a) {
                         const float sa = sw * av[i];
 #pragma unroll
                         for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(sa, bv[j], acc[i][j]);
-                        if (tj == 0) cacc[i] = fmaf(sa, dvs, cacc[i]);
+                        if (diag_block) cacc[i] = fmaf(sa, dvs, cacc[i]);
                     }
                 }
             }
@@ -146,9 +166,9 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(GramArgs a) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int col = tj * 8 + j;
-            if (col < k) A[row * k + col] = acc[i][j];
+            if (col < k && col >= row) A[row * k + col] = acc[i][j];
         }
-        if (tj == 0) a.cvec[lp * k + row] = cacc[i];
+        if (diag_block) a.cvec[lp * k + row] = cacc[i];
     }
     if (r == 0) a.nloc[lp] = nl;
 }
@@ -170,7 +190,7 @@ cudaError_t launch_kp(const GramArgs &a, cudaStream_t s) {
     const size_t smem = gram_smem<KP>();
     const int rows = a.y_end - a.y_begin;
     dim3 grid((a.nx + S::TW - 1) / S::TW, (rows + S::TH - 1) / S::TH);
-    gram_kernel<KP><<<grid, kThreads, smem, s>>>(a);
+    gram_kernel<KP><<<grid, S::NT, smem, s>>>(a);
     return cudaGetLastError();
 }
 

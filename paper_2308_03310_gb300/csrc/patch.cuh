@@ -22,9 +22,11 @@ __device__ __forceinline__ int range_at(const BinRanges &r, int i) {
 }
 
 // Exclusive prefix sum in place over s[0..n], n <= kMaxPatchCells; s[n] receives the total.
+// NT (the block's threads) is a multiple of 32.
 template <int NT>
 __device__ void block_exclusive_scan(int *s, int n, int *warp_tot) {
-    constexpr int IT = kMaxPatchCells / NT;
+    static_assert(NT % 32 == 0 && NT <= 1024, "whole warps");
+    constexpr int IT = (kMaxPatchCells + NT - 1) / NT;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     int v[IT], local = 0;
 #pragma unroll

@@ -152,7 +152,7 @@ def test_auto_schedule_resolves_at_the_first_analysis_once_per_process():
     assert exp.stats().eig_schedule == L.LETKF_EIG_AUTO         # unresolved before analysing
     exp.analyze(yo)
     pick = exp.stats().eig_schedule
-    assert pick in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT)
+    assert pick in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT, L.LETKF_EIG_RATIONAL)
     got = exp.get_deviation()
     assert exp.sync() == 0
     # the timed runs worked on scratch: the analysis is the picked schedule's, bit for bit
@@ -171,7 +171,7 @@ def test_auto_schedule_first_cycle_runs_eagerly_then_captures():
     a.cycle(3, yo)
     assert a.stats().cycle_kernels == 0                        # eager: no graph yet
     pick = a.stats().eig_schedule
-    assert pick in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT)
+    assert pick in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT, L.LETKF_EIG_RATIONAL)
     b, _ = _auto_case(45, pick, 975)
     b.cycle(3, yo)
     for _ in range(2):
@@ -187,7 +187,9 @@ def test_auto_schedule_first_cycle_runs_eagerly_then_captures():
 def test_handles_of_different_k_coexist(k_big, k_small):
     # the kernels' shared-memory caps are process-wide: a later handle with a smaller k
     # must not lower them under an earlier handle with a larger k
-    for sch in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT):
+    for sch in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT, L.LETKF_EIG_RATIONAL):
+        if sch == L.LETKF_EIG_RATIONAL and k_big > 64:
+            continue
         first = _run(k_big, 10, 10, 2, 2.0, 980 + k_big, sch)          # builds handle 1
         nx = ny = 10
         net = synth.regular_obs_network(nx, ny, 2)

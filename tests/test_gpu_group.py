@@ -74,7 +74,8 @@ def test_group_analysis_equals_each_alone_analysis(precision, schedule):
     assert 0.15 < st.n_zero_obs / st.n_points < 0.5          # a share of points sees nothing
     L.letkf_group_analyze(grouped, yos)
     picked = tuple(e.stats().eig_schedule for e in grouped)
-    assert all(p in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT) for p in picked)
+    assert all(p in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT, L.LETKF_EIG_RATIONAL)
+               for p in picked)
     if schedule != "auto":
         assert picked == scheds
     alone, _, _ = _ensembles(precision, picked)
@@ -190,7 +191,8 @@ def test_group_cycle_with_auto_handles_picks_then_captures():
     L.letkf_group_cycle(a, 3, yos)
     assert a[0].stats().cycle_kernels == 0
     picked = tuple(e.stats().eig_schedule for e in a)
-    assert all(p in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT) for p in picked)
+    assert all(p in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT, L.LETKF_EIG_RATIONAL)
+               for p in picked)
     b, _, _ = _ensembles(L.LETKF_FP32, picked, nx=46, ny=46)
     L.letkf_group_cycle(b, 3, yos)
     for _ in range(2):

@@ -94,7 +94,8 @@ def test_points_beyond_the_approximations_go_to_the_fused_kernel(k):
         st = exp.stats()
         exp.close()
     assert st.n_zero_obs == 0
-    assert np.array_equal(out[L.LETKF_EIG_RATIONAL], out[L.LETKF_EIG_FUSED])
+    # Q is numerically singular here, so both may carry non-finite values: in the same places
+    assert np.array_equal(out[L.LETKF_EIG_RATIONAL], out[L.LETKF_EIG_FUSED], equal_nan=True)
 
 
 def test_rational_cycle_equals_forecast_then_analysis():
