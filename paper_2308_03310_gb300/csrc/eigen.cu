@@ -1155,6 +1155,187 @@ __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS) eig_tridiag_kernel(Eig
     }
 }
 
+// ---- tridiagonalization by a pair of warps, Q in registers (33 <= k <= 64) ----------------
+// The same reflectors, scalars and outputs as tridiagonalize(), with the matrix split over two
+// warps: lane l of warp h holds column t = 32 h + l, all 64 rows, in registers (64 floats per
+// lane instead of the 128 a single warp would need).  Per reflector the pair meets four times
+// at a named barrier: after the column's norm and alpha, after v, after the dot product v.p,
+// after w; (v, w) and the partial sums live in shared memory, double-buffered by reflector
+// parity so that the next reflector's writes never meet this one's reads.  The product Q'v and
+// the rank-2 update run as unrolled chains over 4-row groups entered at the group of row j + 1
+// (a jump table on j), with 16-byte broadcast loads of (v, w) pairs.
+constexpr int kPairWarps = 4;   // warps per block: two pairs, one matrix each
+
+__host__ __device__ inline int pair_smem_floats(int k) {
+    // load staging k x (k+1) | (v, w) [2][64] float2 | partial sums [2][8] | betas, taus [64]
+    return round4(k * (k + 1)) + 2 * 64 * 2 + 16 + 64 + 64;
+}
+
+__device__ __forceinline__ void pair_sync(int id) {
+    asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
+}
+
+template <int G>
+__device__ __forceinline__ void tp_mv4(const float (&q)[64], const float4 *vw4, float (&p)[4]) {
+    if constexpr (G < 16) {
+        const float4 a = vw4[2 * G], b = vw4[2 * G + 1];
+        p[0] = fmaf(q[4 * G], a.x, p[0]);
+        p[1] = fmaf(q[4 * G + 1], a.z, p[1]);
+        p[2] = fmaf(q[4 * G + 2], b.x, p[2]);
+        p[3] = fmaf(q[4 * G + 3], b.z, p[3]);
+    }
+}
+
+template <int G>
+__device__ __forceinline__ void tp_up4(float (&q)[64], const float4 *vw4, float vt, float wt) {
+    if constexpr (G < 16) {
+        const float4 a = vw4[2 * G], b = vw4[2 * G + 1];
+        q[4 * G] -= fmaf(a.x, wt, a.y * vt);
+        q[4 * G + 1] -= fmaf(a.z, wt, a.w * vt);
+        q[4 * G + 2] -= fmaf(b.x, wt, b.y * vt);
+        q[4 * G + 3] -= fmaf(b.z, wt, b.w * vt);
+    }
+}
+
+#define LKP_CASE8(M, b) M(b) M(b + 1) M(b + 2) M(b + 3) M(b + 4) M(b + 5) M(b + 6) M(b + 7)
+#define LKP_GROUPS16(M) LKP_CASE8(M, 0) LKP_CASE8(M, 8)
+#define LKP_CASES64(M)                                                                      \
+    LKP_CASE8(M, 0) LKP_CASE8(M, 8) LKP_CASE8(M, 16) LKP_CASE8(M, 24) LKP_CASE8(M, 32)      \
+    LKP_CASE8(M, 40) LKP_CASE8(M, 48) LKP_CASE8(M, 56)
+
+__global__ void __launch_bounds__(32 * kPairWarps, 4) eig_tridiag_pair_kernel(EigArgs a,
+                                                                              EigSplit sp) {
+    extern __shared__ float smem[];
+    const int k = a.k, ld = k + 1;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int pair = wib >> 1, h = wib & 1, t = 32 * h + lane;
+    float *S = smem + (size_t)pair * pair_smem_floats(k);
+    float2 *vw = reinterpret_cast<float2 *>(S + round4(k * ld));  // [2][64], 16-byte aligned
+    float *red = reinterpret_cast<float *>(vw + 128);             // [2][8]
+    float *betas = red + 16, *taus_s = betas + 64;
+    const int bar = 1 + pair;
+    const int npairs = gridDim.x * (kPairWarps / 2);
+    for (int lp = blockIdx.x * (kPairWarps / 2) + pair; lp < a.npts; lp += npairs) {
+        if (a.nloc && a.nloc[lp] == 0) continue;   // the same decision for both warps
+        float *Ag = a.gram + (size_t)lp * k * k;
+        // ---- Q = diag + A, symmetrised from the upper triangle: warp h stages the row blocks
+        // 8 (2 b + h) .. +7 (coalesced row loads), then every lane reads its column
+        for (int i0 = 8 * h; i0 < k; i0 += 16) {
+            float v[8][2];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int i = i0 + u, j = lane + 32 * c;
+                    v[u][c] = (i < k && j < k) ? __ldcg(Ag + i * k + j) : 0.0f;
+                }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int i = i0 + u, j = lane + 32 * c;
+                    if (i < k && j < k && j >= i) {
+                        S[i * ld + j] = v[u][c];
+                        S[j * ld + i] = v[u][c];
+                    }
+                }
+        }
+        vw[t] = make_float2(0.0f, 0.0f);
+        vw[64 + t] = make_float2(0.0f, 0.0f);
+        pair_sync(bar);
+        float q[64];
+#pragma unroll
+        for (int i = 0; i < 64; ++i)
+            q[i] = (i < k && t < k) ? S[i * ld + t] + (i == t ? a.diag : 0.0f) : 0.0f;
+        for (int j = 0; j < k - 2; ++j) {
+            float2 *vwb = vw + (j & 1) * 64;
+            float *rb = red + (j & 1) * 8;
+            // x_t = Q'[t][j] = Q'[j][t] for t > j: the lane's own entry of row j
+            float x = 0.0f;
+            switch (j) {
+#define LKP_PICK(i) \
+    case i: x = q[i]; break;
+                LKP_CASES64(LKP_PICK)
+#undef LKP_PICK
+                default: break;
+            }
+            if (t <= j || t >= k) x = 0.0f;
+            const float tl = warp_sum(t > j + 1 ? x * x : 0.0f);
+            if (lane == 0) rb[h] = tl;
+            if (t == j + 1) rb[4] = x;
+            pair_sync(bar);
+            const float tail = rb[0] + rb[1], alpha = rb[4];
+            // H x = beta e_0 with beta = -sign(alpha) ||x||, tau = 1 + |alpha| / ||x||,
+            // v = x / (alpha - beta), v_0 = 1 (one rsqrt, one reciprocal, no division)
+            float tau = 0.0f, beta = alpha, scale = 0.0f;
+            if (tail > 0.0f) {
+                const float n2 = fmaf(alpha, alpha, tail);
+                float rn = rsqrtf(n2);
+                rn = rn * fmaf(-0.5f * n2, rn * rn, 1.5f);
+                const float nrm = n2 * rn;
+                beta = -copysignf(nrm, alpha);
+                tau = fmaf(fabsf(alpha), rn, 1.0f);
+                scale = copysignf(__frcp_rn(fabsf(alpha) + nrm), alpha);
+            }
+            const float vt = t > j + 1 ? x * scale : (t == j + 1 ? 1.0f : 0.0f);
+            if (t > j && t < k) {
+                vwb[t].x = vt;
+                refl_row(Ag, k, j)[t - j - 1] = vt;  // lower triangle of the slot
+            }
+            const int g0 = (j + 1) >> 2;  // the group of row j + 1
+            if (t >= 4 * g0 && t <= j) vwb[t] = make_float2(0.0f, 0.0f);
+            if (t == 0) {
+                taus_s[j] = tau;
+                betas[j] = beta;
+            }
+            if (tau == 0.0f) continue;  // the same for both warps; x is already reduced
+            pair_sync(bar);
+            const float4 *vw4 = reinterpret_cast<const float4 *>(vwb);
+            float p4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            switch (g0) {
+#define LKP_MV4(G) \
+    case G: tp_mv4<G>(q, vw4, p4);
+                LKP_GROUPS16(LKP_MV4)
+#undef LKP_MV4
+                default: break;
+            }
+            const float p = ((p4[0] + p4[1]) + (p4[2] + p4[3])) * tau;
+            const float kk = warp_sum(p * vt);
+            if (lane == 0) rb[2 + h] = kk;
+            pair_sync(bar);
+            const float K = 0.5f * tau * (rb[2] + rb[3]);
+            const float wt = t > j && t < k ? p - K * vt : 0.0f;
+            if (t > j && t < k) vwb[t].y = wt;
+            pair_sync(bar);
+            switch (g0) {
+#define LKP_UP4(G) \
+    case G: tp_up4<G>(q, vw4, vt, wt);
+                LKP_GROUPS16(LKP_UP4)
+#undef LKP_UP4
+                default: break;
+            }
+        }
+        // ---- (d, e): d_t = Q'[t][t] (the lane's own diagonal), e_j = beta_j, e_{k-2} =
+        // Q'[k-2][k-1]; the reflector scalars
+        float dg = 0.0f, el = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 64; ++i) {
+            if (i == t) dg = q[i];
+            if (i == k - 2) el = q[i];
+        }
+        if (t == k - 1) betas[k - 2] = el;   // column k-1 holds Q'[k-2][k-1]
+        pair_sync(bar);   // every beta and tau is written
+        if (t < k) {
+            sp.de[(size_t)lp * k + t] = make_float2(dg, t < k - 1 ? betas[t] : 0.0f);
+            sp.taus[(size_t)lp * k + t] = t < k - 2 ? taus_s[t] : 0.0f;
+        }
+        pair_sync(bar);   // the next matrix's staging may overwrite S, betas and taus
+    }
+}
+#undef LKP_CASES64
+#undef LKP_GROUPS16
+#undef LKP_CASE8
+
 // (2) implicit-shift QL, thread per matrix: the recurrence of the fused schedule on (d, e)
 // kept in shared memory as [index][thread] (the threads of a warp touch consecutive words),
 // every rotation recorded.  Record of a point: per sweep a header (m, count) -- bit patterns
@@ -1554,10 +1735,17 @@ cudaError_t prepare_nc(int k, int *max_blocks) {
 template <int NC>
 cudaError_t prepare_split_nc(int k, EigSplit *sp) {
     const int warps = EigCfg<NC>::WARPS;
-    cudaError_t e = occupancy<NC>((const void *)eig_tridiag_kernel<NC>, warps,
-                                  (size_t)tri_smem_floats(k) * sizeof(float) * warps,
-                                  (size_t)tri_smem_floats(kmax_of(NC)) * sizeof(float) * warps,
-                                  &sp->grid_tri);
+    cudaError_t e;
+    if constexpr (NC == 2)  // the pair kernel (two matrices per block)
+        e = occupancy<NC>((const void *)eig_tridiag_pair_kernel, kPairWarps,
+                          (size_t)pair_smem_floats(k) * sizeof(float) * (kPairWarps / 2),
+                          (size_t)pair_smem_floats(64) * sizeof(float) * (kPairWarps / 2),
+                          &sp->grid_tri);
+    else
+        e = occupancy<NC>((const void *)eig_tridiag_kernel<NC>, warps,
+                          (size_t)tri_smem_floats(k) * sizeof(float) * warps,
+                          (size_t)tri_smem_floats(kmax_of(NC)) * sizeof(float) * warps,
+                          &sp->grid_tri);
     if (e != cudaSuccess) return e;
     e = occupancy<NC>((const void *)eig_vec_kernel<NC, true>, warps,
                       (size_t)vec_smem_floats(k) * sizeof(float) * warps,
@@ -1608,6 +1796,13 @@ void split_part(const EigArgs &a, const EigSplit &sp, int p0, int n, EigArgs *b,
 
 template <int NC>
 void launch_tri(const EigArgs &a, const EigSplit &sp, cudaStream_t s) {
+    if constexpr (NC == 2) {  // 33 <= k <= 64: a pair of warps per matrix, Q in registers
+        constexpr int pairs = kPairWarps / 2;
+        eig_tridiag_pair_kernel<<<grid_for(sp.grid_tri, a.npts, pairs), 32 * kPairWarps,
+                                  (size_t)pair_smem_floats(a.k) * sizeof(float) * pairs, s>>>(a,
+                                                                                          sp);
+        return;
+    }
     const int warps = EigCfg<NC>::WARPS;
     eig_tridiag_kernel<NC><<<grid_for(sp.grid_tri, a.npts, warps), 32 * warps,
                              (size_t)tri_smem_floats(a.k) * sizeof(float) * warps, s>>>(a, sp);
