@@ -1224,7 +1224,7 @@ def measure(w, members, setup, yos, device, precision, steps, warm, world, eig_s
     sm_mhz = peaks["sm_max_mhz"] or 2070.0
     work = kernel_work(w, w.k, w.n_points, st.mean_local_obs, exp.V, exp.L, st.n_chunks,
                        w.steps_per_cycle)
-    tensor_gram = precision == L.LETKF_MIXED and 33 <= w.k <= 128
+    tensor_gram = precision == L.LETKF_MIXED and 17 <= w.k <= 128
     table = roofline_table(work, ms, peaks, sm_mhz, tensor_gram)
     top = max(table, key=lambda n: table[n]["ms_per_cycle"])
     t = table[top]

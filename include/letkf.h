@@ -58,9 +58,10 @@ extern "C" {
                                   capped at 2c, so every local observation has G > 0   */
 
 #define LETKF_FP32  0          /* plain FP32 CUDA-core analysis                                */
-#define LETKF_MIXED 1          /* split-precision: for 33 <= k <= 128 the localized Gram runs on
+#define LETKF_MIXED 1          /* split-precision: for 17 <= k <= 128 the localized Gram runs on
                                   the tensor cores (tcgen05, FP16 hi+lo operands, FP32
-                                  accumulation); for k <= 32 it stays on CUDA cores         */
+                                  accumulation; for k <= 32 two grid points share one
+                                  operand tile); for k <= 16 it stays on CUDA cores        */
 
 /* Eigensolve schedules (same results up to rounding; see letkf_config.eig_schedule). */
 #define LETKF_EIG_AUTO        0  /* the handle picks one: at its first analysis the schedules

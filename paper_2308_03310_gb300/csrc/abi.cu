@@ -40,7 +40,7 @@ struct Plan {
     size_t npts = 0;
     int nmem = 0, V = 0, LV = 0, kp = 0;
     int tile_w = 1, tile_h = 1;
-    bool tensor_gram = false;  // mixed precision with k in 33..128: tcgen05 split-FP16 Gram
+    bool tensor_gram = false;  // mixed precision with k in 17..128: tcgen05 split-FP16 Gram
     int eig_schedule = LETKF_EIG_FUSED;  // as configured; AUTO keeps both schedules' scratch
     int rcap = 0;              // split schedule: rotation record entries per point
     int chunk_rows = 0;
@@ -97,7 +97,7 @@ int make_plan(const letkf_config *c, Plan *p) {
     p->tile_h = lk::gram_tile_height(p->kp);
     // (the tensor-core kernel's records pack a point as x | y << 16 and a scalar's row with
     // its variable in bits 28..29)
-    p->tensor_gram = c->precision == LETKF_MIXED && p->kp >= 64 && c->nx < 65536 &&
+    p->tensor_gram = c->precision == LETKF_MIXED && p->kp >= 32 && c->nx < 65536 &&
                      c->ny < 65536 && p->LV < (1 << 28);
     if (p->tensor_gram) {  // the bins must fit either kernel's tile patch
         p->tile_w = std::max(p->tile_w, lk::gram_tc_tile_width(p->kp));

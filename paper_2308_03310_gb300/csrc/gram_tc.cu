@@ -9,7 +9,11 @@
 // and A_p = Xh Xh^T + Xl Xh^T + (Xl Xh^T)^T; the Xl Xl^T term (relative size 2^-22) is dropped.
 // The tile [Xl; Xh] (2 kp rows, K-major) gives with one M = 128 MMA per K-step
 //     kp = 64:  D = [Xl; Xh] Xh^T  (128 x 64): rows 0..63 Xl Xh^T, rows 64..127 Xh Xh^T;
-//     kp = 128: two MMAs, D_lh = Xl Xh^T and D_hh = Xh Xh^T (128 x 128 each).
+//     kp = 128: two MMAs, D_lh = Xl Xh^T and D_hh = Xh Xh^T (128 x 128 each);
+//     kp = 32:  two grid points side by side form one 64-member operand X = [X_a | X_b] and
+//               the kp = 64 MMA: the diagonal 32 x 32 blocks of X^T X are A_a and A_b (the
+//               off-diagonal products X_a^T X_b are formed and discarded: the tensor pipe
+//               is far from the kernel's bound).
 // The epilogue forms A = D_hh + (D_lh + D_lh^T) through a shared-memory transpose.
 // c_p = sum_o x_po (sqrt(G_po) (yo_o - ybar_o) / sigma_o) is accumulated in FP32 on the CUDA
 // cores by the threads that build the operands.
@@ -46,30 +50,33 @@ constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 
 template <int KP>
 struct TcShape {
-    static constexpr int P = KP == 64 ? 4 : 1;              // points per tile
-    static constexpr int TW = KP == 64 ? 2 : 1, TH = KP == 64 ? 2 : 1;
+    static constexpr bool PAIR = KP == 32;                  // two points per operand tile
+    static constexpr int KW = PAIR ? 64 : KP;               // members of one operand tile
+    static constexpr int P = KP == 64 ? 4 : KP == 32 ? 8 : 1;   // grid points per tile
+    static constexpr int PV = PAIR ? P / 2 : P;             // operand tiles per tile
+    static constexpr int TW = KP == 128 ? 1 : (PAIR ? 4 : 2), TH = KP == 128 ? 1 : 2;
     static constexpr int KC = 32;                           // slots per chunk (MMA K)
-    static constexpr int NOP = KP == 64 ? 2 : 4;            // operand stages
-    static constexpr int NY = KP == 64 ? 8 : 4;             // dy staging stages
-    static constexpr int SEG = KP == 64 ? 256 : 512;        // slots per candidate segment
+    static constexpr int NOP = KP == 128 ? 4 : 2;           // operand stages
+    static constexpr int NY = KP == 128 ? 4 : 8;            // dy staging stages
+    static constexpr int SEG = KP == 128 ? 512 : 256;       // slots per candidate segment
     static constexpr int SBO = (KC / 8) * 128;              // bytes between 8-row core blocks
-    static constexpr int OPB = 2 * KP * KC * 2;             // operand bytes per point and stage
-    static constexpr int STAGE = P * OPB;
+    static constexpr int OPB = 2 * KW * KC * 2;             // operand bytes per tile and stage
+    static constexpr int STAGE = PV * OPB;
     static constexpr int YROW = KP * 4;                     // bytes of one staged dy row
     static constexpr int YSTAGE = KC * YROW;
-    static constexpr int MQ = KP / 32;                      // member quarters of the producers
+    static constexpr int MQ = KW / 32;                      // member quarters of the producers
     static constexpr int KQ = kProdWarps / MQ;              // producer warps per member quarter
     static constexpr int NG = KC / 8, GPW = NG / KQ;        // 8-slot groups: per chunk, per warp
-    static constexpr int ELD = KP + 1;                      // padded row of the transpose buffer
+    static constexpr int ELD = KW + 1;                      // padded row of the transpose buffer
     static constexpr int OFF_OP = 0;
     static constexpr int OFF_Y = OFF_OP + NOP * STAGE;
     static constexpr int NMB = 2 * kMetaWarps;              // candidate buffers: 2 per ring
     static constexpr int OFF_GIDX = OFF_Y + NY * YSTAGE;    // int   [NMB][SEG]
     static constexpr int OFF_SW = OFF_GIDX + NMB * SEG * 4; // float [NMB][P][SEG]
     static constexpr int OFF_SU = OFF_SW + NMB * P * SEG * 4;  // float [NMB][P][SEG]
-    static constexpr int OFF_E = OFF_SU + NMB * P * SEG * 4;   // float [KP][ELD]
-    static constexpr int OFF_CRED = OFF_E + KP * ELD * 4;   // float [2][KQ][P][KP]
-    static constexpr int SMEM = OFF_CRED + 2 * KQ * P * KP * 4;
+    static constexpr int OFF_E = OFF_SU + NMB * P * SEG * 4;   // float [KW][ELD]
+    static constexpr int OFF_CRED = OFF_E + KW * ELD * 4;   // float [2][KQ][PV][KW]
+    static constexpr int SMEM = OFF_CRED + 2 * KQ * PV * KW * 4;
     static_assert(SEG % KC == 0 && NG % KQ == 0, "chunking");
     static_assert(SMEM <= 227 * 1024 - 1024, "shared memory");
 };
@@ -485,11 +492,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int 
                         for (int ks = 0; ks < KC / 16; ++ks) {
                             const uint32_t acc = (firstc && ks == 0) ? 0u : 1u;
 #pragma unroll
-                            for (int p = 0; p < P; ++p) {
+                            for (int p = 0; p < S::PV; ++p) {
                                 const uint32_t tp = st + p * S::OPB + ks * 256;
                                 const uint64_t dl = sdesc(tp, S::SBO);
-                                const uint64_t dh = sdesc(tp + (KP / 8) * S::SBO, S::SBO);
-                                if (KP == 64) {
+                                const uint64_t dh = sdesc(tp + (S::KW / 8) * S::SBO, S::SBO);
+                                if (S::KW == 64) {
                                     mma_f16(tmem + tb * 256 + p * 64, dl, dh, idesc_f16(128, 64),
                                             acc);
                                 } else {
@@ -539,12 +546,41 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int 
             asm volatile("tcgen05.fence::after_thread_sync;");
             int tx0, ty0;
             tile_origin(tile, tx0, ty0);
-            for (int p = 0; p < P && ok; ++p) {
+            for (int p = 0; p < S::PV && ok; ++p) {
                 const int qx = tx0 + p % TW, qy = ty0 + p / TW;
                 const bool valid = qx < a.nx && qy < a.y_end;
                 const size_t lp = valid ? (size_t)(qy - a.y_begin) * a.nx + qx : 0;
                 float v[32];
-                if (KP == 64) {
+                if (S::PAIR) {
+                    // operand tile p holds points 2p (members 0..31) and 2p + 1 (32..63):
+                    // row m of the 64 x 64 product belongs to point 2p + m / 32, and only its
+                    // diagonal 32 x 32 block is kept
+                    const uint32_t col = tb * 256 + p * 64;
+                    if (eq < 2) {  // rows of Xl Xh^T
+#pragma unroll
+                        for (int c0 = 0; c0 < 64; c0 += 32) {
+                            tmem_ld32(lane_base + col + c0, v);
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) E[r * S::ELD + c0 + i] = v[i];
+                        }
+                    }
+                    epi_barrier();
+                    if (!ok) break;
+                    if (eq >= 2) {  // rows of Xh Xh^T
+                        const int m = r - 64, half = m >> 5, mm = m & 31, c0 = 32 * half;
+                        const int pr = 2 * p + half;
+                        const int rx = tx0 + pr % TW, ry = ty0 + pr / TW;
+                        const bool rvalid = rx < a.nx && ry < a.y_end;
+                        const size_t rlp = rvalid ? (size_t)(ry - a.y_begin) * a.nx + rx : 0;
+                        tmem_ld32(lane_base + col + c0, v);
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            v[i] += E[m * S::ELD + c0 + i] + E[(c0 + i) * S::ELD + m];
+                        if (rvalid && mm < a.k)
+                            store_row32(a.gram + rlp * a.k * a.k + (size_t)mm * a.k, v, 0, a.k);
+                    }
+                    epi_barrier();
+                } else if (KP == 64) {
                     const uint32_t col = tb * 256 + p * 64;
                     if (eq < 2) {  // rows of Xl Xh^T
 #pragma unroll
@@ -599,13 +635,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int 
         // ===================== operands and c_p =====================
         const int pw = warp - kWarpProd;
         const int mq = pw % S::MQ, kq = pw / S::MQ;
-        const int m = 32 * mq + lane;
+        const int m = 32 * mq + lane;               // member of the operand tile
+        const int mr = S::PAIR ? lane : m;          // member of its grid point
         unsigned char *op = dyn + S::OFF_OP;
         int segc[2] = {0, 0}, par = 0, tcount = 0;
         uint32_t g = 0, psync = 0;
-        float cacc[P];
+        float cacc[S::PV];
 #pragma unroll
-        for (int p = 0; p < P; ++p) cacc[p] = 0.0f;
+        for (int p = 0; p < S::PV; ++p) cacc[p] = 0.0f;
         for (int tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x, ++tcount) {
             const int ring = tcount & 1;
             bool last = false, ok = true;
@@ -616,7 +653,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int 
                 last = (d.z & 2) != 0;
                 if (d.z & 1) {
 #pragma unroll
-                    for (int p = 0; p < P; ++p) cacc[p] = 0.0f;
+                    for (int p = 0; p < S::PV; ++p) cacc[p] = 0.0f;
                 }
                 const int nch = max(1, (d.y + KC - 1) / KC);
                 for (int ch = 0; ch < nch; ++ch, ++g) {
@@ -632,11 +669,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int 
                         float yv[8];
 #pragma unroll
                         for (int i = 0; i < 8; ++i)
-                            yv[i] = k8 + i < cnt ? ys[(k8 + i) * KP + m] : 0.0f;
+                            yv[i] = k8 + i < cnt ? ys[(k8 + i) * KP + mr] : 0.0f;
 #pragma unroll
-                        for (int p = 0; p < P; ++p) {
-                            const float *wp = sw_s + (mb * P + p) * SEG + first + k8;
-                            const float *up = su_s + (mb * P + p) * SEG + first + k8;
+                        for (int p = 0; p < S::PV; ++p) {
+                            const int pp = S::PAIR ? 2 * p + mq : p;   // the grid point
+                            const float *wp = sw_s + (mb * P + pp) * SEG + first + k8;
+                            const float *up = su_s + (mb * P + pp) * SEG + first + k8;
                             const float4 w0 = *reinterpret_cast<const float4 *>(wp);
                             const float4 w1 = *reinterpret_cast<const float4 *>(wp + 4);
                             const float4 u0 = *reinterpret_cast<const float4 *>(up);
@@ -657,7 +695,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int 
                                 cacc[p] = fmaf(x1, u[2 * i + 1], cacc[p]);
                             }
                             unsigned char *tp = st + p * S::OPB;
-                            *reinterpret_cast<uint4 *>(tp + core_off_b<KC>(KP + m, k8)) =
+                            *reinterpret_cast<uint4 *>(tp + core_off_b<KC>(S::KW + m, k8)) =
                                 make_uint4(hw[0], hw[1], hw[2], hw[3]);
                             *reinterpret_cast<uint4 *>(tp + core_off_b<KC>(m, k8)) =
                                 make_uint4(lw[0], lw[1], lw[2], lw[3]);
@@ -677,7 +715,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int 
             }
             // ---- c_p: partial sums of the KQ warps sharing a member quarter
 #pragma unroll
-            for (int p = 0; p < P; ++p) cred[((par * S::KQ + kq) * P + p) * KP + m] = cacc[p];
+            for (int p = 0; p < S::PV; ++p)
+                cred[((par * S::KQ + kq) * S::PV + p) * S::KW + m] = cacc[p];
             bar_arrive(&prod_sync);
             if (!wait_bar(&prod_sync, psync & 1, &abort_flag)) {
                 fail();
@@ -688,14 +727,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int 
                 int tx0, ty0;
                 tile_origin(tile, tx0, ty0);
 #pragma unroll
-                for (int p = 0; p < P; ++p) {
+                for (int p = 0; p < S::PV; ++p) {
                     float c = 0.0f;
 #pragma unroll
                     for (int q = 0; q < S::KQ; ++q)
-                        c += cred[((par * S::KQ + q) * P + p) * KP + m];
-                    const int qx = tx0 + p % TW, qy = ty0 + p / TW;
-                    if (m < a.k && qx < a.nx && qy < a.y_end)
-                        a.cvec[((size_t)(qy - a.y_begin) * a.nx + qx) * a.k + m] = c;
+                        c += cred[((par * S::KQ + q) * S::PV + p) * S::KW + m];
+                    const int pp = S::PAIR ? 2 * p + mq : p;
+                    const int qx = tx0 + pp % TW, qy = ty0 + pp / TW;
+                    if (mr < a.k && qx < a.nx && qy < a.y_end)
+                        a.cvec[((size_t)(qy - a.y_begin) * a.nx + qx) * a.k + mr] = c;
                 }
             }
             par ^= 1;
@@ -728,10 +768,17 @@ __global__ void obs_records_kernel(ObsNet net, const float *rinv, const float *y
 
 }  // namespace
 
-int gram_tc_tile_width(int kp) { return kp == 64 ? TcShape<64>::TW : TcShape<128>::TW; }
-int gram_tc_tile_height(int kp) { return kp == 64 ? TcShape<64>::TH : TcShape<128>::TH; }
+int gram_tc_tile_width(int kp) {
+    return kp == 32 ? TcShape<32>::TW : kp == 64 ? TcShape<64>::TW : TcShape<128>::TW;
+}
+int gram_tc_tile_height(int kp) {
+    return kp == 32 ? TcShape<32>::TH : kp == 64 ? TcShape<64>::TH : TcShape<128>::TH;
+}
 
 cudaError_t gram_tc_prepare(int kp) {
+    if (kp == 32)
+        return cudaFuncSetAttribute(gram_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    TcShape<32>::SMEM);
     if (kp == 64)
         return cudaFuncSetAttribute(gram_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     TcShape<64>::SMEM);
@@ -752,7 +799,7 @@ cudaError_t launch_obs_records(const GramArgs &a, float4 *rec, cudaStream_t s) {
 
 cudaError_t launch_gram_tc(const GramArgs &a, int *status, int max_ctas, cudaStream_t s) {
     if (a.y_end <= a.y_begin) return cudaSuccess;
-    if (a.kp != 64 && a.kp != 128) return cudaErrorInvalidValue;
+    if (a.kp != 32 && a.kp != 64 && a.kp != 128) return cudaErrorInvalidValue;
     if (a.orec == nullptr) return cudaErrorInvalidValue;
     const int TW = gram_tc_tile_width(a.kp), TH = gram_tc_tile_height(a.kp);
     const long long tiles =
@@ -774,6 +821,10 @@ cudaError_t launch_gram_tc(const GramArgs &a, int *status, int max_ctas, cudaStr
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (a.kp == 32) {
+        cfg.dynamicSmemBytes = TcShape<32>::SMEM;
+        return cudaLaunchKernelEx(&cfg, gram_tc_kernel<32>, a, status);
+    }
     if (a.kp == 64) {
         cfg.dynamicSmemBytes = TcShape<64>::SMEM;
         return cudaLaunchKernelEx(&cfg, gram_tc_kernel<64>, a, status);

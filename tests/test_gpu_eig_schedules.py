@@ -105,9 +105,12 @@ def test_split_schedule_on_two_streams_matches_fused_and_oracle(k, n, precision)
         assert exp.sync() == 0
     Wb = lbm.W[None, :, None, None]
     fb = _flat(f0.astype(np.float64) - Wb)
+    # the same algorithm; at 33 <= k <= 64 the split tridiagonalization sums its dot products
+    # over two warps (another summation order), and the increment's rounding difference
+    # scales with Q's condition number (up to ~80 here: 80 x FP32 epsilon ~ 5e-6)
     for sch in (L.LETKF_EIG_SPLIT, L.LETKF_EIG_SPLIT_CHECK):
         errs = C.point_parity(_flat(outs[sch]), _flat(outs[L.LETKF_EIG_FUSED]), fb)
-        assert max(errs) < 2e-6, (sch, errs)
+        assert max(errs) < 5e-6, (sch, errs)
     half = (n * n // 2 + 63) // 64 * 64
     pts = sorted({0, half - 1, half, half + 1, n * n - 1, n * n // 3})
     ref = C.oracle_points(f0, Yf, yo, net, var, 3.0, UV, [(p % n, p // n) for p in pts])

@@ -1,6 +1,6 @@
 """Mixed precision (LETKF_MIXED): the tensor-core Gram path against the FP64 oracle.
 
-For 33 <= k <= 128 the mixed form builds A = Yb^T R_loc^-1 Yb and c on the tcgen05 tensor
+For 17 <= k <= 128 the mixed form builds A = Yb^T R_loc^-1 Yb and c on the tcgen05 tensor
 cores from split FP16 operands (hi + lo, ~22 significant bits) with FP32 accumulation; the
 rest of the analysis is the FP32 path.  Its stated error against the oracle, per output:
   Gram matrix A, vector c            1e-5 relative L2 (measured ~1e-6)
@@ -8,8 +8,9 @@ rest of the analysis is the FP32 path.  Its stated error against the oracle, per
   eigenvalues of Q                    1e-5 of the largest
   analysis mean, mean increment,
   analysis perturbations              1e-5 relative L2 (the bar of the FP32 form)
-The cases cover both tile shapes of the kernel (k padded to 64: 2x2 points per tile; k
-padded to 128: one point per tile), members beyond k in the padding, ragged tiles, tiles
+The cases cover the three tile shapes of the kernel (k padded to 32: 4x2 points per tile,
+two points per operand tile; k padded to 64: 2x2 points per tile; k padded to 128: one point
+per tile), members beyond k in the padding, ragged tiles, tiles
 whose candidates fill several segments, points and whole tiles without local observations,
 row-chunked launches, and bitwise reproducibility.
 """
@@ -64,7 +65,10 @@ def _parity(exp, f0, yo, net, var, radius, obs_vars=UV, tol=1e-5):
 
 
 @pytest.mark.parametrize("k,nx,ny,stride,radius", [
-    (33, 21, 19, 3, 3.0),     # smallest k of the form; 31 padded members; ragged 2x2 tiles
+    (17, 22, 19, 3, 3.0),     # smallest k of the form; 15 padded members; ragged 4x2 tiles
+    (24, 20, 18, 2, 2.5),     # two points per operand tile
+    (32, 16, 16, 2, 3.0),     # no padding in the 32-member form
+    (33, 21, 19, 3, 3.0),     # 31 padded members; ragged 2x2 tiles
     (50, 20, 20, 2, 2.5),     # k not a multiple of 4 (scalar epilogue stores)
     (64, 16, 16, 2, 3.0),     # no padding, ~110 local observation scalars
     (65, 13, 11, 3, 2.0),     # first k of the 128-member tile
@@ -88,6 +92,8 @@ def test_mixed_gram_cvec_counts_eigenvalues_match_oracle(k, nx, ny, stride, radi
 
 
 @pytest.mark.parametrize("k,nx,ny,stride,radius", [
+    (20, 23, 17, 3, 3.0),
+    (32, 18, 18, 2, 3.0),
     (48, 18, 17, 3, 3.0),
     (64, 16, 16, 2, 3.0),
     (96, 12, 12, 3, 2.5),
