@@ -723,6 +723,8 @@ def main(argv=None):
         return group_main(args, device, rank, world)
     if args.workload == "evd_table1":
         return evd_main(args, device, rank, world)
+    if args.workload in ("paper_dense", "paper_sparse"):
+        return paper_main(args, device, rank, world)
     w = synth.WORKLOADS[args.workload]
     steps = args.steps if args.steps is not None else DEFAULT_STEPS.get(args.workload, 20)
     warm = max(3, args.warmup)
@@ -899,6 +901,121 @@ def evd_main(args, device, rank, world):
                           "comparator": "torch.linalg.eigh: library, context only",
                           "paper_hardware": "A100 40 GB (context, not a target)",
                           "results": rows}))
+    return 0
+
+
+# The paper's LETKF time per cycle at M = 64 on one A100 for its naive parallelization (case A,
+# every GPU analyses every grid point): 39.5 ms (dense), and the total cycle times 73.0 ms
+# (sparse, case A) and 19.2 ms (sparse, case C on 64 GPUs).  Context, not targets.
+PAPER_DENSE_LETKF_MS_M64 = 39.5
+PAPER_SPARSE_CYCLE_MS_M64 = {"case_A": 73.0, "case_C": 19.2}
+
+
+def paper_main(args, device, rank, world):
+    """The paper's own workloads (Sec. V): a 128 x 128 D2Q9 turbulence (tau 0.52, the
+    Kolmogorov plus band-limited forcing of the 256^2 workload, 5,000-step spin-up of the truth
+    and of every member from perturbed copies of it), rho, u and v observed (V = 3) with 20 %
+    noise per variable, 100 steps per cycle, ensembles of M = 4, 16 and 64.
+      paper_dense   every grid point observed, only its own observation local (l_max = 1)
+      paper_sparse  every 4th point observed (L = 32^2), Gaspari-Cohn with cutoff 6 cells
+    Timed: graph-captured cycles of each form, and the analysis alone (obs operator,
+    transposes, Gram, eigensolve/transform/update) from the cycle's phase events."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2308_03310_gb300 import letkf as L
+
+    n = 128
+    dense = args.workload == "paper_dense"
+    steps = args.steps if args.steps is not None else 20
+    warm = max(3, args.warmup)
+    kol = synth.kolmogorov_force(n, n, 1e-5, 4)
+    rnd = synth.band_limited_force(n, n, 4.0, 6.0, 1e-5, 20230804)
+    force = np.stack([kol[0] + rnd[0], kol[1] + rnd[1]]).astype(np.float32)
+    net = synth.regular_obs_network(n, n, 1 if dense else 4)
+    ruv = L.LETKF_OBS_RHO | L.LETKF_OBS_U | L.LETKF_OBS_V
+    if dense:
+        loc = dict(loc_radius=1.0, loc_cutoff2=1.0, loc_kind=L.LETKF_LOC_GAUSS)
+    else:
+        loc = dict(loc_radius=3.0 / math.sqrt(10.0 / 3.0), loc_cutoff2=36.0,
+                   loc_kind=L.LETKF_LOC_GC)
+    rows = []
+    for k in (4, 16, 64):
+        # nature run and members spun up together (the truth is the auxiliary member)
+        spin = L.Experiment(n, n, k, 0.52, net, np.ones(len(net) * 3, np.float32),
+                            obs_vars=ruv, n_aux=1, force=force, device=device, **loc)
+        ux0 = synth.gaussian((n, n), 1e-3, 71)
+        uy0 = synth.gaussian((n, n), 1e-3, 72)
+        ux = np.concatenate([ux0[None] + synth.gaussian((k, n, n), 5e-3, 73), ux0[None]])
+        uy = np.concatenate([uy0[None] + synth.gaussian((k, n, n), 5e-3, 74), uy0[None]])
+        spin.set_macro(np.ones((k + 1, n, n), np.float32), ux.astype(np.float32),
+                       uy.astype(np.float32))
+        spin.forecast(5000)
+        y0 = spin.get_obs()[k]
+        sig = 0.2 * np.array([np.std(y0[0::3] - 1.0), np.std(y0[1::3]), np.std(y0[2::3])])
+        var = np.tile(sig ** 2, len(net)).astype(np.float32)
+        yos = []
+        for c in range(warm + steps):
+            spin.forecast(100)
+            y = spin.get_obs()[k]
+            yos.append(torch.from_numpy((y + np.tile(sig, len(net)) * synth.gaussian(
+                y.shape, 1.0, 9000 + c)).astype(np.float32)).to(device))
+        members = torch.empty((k, 9, n, n), dtype=torch.float32, device=device)
+        L.letkf_get_deviation(spin.h, members.data_ptr(), 0, k, L.LETKF_DEVICE)
+        torch.cuda.synchronize(device)
+        spin.close()
+        row = {"M": k}
+        for name, prec in (("fp32", L.LETKF_FP32), ("mixed", L.LETKF_MIXED)):
+            exp = L.Experiment(n, n, k, 0.52, net, var, obs_vars=ruv, force=force,
+                               precision=prec, device=device, **loc)
+            L.letkf_set_deviation(exp.h, members.data_ptr(), 0, k, L.LETKF_DEVICE)
+            exp.enable_timing(True)
+            for c in range(warm):
+                exp.cycle(100, yos[c])
+            torch.cuda.synchronize(device)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(steps)]
+            ana = []
+            for c in range(steps):
+                ev[c][0].record(exp.stream)
+                exp.cycle(100, yos[warm + c])
+                ev[c][1].record(exp.stream)
+                t = exp.timings()                 # waits for this cycle's phase events
+                ana.append(t["obs_ms"] + t["transpose_in_ms"] + t["gram_ms"] + t["eigen_ms"] +
+                           t["transpose_out_ms"])
+            torch.cuda.synchronize(device)
+            cyc = [a.elapsed_time(b) for a, b in ev]
+            rc = exp.sync()
+            if rc:
+                raise RuntimeError(f"{args.workload} M={k} {name}: {L.strerror(rc)}")
+            st = exp.stats()
+            row[name] = {"analyses_per_s": n * n * steps / (sum(cyc) / 1e3),
+                         "ms_per_cycle": statistics.mean(cyc),
+                         "analysis_ms_per_cycle": statistics.mean(ana),
+                         "eig_schedule": EIG_NAMES.get(st.eig_schedule, str(st.eig_schedule))}
+            exp.close()
+        row["max_local_obs"] = st.max_local_obs
+        rows.append(row)
+        del members, yos
+        torch.cuda.empty_cache()
+    head = rows[-1]["fp32"]
+    line = {"metric": METRIC, "value": reduce_sum(head["analyses_per_s"], device), "unit": UNIT,
+            "n_gpus": world, "steps": steps, "warmup": warm,
+            "ms_per_step": head["ms_per_cycle"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "grid": "128x128", "M": [4, 16, 64],
+                       "obs": "every point, l_max = 1" if dense else
+                              "every 4th point, Gaspari-Cohn cutoff 6",
+                       "obs_vars": "rho,u,v", "obs_noise": "20 % of each variable's RMS",
+                       "steps_per_cycle": 100, "value_at": "M = 64, FP32",
+                       "parallelism": "independent replica per GPU"},
+            "results": rows,
+            "paper_a100_context": ({"letkf_ms_per_cycle_M64_case_A": PAPER_DENSE_LETKF_MS_M64}
+                                   if dense else
+                                   {"cycle_ms_M64": PAPER_SPARSE_CYCLE_MS_M64})}
+    if rank == 0:
+        print(json.dumps(line))
     return 0
 
 

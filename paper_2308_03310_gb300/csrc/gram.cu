@@ -25,7 +25,16 @@
 namespace lk {
 namespace {
 
-constexpr int kChunk = 32;  // observation points per staged chunk
+constexpr int kChunk = 64;  // observation points per staged chunk
+
+// Staged dy rows are stored with their 16-byte pieces permuted: piece 2 b + h (h = 0, 1: the
+// two halves of the 8-float block b) goes to position h KB + b.  A warp's 16-byte loads of the
+// first (or second) halves of up to 8 distinct blocks then fall in distinct bank groups
+// (position mod 8), where the natural order put blocks b and b + 4 in the same group.
+template <int KB>
+__device__ __forceinline__ int piece_pos(int c4) {
+    return (c4 & 1) * KB + (c4 >> 1);
+}
 
 template <int KP>
 struct GramShape {
@@ -115,7 +124,7 @@ __global__ void __launch_bounds__(GramShape<KP>::NT, 2) gram_kernel(GramArgs a) 
         for (int e = tid; e < nch * V * Q4; e += NT) {
             const int row = e / Q4, c4 = e % Q4;
             const int s = oidx[row / V] * V + row % V;
-            reinterpret_cast<float4 *>(ys + row * KP)[c4] =
+            reinterpret_cast<float4 *>(ys + row * KP)[piece_pos<KB>(c4)] =
                 __ldg(reinterpret_cast<const float4 *>(a.yb + (size_t)s * KP) + c4);
         }
         // localization weights of every (point, observation) pair of the chunk
@@ -134,11 +143,9 @@ __global__ void __launch_bounds__(GramShape<KP>::NT, 2) gram_kernel(GramArgs a) 
                 nl += (r == 0);
                 for (int v = 0; v < V; ++v) {
                     const float sw = w * rv[t * V + v];
-                    const float *row = ys + (t * V + v) * KP;
-                    const float4 a0 = reinterpret_cast<const float4 *>(row + ti * 8)[0];
-                    const float4 a1 = reinterpret_cast<const float4 *>(row + ti * 8)[1];
-                    const float4 b0 = reinterpret_cast<const float4 *>(row + tj * 8)[0];
-                    const float4 b1 = reinterpret_cast<const float4 *>(row + tj * 8)[1];
+                    const float4 *row = reinterpret_cast<const float4 *>(ys + (t * V + v) * KP);
+                    const float4 a0 = row[ti], a1 = row[KB + ti];
+                    const float4 b0 = row[tj], b1 = row[KB + tj];
                     const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
                     const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
                     const float dvs = dv[t * V + v];
