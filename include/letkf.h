@@ -259,7 +259,7 @@ int letkf_cycle(letkf_handle *h, int32_t nsteps, const float *yo, int32_t where)
  * same stream.  Each handle's result equals its letkf_analyze on its schedule bit for bit.  A
  * handle on LETKF_EIG_AUTO that has not picked yet picks at its first group analysis (as at
  * its first letkf_analyze); a group cycle that contains such a handle runs without capture.
- *   hs     n distinct handles of one device, 1 <= n <= 8; the work runs on hs[0]'s stream,
+ *   hs     n distinct handles of one device, 1 <= n <= 16; the work runs on hs[0]'s stream,
  *          ordered after each handle's earlier work and before its later work
  *   yo     n observation vectors (where = LETKF_HOST/DEVICE), yo[i] of handle hs[i]
  * letkf_group_cycle(hs, n, nsteps, yo, where): every handle's lbm_forecast(nsteps) and the

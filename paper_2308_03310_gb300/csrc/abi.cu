@@ -571,7 +571,7 @@ int enqueue_analysis(letkf_handle *h, letkf_probe *probe) {
 
 // ---- groups of handles -----------------------------------------------------------------
 
-constexpr int kMaxGroup = 8;
+constexpr int kMaxGroup = 16;
 
 // Resident grids of the grouped eigen kernels, per device, prepared once per process.
 int group_blocks(int device, const int **out) {

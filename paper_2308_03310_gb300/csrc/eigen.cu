@@ -1218,7 +1218,9 @@ __global__ void __launch_bounds__(32 * kPairWarps, 5) eig_tridiag_pair_kernel(Ei
         if (a.nloc && a.nloc[lp] == 0) continue;   // the same decision for both warps
         float *Ag = a.gram + (size_t)lp * k * k;
         // ---- the lane's column of Q = diag + A from the upper triangle: rows i <= t from row
-        // i (coalesced over the lanes), rows i > t from the lane's own row t
+        // i (coalesced over the lanes), rows i > t from the lane's own row t (each 32-byte
+        // sector of it is read by eight consecutive loads: through L1; the kernel writes only
+        // the lower triangle, so the upper triangle it reads never changes under it)
         float q[64];
         {
             const float *col = Ag + t;          // Q[i][t], i <= t: down column t
@@ -1226,7 +1228,7 @@ __global__ void __launch_bounds__(32 * kPairWarps, 5) eig_tridiag_pair_kernel(Ei
             const bool own = t < k;
 #pragma unroll
             for (int i = 0; i < 64; ++i) {
-                q[i] = (own && i < k) ? __ldcg(i <= t ? col : row + i) : 0.0f;
+                q[i] = (own && i < k) ? __ldg(i <= t ? col : row + i) : 0.0f;
                 col += k;
             }
         }

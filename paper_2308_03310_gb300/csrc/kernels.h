@@ -125,7 +125,7 @@ struct EigSplit {
 };
 // Grouped schedule: the points of several chunks (segments) of any k, one persistent launch
 // per column class (k <= 32, <= 64, <= 128) with dynamic work distribution.
-constexpr int kMaxGroupSeg = 8;  // segments per column class and launch
+constexpr int kMaxGroupSeg = 16;  // segments per column class and launch
 struct EigGroup {
     int n;                       // segments
     int kmax;                    // largest k among them: each warp's shared-memory slice

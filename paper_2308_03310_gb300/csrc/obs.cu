@@ -30,13 +30,19 @@ __global__ void __launch_bounds__(128) obs_operator_kernel(ObsOpArgs a) {
             val[r][0] = val[r][1] = val[r][2] = 0.0f;
             if (m < a.nmem) {
                 const float *src = a.g + (size_t)m * NV * npts + p;
-                float drho = 0.0f, jx = 0.0f, jy = 0.0f;
+                float gq[NV];
+#pragma unroll
+                for (int q = 0; q < NV; ++q) gq[q] = src[q * npts];
+                // rho - 1 summed over opposite directions first: their deviations' parts that
+                // are odd in c (the momentum) cancel inside each pair, so the partial sums stay
+                // at the size of rho - 1 instead of the flow's u / 3
+                const float drho = gq[4] + ((gq[0] + gq[8]) + (gq[2] + gq[6])) +
+                                   ((gq[1] + gq[7]) + (gq[3] + gq[5]));
+                float jx = 0.0f, jy = 0.0f;
 #pragma unroll
                 for (int q = 0; q < NV; ++q) {
-                    const float gq = src[q * npts];
-                    drho += gq;
-                    if (cx(q) != 0) jx += cx(q) > 0 ? gq : -gq;
-                    if (cy(q) != 0) jy += cy(q) > 0 ? gq : -gq;
+                    if (cx(q) != 0) jx += cx(q) > 0 ? gq[q] : -gq[q];
+                    if (cy(q) != 0) jy += cy(q) > 0 ? gq[q] : -gq[q];
                 }
                 const float rinv = 1.0f / (1.0f + drho);
                 // density is carried as rho - 1 so that its perturbations keep their digits
