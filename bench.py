@@ -45,8 +45,13 @@ SMS = 152
 #                 populations; two time steps per launch) + 8 B per node of force
 #   transpose     2 x 36 k B per grid point (read + write of the 9 x k block)
 #   obs_operator  36 B per (observation point, member) read + 4 V B per (point, member) written x2
-#   gram          2 k^2 flops per local observed scalar per grid point
-#   eigen_update  11 k^3 flops per grid point (symmetric EVD with vectors + transform)
+#   gram          k (k + 1) flops per local observed scalar per grid point (the upper triangle
+#                 of the symmetric A, one multiply-add per entry) + 2 k for c
+#   eigen_update  eigenvector schedules (FUSED, SPLIT): 11 k^3 flops per grid point (symmetric
+#                 EVD with vectors ~9 k^3, transform ~2 k^3); EVD-free schedule (RATIONAL):
+#                 4/3 k^3 (Householder tridiagonalization) + 40 k^2 (the reflectors applied to
+#                 the 10 rows [dX; c] twice) + 36 k (n + 1) (n shifted solves of 9 rows and the
+#                 mean's solve, forward and back; n = 8 poles below condition 1e2)
 
 
 def parse_args(argv=None):
@@ -222,7 +227,14 @@ def fp32_peak_tflops(sm_mhz: float) -> float:
     return SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
-def kernel_work(w, k, npts, mean_local_obs, V, nobs_pts, chunks, steps):
+def eigen_flops_per_point(k, schedule):
+    """Algorithmic flops of the eigensolve phase per grid point for the schedule in use."""
+    if schedule == 4:   # RATIONAL: tridiagonalization, reflector passes, shifted solves
+        return 4.0 / 3.0 * k ** 3 + 40.0 * k * k + 36.0 * k * 9
+    return 11.0 * k ** 3
+
+
+def kernel_work(w, k, npts, mean_local_obs, V, nobs_pts, chunks, steps, schedule=1):
     """Algorithmic work of one cycle per kernel: (unit, amount, launches)."""
     return {
         # two steps per launch: one read and one write of the state (+ the force) per launch
@@ -230,8 +242,8 @@ def kernel_work(w, k, npts, mean_local_obs, V, nobs_pts, chunks, steps):
                      steps // 2 + steps % 2),
         "obs_operator": ("GB", (36.0 + 8.0 * V) * nobs_pts * k / 1e9, 1),
         "transpose_in": ("GB", 72.0 * k * npts / 1e9, 1),
-        "gram": ("TFLOP", 2.0 * k * k * V * mean_local_obs * npts / 1e12, chunks),
-        "eigen_update": ("TFLOP", 11.0 * k ** 3 * npts / 1e12, chunks),
+        "gram": ("TFLOP", (k * (k + 1) + 2 * k) * V * mean_local_obs * npts / 1e12, chunks),
+        "eigen_update": ("TFLOP", eigen_flops_per_point(k, schedule) * npts / 1e12, chunks),
         "transpose_out": ("GB", 72.0 * k * npts / 1e9, 1),
     }
 
@@ -721,6 +733,8 @@ def main(argv=None):
         return serve_main(args, device, rank, world)
     if args.workload == "group_cfg4":
         return group_main(args, device, rank, world)
+    if args.workload == "group_small":
+        return group_small_main(args, device, rank, world)
     if args.workload == "evd_table1":
         return evd_main(args, device, rank, world)
     if args.workload in ("paper_dense", "paper_sparse"):
@@ -1137,6 +1151,123 @@ def group_main(args, device, rank, world):
     return 0
 
 
+def group_small_main(args, device, rank, world):
+    """Uneven batching where one launch has to carry the GPU: 16 co-resident ensembles on
+    64 x 64 grids (4,096 points each: one ensemble alone fills a small part of the GPU), k
+    cycling through 16, 24, 32, 40, 48, 56, 64 and 20, a clustered network (every 2nd point
+    over a quarter of the domain, every 8th elsewhere, a band without observations, r = 2).
+    Timed per form (graph-captured cycles of 25 steps):
+      grouped_fused   one grouped cycle, every ensemble on the FUSED schedule: the
+                      eigensolve of all 16 ensembles' points is one persistent launch per
+                      column class (k <= 32, <= 64), warps taking points from a counter
+      grouped_auto    one grouped cycle, each ensemble on the schedule AUTO picks for it
+      separate_auto   the 16 ensembles cycled one after another on their own streams
+    value = grid-point analyses per second of grouped_fused (FP32)."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2308_03310_gb300 import letkf as L
+
+    nx = ny = 64
+    ks = (16, 24, 32, 40, 48, 56, 64, 20) * 2
+    r = 2.0
+    net = synth.clustered_obs_network(nx, ny, 2, 8, patch=(4, 4, nx // 2, ny // 2),
+                                      empty_band=(44, 12))
+    LV = len(net) * 2
+    sigma = 0.01
+    var = np.full(LV, sigma * sigma, dtype=np.float32)
+    steps_cycle = 25
+    steps = args.steps if args.steps is not None else 20
+    warm = max(3, args.warmup)
+    tx, ty = synth.band_limited_force(nx, ny, 2.0, 5.0, 0.02, 61)
+    xs, ys = net[:, 0], net[:, 1]
+    ytrue = np.stack([tx[ys, xs], ty[ys, xs]], axis=1).reshape(-1)
+    obs = [torch.from_numpy((ytrue + synth.gaussian(LV, sigma, 91 + c)).astype(np.float32))
+           .to(device) for c in range(warm + steps)]
+
+    def ensembles(prec, schedule):
+        exps = []
+        for i, k in enumerate(ks):
+            e = L.Experiment(nx, ny, k, 0.55, net, var, loc_radius=r, precision=prec,
+                             device=device, eig_schedule=schedule)
+            px = synth.gaussian((k, ny, nx), 0.005, 3000 + 2 * i)
+            py = synth.gaussian((k, ny, nx), 0.005, 3001 + 2 * i)
+            e.set_macro(np.ones((k, ny, nx), np.float32), (tx[None] + px).astype(np.float32),
+                        (ty[None] + py).astype(np.float32))
+            exps.append(e)
+        return exps
+
+    def timed(exps, run_cycle):
+        stream = exps[0].stream
+        for c in range(warm):
+            run_cycle(exps, c)
+        torch.cuda.synchronize(device)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for c in range(steps):
+            ev[c][0].record(stream)
+            run_cycle(exps, warm + c)
+            ev[c][1].record(stream)
+        torch.cuda.synchronize(device)
+        for e in exps:
+            rc = e.sync()
+            if rc:
+                raise RuntimeError(f"group_small cycle failed: {L.strerror(rc)}")
+        return [a.elapsed_time(b) for a, b in ev]
+
+    def group_cycle(exps, c):
+        L.letkf_group_cycle(exps, steps_cycle, [obs[c]] * len(exps))
+
+    def separate_cycles(exps, c):
+        for e in exps:
+            e.cycle(steps_cycle, obs[c])
+        stream = exps[0].stream
+        for e in exps[1:]:
+            done = torch.cuda.Event()
+            done.record(e.stream)
+            stream.wait_event(done)
+
+    pts = nx * ny * len(ks)
+    out = {}
+    for name, prec in (("fp32", L.LETKF_FP32), ("mixed", L.LETKF_MIXED)):
+        res = {}
+        for variant, sched, runner in (("grouped_fused", L.LETKF_EIG_FUSED, group_cycle),
+                                       ("grouped_auto", L.LETKF_EIG_AUTO, group_cycle),
+                                       ("separate_auto", L.LETKF_EIG_AUTO, separate_cycles)):
+            exps = ensembles(prec, sched)
+            cyc = timed(exps, runner)
+            res[variant] = {"analyses_per_s": pts * len(cyc) / (sum(cyc) / 1e3),
+                            "ms_per_cycle": statistics.mean(cyc),
+                            "p99_cycle_ms": float(np.percentile(cyc, 99)),
+                            "schedules": sorted({EIG_NAMES.get(e.stats().eig_schedule, "auto")
+                                                 for e in exps})}
+            st = exps[0].stats()
+            for e in exps:
+                e.close()
+            del exps
+            torch.cuda.empty_cache()
+        res["zero_obs_fraction"] = st.n_zero_obs / st.n_points
+        res["max_local_obs"] = st.max_local_obs
+        res["grouped_fused_vs_separate"] = (res["grouped_fused"]["analyses_per_s"] /
+                                            res["separate_auto"]["analyses_per_s"])
+        out[name] = res
+    head = out["fp32"]["grouped_fused"]
+    line = {"metric": METRIC, "value": reduce_sum(head["analyses_per_s"], device), "unit": UNIT,
+            "n_gpus": world, "steps": steps, "warmup": warm, "ms_per_step": head["ms_per_cycle"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "group_small", "grid": "64x64", "ensembles": len(ks),
+                       "k": list(ks), "network": "clustered: every 2nd point over a quarter, "
+                       "every 8th elsewhere, a band without observations", "loc_radius": r,
+                       "steps_per_cycle": steps_cycle, "precision": "fp32",
+                       "parallelism": "one grouped cycle of 16 ensembles"},
+            "p99_cycle_ms": head["p99_cycle_ms"], "group": out}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def serve_main(args, device, rank, world):
     """The serving workload: a seeded Poisson stream of independent DA experiments (arrivals
     at 20/s; grids 128^2..1024^2, k 16..128, 10..100 cycles, (u, v) every 4th or 8th point),
@@ -1340,7 +1471,7 @@ def measure(w, members, setup, yos, device, precision, steps, warm, world, eig_s
         peaks["fp32_tflops"] = peak32["tflops"]
     sm_mhz = peaks["sm_max_mhz"] or 2070.0
     work = kernel_work(w, w.k, w.n_points, st.mean_local_obs, exp.V, exp.L, st.n_chunks,
-                       w.steps_per_cycle)
+                       w.steps_per_cycle, exp.stats().eig_schedule)
     tensor_gram = precision == L.LETKF_MIXED and 17 <= w.k <= 128
     table = roofline_table(work, ms, peaks, sm_mhz, tensor_gram)
     top = max(table, key=lambda n: table[n]["ms_per_cycle"])

@@ -61,10 +61,12 @@ __device__ __forceinline__ void upper_block(int r, int &ti, int &tj) {
     tj = i + rem;
 }
 
-template <int KP>
+// VV: observed variables per point (1..3), a template parameter so the per-scalar loop unrolls
+template <int KP, int VV>
 __global__ void __launch_bounds__(GramShape<KP>::NT, 2) gram_kernel(GramArgs a) {
     using S = GramShape<KP>;
     constexpr int KB = S::KB, T = S::T, P = S::P, TW = S::TW, TH = S::TH, NT = S::NT;
+    constexpr int V = VV;
 
     __shared__ int cell_base[kMaxPatchCells];
     __shared__ int cell_pre[kMaxPatchCells + 1];
@@ -78,7 +80,6 @@ __global__ void __launch_bounds__(GramShape<KP>::NT, 2) gram_kernel(GramArgs a) 
     float *wts = ys + kChunk * 3 * KP;                 // [P][kChunk]
 
     const ObsNet &net = a.net;
-    const int V = net.V;
     const int tid = threadIdx.x;
     const int tx0 = blockIdx.x * TW;
     const int ty0 = a.y_begin + blockIdx.y * TH;
@@ -141,6 +142,7 @@ __global__ void __launch_bounds__(GramShape<KP>::NT, 2) gram_kernel(GramArgs a) 
                 const float w = wts[p * kChunk + t];
                 if (w == 0.0f) continue;
                 nl += (r == 0);
+#pragma unroll 1
                 for (int v = 0; v < V; ++v) {
                     const float sw = w * rv[t * V + v];
                     const float4 *row = reinterpret_cast<const float4 *>(ys + (t * V + v) * KP);
@@ -187,8 +189,16 @@ size_t gram_smem() {
 
 template <int KP>
 cudaError_t prepare_kp() {
-    return cudaFuncSetAttribute(gram_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)gram_smem<KP>());
+    const int smem = (int)gram_smem<KP>();
+    cudaError_t e = cudaFuncSetAttribute(gram_kernel<KP, 1>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gram_kernel<KP, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gram_kernel<KP, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem);
+    return e;
 }
 
 template <int KP>
@@ -197,7 +207,12 @@ cudaError_t launch_kp(const GramArgs &a, cudaStream_t s) {
     const size_t smem = gram_smem<KP>();
     const int rows = a.y_end - a.y_begin;
     dim3 grid((a.nx + S::TW - 1) / S::TW, (rows + S::TH - 1) / S::TH);
-    gram_kernel<KP><<<grid, S::NT, smem, s>>>(a);
+    switch (a.net.V) {
+        case 1: gram_kernel<KP, 1><<<grid, S::NT, smem, s>>>(a); break;
+        case 2: gram_kernel<KP, 2><<<grid, S::NT, smem, s>>>(a); break;
+        case 3: gram_kernel<KP, 3><<<grid, S::NT, smem, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -104,31 +104,29 @@ __device__ __forceinline__ void apply_reflector(float (&y)[KM], const float4 *v4
     }
 }
 
-// The reflector's entries that lane r of a point stages for reflector j: rows 4 G0 + r + 10 u
-// (G0 = the 4-row group of row j + 1), v_j by absolute row, zero outside rows j+1..k-1.
-constexpr int kStage = 7;  // ceil(64 / 10) rows per lane
+// Lane r of a point stages entries r + 10 u of reflector j (m = k-1-j entries) into rows
+// j + 1 + r + 10 u of the staging slot, and lanes r < 3 zero the rows 4 G0 .. j below them
+// in the 4-row group G0 of row j + 1 (rows at and beyond k stay zero from the start).
+constexpr int kStage = 7;  // ceil(64 / 10) entries per lane
 
-template <int KM>
 __device__ __forceinline__ void fetch_reflector(const float *Ag, int k, int j, int r, bool act,
                                                 float (&pf)[kStage]) {
-    const int base = 4 * ((j + 1) >> 2) + r;
-    const float *v = refl(Ag, k, j);
+    const int n = act ? k - 1 - j - r : 0;   // entries r, r + 10, .. below m
+    const float *v = refl(Ag, k, j) + r;
 #pragma unroll
-    for (int u = 0; u < kStage; ++u) {
-        const int row = base + 10 * u;
-        pf[u] = (act && row >= j + 1 && row < k) ? __ldcg(v + (row - j - 1)) : 0.0f;
-    }
+    for (int u = 0; u < kStage; ++u) pf[u] = 10 * u < n ? __ldcg(v + 10 * u) : 0.0f;
 }
 
-template <int KM>
-__device__ __forceinline__ void stage_reflector(float *vb, int j, int r, bool lane_ok,
+__device__ __forceinline__ void stage_reflector(float *vb, int k, int j, int r, bool lane_ok,
                                                 const float (&pf)[kStage]) {
-    const int base = 4 * ((j + 1) >> 2) + r;
+    if (!lane_ok) return;
+    const int n = k - 1 - j - r;
+    float *dst = vb + j + 1 + r;
 #pragma unroll
-    for (int u = 0; u < kStage; ++u) {
-        const int row = base + 10 * u;
-        if (lane_ok && row < KM) vb[row] = pf[u];
-    }
+    for (int u = 0; u < kStage; ++u)
+        if (10 * u < n) dst[10 * u] = pf[u];
+    const int pad = 4 * ((j + 1) >> 2) + r;   // rows of the first group below row j + 1
+    if (r < 3 && pad <= j) vb[pad] = 0.0f;
 }
 
 // y <- y H (forward: H_0 first) or y <- y H^T (reverse: H_{k-3} first), every row of the warp's
@@ -144,12 +142,13 @@ __device__ __forceinline__ void apply_h(float (&y)[KM], const float *Ag, const f
     if (nrefl <= 0) return;
     float pf[kStage];
     int j = reverse ? k - 3 : 0;
-    fetch_reflector<KM>(Ag, k, j, r, act, pf);
+    fetch_reflector(Ag, k, j, r, act, pf);
+    float *vb0 = vbuf + (lane_ok ? pg : 0) * VS;
     for (int it = 0; it < nrefl; ++it) {
-        float *vb = vbuf + (it & 1) * kPts * VS + (lane_ok ? pg : 0) * VS;
-        stage_reflector<KM>(vb, j, r, lane_ok, pf);
+        float *vb = vb0 + (it & 1) * kPts * VS;
+        stage_reflector(vb, k, j, r, lane_ok, pf);
         const int jn = reverse ? j - 1 : j + 1;
-        if (it + 1 < nrefl) fetch_reflector<KM>(Ag, k, jn, r, act, pf);
+        if (it + 1 < nrefl) fetch_reflector(Ag, k, jn, r, act, pf);
         __syncwarp();
         const float tau = act ? tau_s[j] : 0.0f;
         apply_reflector<KM>(y, reinterpret_cast<const float4 *>(vb), tau, (j + 1) >> 2);
@@ -224,6 +223,9 @@ __global__ void __launch_bounds__(32 * kWarpsR) eig_rational_kernel(EigArgs a, E
     float2 *tab = reinterpret_cast<float2 *>(ws + S::off_tab + pgc * S::TS);
     const int k = a.k;
     const float sk1 = sqrtf((float)(k - 1));
+    // staging slots: rows at and beyond k (and every row before its first use) hold zeros
+    for (int i = lane; i < 2 * kPts * S::VS; i += 32) vbuf[i] = 0.0f;
+    __syncwarp();
     const long long ntask = ((long long)a.npts + kPts - 1) / kPts;
     const long long nw = (long long)gridDim.x * kWarpsR;
     for (long long task = (long long)blockIdx.x * kWarpsR + wib; task < ntask; task += nw) {

@@ -210,3 +210,39 @@ def test_invalid_groups_are_rejected():
         L.letkf_group_analyze([exps[0], exps[0]], yos[:2])   # a handle twice
     with pytest.raises(L.LetkfError):
         L.letkf_group_analyze([], [])
+
+
+def test_sixteen_small_ensembles_in_one_group():
+    # the largest group: 16 handles of mixed k on small grids, every one on the FUSED
+    # schedule, so the eigensolve of all their points is one persistent launch per column
+    # class; each grouped result equals its own analysis bit for bit; 17 handles are rejected
+    nx = ny = 20
+    ks = (16, 24, 32, 40, 48, 56, 64, 20) * 2
+    net = _network(nx, ny)
+    var = np.full(len(net) * 2, 1e-4, dtype=np.float32)
+
+    def build():
+        exps, f0s, yos = [], [], []
+        for i, k in enumerate(ks):
+            f0 = C.perturb_nonequilibrium(C.ensemble_state(k, nx, ny, seed=1800 + i), 1e-4,
+                                          1850 + i)
+            e = L.Experiment(nx, ny, k, 0.6, net, var, loc_radius=2.0,
+                             eig_schedule=L.LETKF_EIG_FUSED)
+            e.set_state(f0)
+            exps.append(e)
+            f0s.append(f0)
+            yos.append(C.observations(C.ensemble_state(1, nx, ny, seed=1900 + i), net, UV,
+                                      0.01, 1950 + i)[0])
+        return exps, f0s, yos
+
+    grouped, _, yos = build()
+    L.letkf_group_analyze(grouped, yos)
+    alone, _, _ = build()
+    for e, y in zip(alone, yos):
+        e.analyze(y)
+    for g, a in zip(grouped, alone):
+        assert np.array_equal(g.get_deviation(), a.get_deviation())
+        assert g.sync() == 0 and a.sync() == 0
+    extra = L.Experiment(nx, ny, 8, 0.6, net, var, loc_radius=2.0)
+    with pytest.raises(L.LetkfError):
+        L.letkf_group_analyze(grouped + [extra], yos + [yos[0]])
