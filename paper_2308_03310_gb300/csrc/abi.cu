@@ -199,6 +199,9 @@ struct letkf_handle {
     // the split eigensolve's second stream and its fork/join events (halves of a chunk overlap)
     cudaStream_t stream2 = nullptr;
     cudaEvent_t split_fork = nullptr, split_join = nullptr;
+    // in a group: the stream of this handle's own branch and its fork/join events
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t gfork = nullptr, gjoin = nullptr;
     unsigned char *ws = nullptr;
     bool own_ws = false;
     float *state[2] = {nullptr, nullptr};
@@ -638,54 +641,89 @@ int group_fence(letkf_handle *const *hs, int n, bool join) {
     return LETKF_OK;
 }
 
-// The group's work on the group stream (inside a GroupScope): optional forecasts, then per
-// handle the observation operator and transpose; per chunk round every handle's Gram chunk,
-// the split eigensolve of the handles on the SPLIT schedule, and one grouped eigen launch per
-// column class over the handles on the FUSED schedule; the transposes back.  A handle still on
-// AUTO picks its schedule at its first Gram chunk (eager calls only: the callers do not
-// capture while a handle has yet to pick).
+// The group's work (inside a GroupScope, whose stream S is the first handle's).  Every handle's
+// own phases run on its own branch stream, forked from S: the forecast, the observation
+// operator and transpose, per chunk round its Gram chunk and (SPLIT and RATIONAL schedules) its
+// eigensolve, the transpose back.  The handles on the FUSED schedule join S after each round's
+// Gram chunks for one grouped eigen launch per column class over all of them, and fork again
+// after it.  All branches join S at the end, so the group's work is ordered on S (and inside a
+// capture forms one graph with parallel branches).  A handle still on AUTO picks its schedule
+// at its first Gram chunk (eager calls only: the callers do not capture while a handle has yet
+// to pick).
 int enqueue_group(letkf_handle *const *hs, int n, int nsteps) {
     letkf_handle *h = hs[0];
+    const cudaStream_t S = h->stream;
     const int *blocks = nullptr;
     int rc = group_blocks(h->device, &blocks);
     if (rc) return rc;
-    for (int i = 0; i < n && nsteps >= 0; ++i)
-        if ((rc = enqueue_forecast(hs[i], nsteps))) return rc;
+    auto fork = [&](letkf_handle *g) -> int {   // g's branch after S's current work
+        CK(cudaEventRecord(h->gfork, S));
+        CK(cudaStreamWaitEvent(g->gstream, h->gfork, 0));
+        return LETKF_OK;
+    };
+    auto join = [&](letkf_handle *g) -> int {   // S after g's branch
+        CK(cudaEventRecord(g->gjoin, g->gstream));
+        CK(cudaStreamWaitEvent(S, g->gjoin, 0));
+        return LETKF_OK;
+    };
+    struct OnBranch {  // g enqueues on its branch while this lives
+        letkf_handle *g;
+        cudaStream_t s;
+        explicit OnBranch(letkf_handle *g_) : g(g_), s(g_->stream) { g->stream = g->gstream; }
+        ~OnBranch() { g->stream = s; }
+    };
+    for (int i = 0; i < n; ++i)
+        if ((rc = fork(hs[i]))) return rc;
     int rounds = 0;
     for (int i = 0; i < n; ++i) {
         letkf_handle *g = hs[i];
+        OnBranch b(g);
+        if (nsteps >= 0 && (rc = enqueue_forecast(g, nsteps))) return rc;
         if ((rc = enqueue_obs(g))) return rc;
         const cudaError_t e = lk::launch_transpose_in(g->state[g->cur], g->xg, g->cfg.k,
-                                                      g->plan.npts, h->stream);
+                                                      g->plan.npts, g->stream);
         if (e != cudaSuccess) return cuda_fail(g, e);
         rounds = std::max(rounds, (g->cfg.ny + g->plan.chunk_rows - 1) / g->plan.chunk_rows);
     }
     for (int r = 0; r < rounds; ++r) {
         lk::EigArgs segs[kMaxGroup];
+        letkf_handle *fused[kMaxGroup];
         int m = 0;
         for (int i = 0; i < n; ++i) {
             letkf_handle *g = hs[i];
             const int y0 = r * g->plan.chunk_rows;
             if (y0 >= g->cfg.ny) continue;
             const int y1 = std::min(g->cfg.ny, y0 + g->plan.chunk_rows);
+            OnBranch b(g);
             if ((rc = enqueue_gram_chunk(g, r, y0, y1))) return rc;
             if (g->eig_schedule == LETKF_EIG_AUTO && (rc = tune_eig_schedule(g, y0, y1)))
                 return rc;
             if (g->eig_schedule == LETKF_EIG_FUSED) {
-                segs[m++] = eig_args(g, y0, y1);
+                segs[m] = eig_args(g, y0, y1);
+                fused[m++] = g;
             } else {
                 const cudaError_t e =
-                    launch_eig_schedule(g, g->eig_schedule, eig_args(g, y0, y1), h->stream, false);
+                    launch_eig_schedule(g, g->eig_schedule, eig_args(g, y0, y1), g->stream, false);
                 if (e != cudaSuccess) return cuda_fail(g, e);
             }
         }
-        if (m > 0) CK(lk::launch_eigen_group(segs, m, h->status + 16, blocks, h->stream));
+        if (m > 0) {
+            for (int i = 0; i < m; ++i)
+                if ((rc = join(fused[i]))) return rc;
+            CK(lk::launch_eigen_group(segs, m, h->status + 16, blocks, S));
+            for (int i = 0; i < m; ++i)
+                if ((rc = fork(fused[i]))) return rc;
+        }
     }
     for (int i = 0; i < n; ++i) {
         letkf_handle *g = hs[i];
-        const cudaError_t e = lk::launch_transpose_out(g->xg, g->state[g->cur], g->cfg.k,
-                                                       g->plan.npts, h->stream);
-        if (e != cudaSuccess) return cuda_fail(g, e);
+        {
+            OnBranch b(g);
+            const cudaError_t e = lk::launch_transpose_out(g->xg, g->state[g->cur], g->cfg.k,
+                                                           g->plan.npts, g->stream);
+            if (e != cudaSuccess) return cuda_fail(g, e);
+        }
+        if ((rc = join(g))) return rc;
     }
     return LETKF_OK;
 }
@@ -774,7 +812,10 @@ int letkf_init(const letkf_config *cfg, void *workspace, size_t workspace_bytes,
     }
     if (cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->split_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->split_join, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&h->split_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->gfork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->gjoin, cudaEventDisableTiming) != cudaSuccess)
         return fail(LETKF_ECUDA);
     if (workspace) {
         h->ws = (unsigned char *)workspace;
@@ -935,11 +976,15 @@ int letkf_destroy(letkf_handle *h) {
     if (dev != h->device) cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->stream2) cudaStreamSynchronize(h->stream2);
+    if (h->gstream) cudaStreamSynchronize(h->gstream);
     destroy_graphs(h);
     destroy_events(h);
     if (h->split_fork) cudaEventDestroy(h->split_fork);
     if (h->split_join) cudaEventDestroy(h->split_join);
+    if (h->gfork) cudaEventDestroy(h->gfork);
+    if (h->gjoin) cudaEventDestroy(h->gjoin);
     if (h->stream2) cudaStreamDestroy(h->stream2);
+    if (h->gstream) cudaStreamDestroy(h->gstream);
     if (h->own_ws && h->ws) cudaFree(h->ws);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     if (dev >= 0 && dev != h->device) cudaSetDevice(dev);

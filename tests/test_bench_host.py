@@ -124,3 +124,19 @@ def test_all_core_oracle_baseline_sums_concurrent_samples(monkeypatch):
     assert r["cores"] == 6 and r["value"] == pytest.approx(60.0)
     assert calls == [("tgv32_k8", 1.5)] * 6
     assert r["sample"].startswith("6 concurrent single-threaded samples")
+
+
+def test_kernel_work_counts_the_algorithm_of_each_kernel():
+    # the Gram forms the upper triangle of a symmetric A (k (k+1) flops per scalar, + 2 k for
+    # c); the eigen phase is an EVD with vectors (11 k^3) on the eigenvector schedules and a
+    # tridiagonalization plus O(k^2) transform on the EVD-free one
+    import synth
+    w = synth.WORKLOADS["turb1024_k64"]
+    k, npts, lv = 64, 1 << 20, 375.0
+    fused = bench.kernel_work(w, k, npts, lv, 2, 65536, 16, 100, schedule=1)
+    rat = bench.kernel_work(w, k, npts, lv, 2, 65536, 16, 100, schedule=4)
+    assert fused["gram"][1] == pytest.approx((k * (k + 1) + 2 * k) * 2 * lv * npts / 1e12)
+    assert fused["eigen_update"][1] == pytest.approx(11.0 * k ** 3 * npts / 1e12)
+    assert rat["eigen_update"][1] == pytest.approx(
+        (4.0 / 3.0 * k ** 3 + 40.0 * k * k + 36.0 * k * 9) * npts / 1e12)
+    assert rat["eigen_update"][1] < 0.2 * fused["eigen_update"][1]
