@@ -216,8 +216,8 @@ def measured_peaks():
             "source": "fallback"}
 
 
-EIG_SCHEDULES = {"auto": 0, "fused": 1, "split": 2, "rational": 4}
-EIG_NAMES = {1: "fused", 2: "split", 3: "split_check", 4: "rational"}
+EIG_SCHEDULES = {"auto": 0, "fused": 1, "split": 2, "rational": 4, "chebyshev": 5}
+EIG_NAMES = {1: "fused", 2: "split", 3: "split_check", 4: "rational", 5: "chebyshev"}
 PEAK_NAMES = {"hbm": "hbm_gbs", "alu": "FP32 FMA peak from the unit counts at max SM clock",
               "tensor": "bf16_tflops_sustained (FP16 operands, same nominal rate)"}
 
@@ -229,13 +229,26 @@ def fp32_peak_tflops(sm_mhz: float) -> float:
 
 def eigen_flops_per_point(k, schedule):
     """Algorithmic flops of the eigensolve phase per grid point for the schedule in use."""
-    if schedule == 4:   # RATIONAL: tridiagonalization, reflector passes, shifted solves
+    if schedule in (4, 5):   # RATIONAL: tridiagonalization, reflector passes, shifted solves
         return 4.0 / 3.0 * k ** 3 + 40.0 * k * k + 36.0 * k * 9
     return 11.0 * k ** 3
 
 
-def kernel_work(w, k, npts, mean_local_obs, V, nobs_pts, chunks, steps, schedule=1):
-    """Algorithmic work of one cycle per kernel: (unit, amount, launches)."""
+def cheb_flops(k, counts):
+    """Flops of the CHEBYSHEV schedule for the given counts (points, products, handed on):
+    each product R A of the ten rows with the k x k Gram matrix is 20 k^2 flops, the final
+    increment and combination 4 k per row; the points passed on cost the RATIONAL count."""
+    return (20.0 * k * k * counts["cheb_products"] + 36.0 * k * counts["cheb_points"]
+            + eigen_flops_per_point(k, 4) * counts["cheb_handed_on"])
+
+
+def kernel_work(w, k, npts, mean_local_obs, V, nobs_pts, chunks, steps, schedule=1,
+                cheb_counts=None):
+    """Algorithmic work of one cycle per kernel: (unit, amount, launches).  For the CHEBYSHEV
+    schedule the eigen phase's work follows the device counters of the cycle (cheb_counts);
+    without them it falls back to the RATIONAL count."""
+    eig = (cheb_flops(k, cheb_counts) if schedule == 5 and cheb_counts
+           else eigen_flops_per_point(k, schedule) * npts)
     return {
         # two steps per launch: one read and one write of the state (+ the force) per launch
         "lbm_step": ("GB", (72.0 * npts * k + 8.0 * npts) * (steps // 2 + steps % 2) / 1e9,
@@ -243,7 +256,7 @@ def kernel_work(w, k, npts, mean_local_obs, V, nobs_pts, chunks, steps, schedule
         "obs_operator": ("GB", (36.0 + 8.0 * V) * nobs_pts * k / 1e9, 1),
         "transpose_in": ("GB", 72.0 * k * npts / 1e9, 1),
         "gram": ("TFLOP", (k * (k + 1) + 2 * k) * V * mean_local_obs * npts / 1e12, chunks),
-        "eigen_update": ("TFLOP", eigen_flops_per_point(k, schedule) * npts / 1e12, chunks),
+        "eigen_update": ("TFLOP", eig / 1e12, chunks),
         "transpose_out": ("GB", 72.0 * k * npts / 1e9, 1),
     }
 
@@ -1430,6 +1443,7 @@ def measure(w, members, setup, yos, device, precision, steps, warm, world, eig_s
     rc = exp.sync()
     if rc:
         raise RuntimeError(f"warm-up cycle failed: {L.strerror(rc)}")
+    counts0 = exp.work_counts()
 
     # ---- timed region: device-resident inputs, L2 flushed between cycles
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -1455,6 +1469,8 @@ def measure(w, members, setup, yos, device, precision, steps, warm, world, eig_s
         raise RuntimeError(f"timed cycles failed: {L.strerror(rc)}")
     cyc_ms = [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]
     total_s = reduce_max(sum(cyc_ms) / 1e3, device)
+    counts1 = exp.work_counts()
+    cheb = {n: (counts1[n] - counts0[n]) / steps for n in counts0}   # per timed cycle
     value = whole_job_rate(w.n_points * steps, total_s, world)
 
     # ---- per-kernel device time and roofline (the same timed cycles)
@@ -1471,7 +1487,7 @@ def measure(w, members, setup, yos, device, precision, steps, warm, world, eig_s
         peaks["fp32_tflops"] = peak32["tflops"]
     sm_mhz = peaks["sm_max_mhz"] or 2070.0
     work = kernel_work(w, w.k, w.n_points, st.mean_local_obs, exp.V, exp.L, st.n_chunks,
-                       w.steps_per_cycle, exp.stats().eig_schedule)
+                       w.steps_per_cycle, exp.stats().eig_schedule, cheb)
     tensor_gram = precision == L.LETKF_MIXED and 17 <= w.k <= 128
     table = roofline_table(work, ms, peaks, sm_mhz, tensor_gram)
     top = max(table, key=lambda n: table[n]["ms_per_cycle"])
@@ -1530,6 +1546,9 @@ def measure(w, members, setup, yos, device, precision, steps, warm, world, eig_s
         "clocks": clocks,
         "local_obs": {"mean": st.mean_local_obs, "max": st.max_local_obs,
                       "zero_fraction": st.n_zero_obs / st.n_points},
+        **({"chebyshev_per_cycle": {**cheb, "mean_degree": (cheb["cheb_products"]
+                                                            / max(cheb["cheb_points"], 1))}}
+           if st_end.eig_schedule == L.LETKF_EIG_CHEBYSHEV else {}),
     }
 
 

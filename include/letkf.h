@@ -65,7 +65,8 @@ extern "C" {
 
 /* Eigensolve schedules (same results up to rounding; see letkf_config.eig_schedule). */
 #define LETKF_EIG_AUTO        0  /* the handle picks one: at its first analysis the schedules
-                                    (FUSED, SPLIT and, for k <= 64, RATIONAL) are timed on
+                                    (FUSED, SPLIT and, for k <= 64, RATIONAL and CHEBYSHEV)
+                                    are timed on
                                     that analysis' first chunk of Gram matrices
                                     (applied to a scratch copy of the forecast, so the analysis
                                     itself is unaffected; one host synchronisation), and the
@@ -88,6 +89,18 @@ extern "C" {
                                     eigenvectors are formed.  A point whose condition bound
                                     exceeds 1e6 is solved by the fused schedule instead.  A
                                     probe's eigenvalues come from an extra eigenvalue-only QL. */
+#define LETKF_EIG_CHEBYSHEV   5  /* EVD-free transform by polynomials in Q, k <= 64: with
+                                    S = Q (rho / (k-1)), whose spectrum lies in [1, kappa],
+                                    kappa from the least of the Gershgorin, Frobenius and trace
+                                    bounds of A, t^-1/2 and t^-1 are replaced by their Chebyshev
+                                    interpolants on [1, kappa_max] (relative error < 2e-8,
+                                    degree 4 at kappa_max = 1.1 up to 36 at 16) and applied to
+                                    [dX; c^T] by Clenshaw's recurrence, one product with A per
+                                    degree.  No factorization or tridiagonalization; a point
+                                    whose bound exceeds 16 is passed to the RATIONAL schedule.
+                                    Pays where Q is well conditioned (ensemble spread small
+                                    against the observation error).  A probe's eigenvalues come
+                                    from a tridiagonalization and an eigenvalue-only QL.      */
 
 /* ---- problem statement --------------------------------------------------
  * Follows the paper's statement of the problem (Sec. II-B): the grid, the
@@ -369,6 +382,22 @@ int letkf_fp32_peak_run(int32_t iters, float *out, int64_t *flops, void *stream)
  * for invalid arguments. */
 double letkf_rational_coefficients(double kappa_max, int32_t n, double *poles,
                                    double *residues);
+
+/* The coefficients of LETKF_EIG_CHEBYSHEV (host computation, FP64): the degree-n interpolants
+ * at the Chebyshev points of the first kind of t^-1/2 (c_rsqrt) and t^-1 (c_inv) on
+ * [1, kappa_max], as coefficients of T_0..T_n in s = (2 t - kappa_max - 1) / (kappa_max - 1)
+ * (caller arrays of n + 1 doubles, 1 <= n <= 256, 1 < kappa_max < 1e6).  Returns the larger of
+ * the two largest relative errors on a fine grid of the interval, or -1 for invalid
+ * arguments. */
+double letkf_chebyshev_coefficients(double kappa_max, int32_t n, double *c_rsqrt,
+                                    double *c_inv);
+
+/* Cumulative counts of the LETKF_EIG_CHEBYSHEV transform on this handle since letkf_init
+ * (device counters, also advanced by the AUTO tuner's trial runs): counts[0] grid points
+ * transformed, counts[1] products with A formed (the sum of the degrees used), counts[2]
+ * points passed on to the RATIONAL schedule.  Waits for the handle's stream; LETKF_EINVAL for
+ * NULL arguments. */
+int letkf_get_work_counts(letkf_handle *h, int64_t *counts);
 
 #ifdef __cplusplus
 }

@@ -52,7 +52,8 @@ struct Plan {
     // byte offsets inside the workspace
     size_t off_state[2], off_force, off_xg, off_obs_xy, off_cell_start, off_cell_obs, off_rinv,
         off_yf, off_yb, off_ybar, off_yo, off_orec, off_gram, off_cvec, off_nloc, off_nloc_all,
-        off_eigval, off_de, off_taus, off_rot, off_nrot, off_list, off_status, total;
+        off_eigval, off_de, off_taus, off_rot, off_nrot, off_list, off_pre_list, off_status,
+        total;
 };
 
 int validate(const letkf_config *c) {
@@ -69,9 +70,10 @@ int validate(const letkf_config *c) {
         return LETKF_EINVAL;
     if (!(c->infl > 0.0f) || !isfinite(c->infl)) return LETKF_EINVAL;
     if (c->precision != LETKF_FP32 && c->precision != LETKF_MIXED) return LETKF_EINVAL;
-    if (c->eig_schedule < LETKF_EIG_AUTO || c->eig_schedule > LETKF_EIG_RATIONAL)
+    if (c->eig_schedule < LETKF_EIG_AUTO || c->eig_schedule > LETKF_EIG_CHEBYSHEV)
         return LETKF_EINVAL;
     if (c->eig_schedule == LETKF_EIG_RATIONAL && c->k > lk::kRationalMaxK) return LETKF_EINVAL;
+    if (c->eig_schedule == LETKF_EIG_CHEBYSHEV && c->k > lk::kChebMaxK) return LETKF_EINVAL;
     if (c->chunk_bytes < 0) return LETKF_EINVAL;
     const int V = popcount3(c->obs_vars);
     for (int l = 0; l < c->n_obs; ++l) {
@@ -175,7 +177,8 @@ int make_plan(const letkf_config *c, Plan *p) {
     // (d, e), reflector scalars and the hand-off list: every schedule but FUSED; the rotation
     // record: the split schedules (and AUTO, which may pick one)
     const bool split = p->eig_schedule != LETKF_EIG_FUSED;
-    const bool record = split && p->eig_schedule != LETKF_EIG_RATIONAL;
+    const bool record = split && p->eig_schedule != LETKF_EIG_RATIONAL &&
+                        p->eig_schedule != LETKF_EIG_CHEBYSHEV;
     p->rcap = !record ? 0
               : p->eig_schedule == LETKF_EIG_SPLIT_CHECK ? c->k : c->k * c->k + 4 * c->k;
     p->off_de = take(split ? p->chunk_pts * c->k * sizeof(float2) : 0);
@@ -183,6 +186,10 @@ int make_plan(const letkf_config *c, Plan *p) {
     p->off_rot = take(record ? p->chunk_pts * (size_t)p->rcap * sizeof(float2) : 0);
     p->off_nrot = take(record ? p->chunk_pts * sizeof(int) : 0);
     p->off_list = take(split ? (p->chunk_pts + 4) * sizeof(int) : 0);
+    // the Chebyshev transform's hand-off list (CHEBYSHEV, and AUTO where it is a candidate)
+    const bool cheb = (p->eig_schedule == LETKF_EIG_CHEBYSHEV ||
+                       p->eig_schedule == LETKF_EIG_AUTO) && c->k <= lk::kChebMaxK;
+    p->off_pre_list = take(cheb ? (p->chunk_pts + 4) * sizeof(int) : 0);
     p->off_status = take(kAlign);
     p->total = align_up(off, kAlign);
     return LETKF_OK;
@@ -219,6 +226,7 @@ struct letkf_handle {
     lk::EigSplit eig_split;
     int eig_schedule = LETKF_EIG_FUSED;  // resolved: FUSED, SPLIT, SPLIT_CHECK or RATIONAL
     int rat_grid = 0;                    // resident grid of the EVD-free transform kernel
+    int cheb_grid = 0;                   // resident grid of the Chebyshev transform kernel
     int tc_ctas = 0;
     letkf_stats stats;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -387,6 +395,13 @@ int enqueue_gram_chunk(letkf_handle *h, int chunk, int y0, int y1) {
     return LETKF_OK;
 }
 
+// The handle's status block (kAlign bytes, zeroed at letkf_init): word 0 the latched status
+// bits, words 16..18 the grouped launches' work counters, bytes 128..151 the Chebyshev
+// transform's cumulative counts (points, products, points handed on).
+unsigned long long *work_counters(letkf_handle *h) {
+    return reinterpret_cast<unsigned long long *>(h->status + 32);
+}
+
 lk::EigArgs eig_args(letkf_handle *h, int y0, int y1) {
     const int k = h->cfg.k;
     lk::EigArgs e;
@@ -404,13 +419,20 @@ lk::EigArgs eig_args(letkf_handle *h, int y0, int y1) {
     e.max_blocks = h->eig_blocks;
     e.refine = h->cfg.precision == LETKF_MIXED ? 1 : 0;  // FP64 sweep over clustered eigenpairs
     e.refine_tau = 1e-6f;
+    e.work = work_counters(h);
     return e;
 }
 
-// The EVD-free schedule serves k <= kRationalMaxK; AUTO considers it there.
+// The EVD-free schedules serve k <= 64; AUTO considers them there.  The Chebyshev schedule
+// hands the points beyond its approximations to the rational one, which it therefore needs.
 bool rational_candidate(int schedule, int k) {
-    return (schedule == LETKF_EIG_RATIONAL || schedule == LETKF_EIG_AUTO) &&
+    return (schedule == LETKF_EIG_RATIONAL || schedule == LETKF_EIG_CHEBYSHEV ||
+            schedule == LETKF_EIG_AUTO) &&
            k <= lk::kRationalMaxK;
+}
+bool cheb_candidate(int schedule, int k) {
+    return (schedule == LETKF_EIG_CHEBYSHEV || schedule == LETKF_EIG_AUTO) &&
+           k <= lk::kChebMaxK;
 }
 
 // The chunk's eigensolve, transform and update on the handle's resolved schedule.
@@ -423,6 +445,10 @@ cudaError_t launch_eig_schedule(letkf_handle *h, int schedule, lk::EigArgs e, cu
     if (schedule == LETKF_EIG_RATIONAL) {
         e.eigval = want_eigval ? h->eigval : nullptr;
         return lk::launch_eigen_rational(e, h->eig_split, h->rat_grid, s);
+    }
+    if (schedule == LETKF_EIG_CHEBYSHEV) {
+        e.eigval = want_eigval ? h->eigval : nullptr;
+        return lk::launch_eigen_chebyshev(e, h->eig_split, h->cheb_grid, h->rat_grid, s);
     }
     e.eigval = h->eigval;
     return lk::launch_eigen_split(e, h->eig_split, s, h->stream2, h->split_fork, h->split_join);
@@ -479,9 +505,11 @@ int tune_eig_schedule(letkf_handle *h, int y0, int y1) {
     CK(cudaStreamSynchronize(h->stream));
     CK(cudaMemcpy(&saved, h->status, sizeof(int), cudaMemcpyDeviceToHost));
     cudaEvent_t t0 = nullptr, t1 = nullptr;
-    const int cand[3] = {LETKF_EIG_FUSED, LETKF_EIG_SPLIT, LETKF_EIG_RATIONAL};
-    const int ncand = rational_candidate(LETKF_EIG_AUTO, k) ? 3 : 2;
-    float best[3] = {0.0f, 0.0f, 0.0f};
+    int cand[4] = {LETKF_EIG_FUSED, LETKF_EIG_SPLIT, 0, 0};
+    int ncand = 2;
+    if (rational_candidate(LETKF_EIG_AUTO, k)) cand[ncand++] = LETKF_EIG_RATIONAL;
+    if (cheb_candidate(LETKF_EIG_AUTO, k)) cand[ncand++] = LETKF_EIG_CHEBYSHEV;
+    float best[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     cudaError_t err = cudaEventCreate(&t0);
     if (err == cudaSuccess) err = cudaEventCreate(&t1);
     for (int sch = 0; sch < ncand && err == cudaSuccess; ++sch) {
@@ -852,6 +880,10 @@ int letkf_init(const letkf_config *cfg, void *workspace, size_t workspace_bytes,
         h->eig_split.nrot = plan.rcap > 0 ? (int *)(w + plan.off_nrot) : nullptr;
         h->eig_split.list = (int *)(w + plan.off_list);
         h->eig_split.list_count = h->eig_split.list + plan.chunk_pts;
+        if (cheb_candidate(plan.eig_schedule, cfg->k)) {
+            h->eig_split.pre_list = (int *)(w + plan.off_pre_list);
+            h->eig_split.pre_count = h->eig_split.pre_list + plan.chunk_pts;
+        }
         h->eig_split.rcap = plan.rcap;
     }
     h->status = (int *)(w + plan.off_status);
@@ -911,7 +943,9 @@ int letkf_init(const letkf_config *cfg, void *workspace, size_t workspace_bytes,
         (plan.eig_schedule != LETKF_EIG_FUSED &&
          lk::eigen_split_prepare(cfg->k, &h->eig_split) != cudaSuccess) ||
         (rational_candidate(plan.eig_schedule, cfg->k) &&
-         lk::eigen_rational_prepare(cfg->k, &h->rat_grid) != cudaSuccess))
+         lk::eigen_rational_prepare(cfg->k, &h->rat_grid) != cudaSuccess) ||
+        (cheb_candidate(plan.eig_schedule, cfg->k) &&
+         lk::eigen_cheb_prepare(cfg->k, &h->cheb_grid) != cudaSuccess))
         return fail(LETKF_ECUDA);
     if (plan.tensor_gram) {
         int sms = 0;
@@ -989,6 +1023,17 @@ int letkf_destroy(letkf_handle *h) {
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     if (dev >= 0 && dev != h->device) cudaSetDevice(dev);
     delete h;
+    return LETKF_OK;
+}
+
+int letkf_get_work_counts(letkf_handle *h, int64_t *counts) {
+    if (!h || !counts) return LETKF_EINVAL;
+    int rc = device_check(h);
+    if (rc) return rc;
+    unsigned long long c[3] = {0, 0, 0};
+    CK(cudaMemcpyAsync(c, work_counters(h), sizeof(c), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < 3; ++i) counts[i] = (int64_t)c[i];
     return LETKF_OK;
 }
 

@@ -1139,7 +1139,9 @@ __global__ void __launch_bounds__(32 * EigCfg<NC>::WARPS) eig_tridiag_kernel(Eig
     float *taus = reinterpret_cast<float *>(de + k);
     const int warps_per_block = blockDim.x >> 5;
     const int nw = gridDim.x * warps_per_block;
-    for (int lp = blockIdx.x * warps_per_block + wib; lp < a.npts; lp += nw) {
+    const int npts = a.list ? *a.list_count : a.npts;   // the chunk, or the listed points
+    for (int it = blockIdx.x * warps_per_block + wib; it < npts; it += nw) {
+        const int lp = a.list ? a.list[it] : it;
         if (a.nloc && a.nloc[lp] == 0) continue;
         float *Ag = a.gram + (size_t)lp * k * k;
         load_q<NC>(Ag, S, k, ld, lane, a.diag);
@@ -1215,7 +1217,9 @@ __global__ void __launch_bounds__(32 * kPairWarps, 5) eig_tridiag_pair_kernel(Ei
     float *betas = red + 16, *taus_s = betas + 64;
     const int bar = 1 + pair;
     const int npairs = gridDim.x * (kPairWarps / 2);
-    for (int lp = blockIdx.x * (kPairWarps / 2) + pair; lp < a.npts; lp += npairs) {
+    const int npts = a.list ? *a.list_count : a.npts;   // the chunk, or the listed points
+    for (int it = blockIdx.x * (kPairWarps / 2) + pair; it < npts; it += npairs) {
+        const int lp = a.list ? a.list[it] : it;
         if (a.nloc && a.nloc[lp] == 0) continue;   // the same decision for both warps
         float *Ag = a.gram + (size_t)lp * k * k;
         // ---- Q = diag + A, symmetrised from the upper triangle: warp h stages the row blocks
@@ -1966,12 +1970,17 @@ cudaError_t launch_rational_nc(const EigArgs &a, const EigSplit &sp, int grid, c
     const int warps = EigCfg<NC>::WARPS;
     cudaError_t e = cudaMemsetAsync(sp.list_count, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    launch_tri<NC>(a, sp, s);
+    EigArgs t = a;   // eigenvalues asked for: every point of the chunk is tridiagonalized
+    if (a.eigval) {
+        t.list = nullptr;
+        t.list_count = nullptr;
+    }
+    launch_tri<NC>(t, sp, s);
     if (a.eigval) {  // eigenvalues for a caller that asked for them: the QL without a record
         EigSplit v = sp;
         v.rot = nullptr;
         v.nrot = nullptr;
-        launch_ql(a, v, s);
+        launch_ql(t, v, s);
     }
     if ((e = launch_eigen_rational_transform(a, sp, grid, s)) != cudaSuccess) return e;
     EigArgs f = a;  // points beyond the approximations' range: the fused kernel
@@ -1989,6 +1998,23 @@ cudaError_t launch_eigen_rational(const EigArgs &a, const EigSplit &sp, int grid
         return cudaErrorInvalidValue;
     if (a.k <= 32) return launch_rational_nc<1>(a, sp, grid, s);
     if (a.k <= kRationalMaxK) return launch_rational_nc<2>(a, sp, grid, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_eigen_chebyshev(const EigArgs &a, const EigSplit &sp, int cheb_grid,
+                                   int rat_grid, cudaStream_t s) {
+    if (a.npts <= 0) return cudaSuccess;
+    if (!sp.de || !sp.taus || !sp.list || !sp.list_count || !sp.pre_list || !sp.pre_count ||
+        !a.x || !a.cvec || a.list)
+        return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(sp.pre_count, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = launch_eigen_cheb_transform(a, sp, cheb_grid, s);
+    if (e != cudaSuccess) return e;
+    EigArgs r = a;   // the points beyond the Chebyshev sets: the rational schedule
+    r.list = sp.pre_list;
+    r.list_count = sp.pre_count;
+    if (a.k <= 32) return launch_rational_nc<1>(r, sp, rat_grid, s);
+    if (a.k <= kChebMaxK) return launch_rational_nc<2>(r, sp, rat_grid, s);
     return cudaErrorInvalidValue;
 }
 

@@ -105,11 +105,13 @@ struct EigArgs {
     float *eigval = nullptr;        // [npts][k] eigenvalues; optional for the fused schedule
     int *status = nullptr;          // device status word
     int max_blocks = 0;             // resident grid of the fused kernel (eigen_prepare)
-    const int *list = nullptr;      // fused kernel: only these points (count in *list_count)
-    const int *list_count = nullptr;
+    const int *list = nullptr;      // only these points (count in *list_count): the fused
+    const int *list_count = nullptr;  // kernel, the tridiagonalizations, the rational transform
     float *evec = nullptr;          // optional [npts][k][k]: row i = eigenvector of eigval[i]
     int refine = 0;                 // FP64 refinement sweep of clustered eigenpairs
     float refine_tau = 0.0f;        // relative eigenvalue distance that makes a cluster
+    unsigned long long *work = nullptr;  // optional [3] counters added to by the Chebyshev
+                                         // transform: points, products, points handed on
 };
 // Split schedule: scratch of one chunk and the resident grids of its kernels.
 struct EigSplit {
@@ -119,6 +121,8 @@ struct EigSplit {
     int *nrot = nullptr;            // [npts] record length, -1: handed to the fused kernel
     int *list = nullptr;            // [npts] points handed to the fused kernel
     int *list_count = nullptr;      // [1]
+    int *pre_list = nullptr;        // [npts] points the Chebyshev transform hands to the
+    int *pre_count = nullptr;       // [1]    rational schedule
     int list_offset = 0;            // added to a point's index when it is listed
     int rcap = 0;                   // record capacity per point (entries)
     int grid_tri = 0, grid_vec = 0; // resident grids (eigen_split_prepare)
@@ -160,6 +164,29 @@ cudaError_t launch_eigen_rational_transform(const EigArgs &a, const EigSplit &sp
 // list_count (no rotation record)
 cudaError_t launch_eigen_rational(const EigArgs &a, const EigSplit &sp, int grid,
                                   cudaStream_t s);
+
+// EVD-free transform by Chebyshev expansions of t^-1/2 and t^-1 on [1, kappa_max]
+// (LETKF_EIG_CHEBYSHEV, k <= kChebMaxK): coefficients of T_j in s = (2t - kappa_max - 1) /
+// (kappa_max - 1), FP32 copies of the FP64 interpolants, the first set that covers a point's
+// condition bound is used.
+constexpr int kChebSets = 12;
+constexpr int kChebMaxDeg = 36;
+constexpr int kChebMaxK = 64;
+struct ChebTable {
+    float kappa_max[kChebSets];
+    int n[kChebSets];                        // degree
+    float2 c[kChebSets][kChebMaxDeg + 1];    // (t^-1/2, t^-1) coefficients of T_0 .. T_n
+};
+const ChebTable &cheb_table();              // computed once per process (chebyshev.cu)
+double chebyshev_coefficients(double kappa, int n, double *ca, double *cb);
+cudaError_t eigen_cheb_prepare(int k, int *grid);
+// the Chebyshev transform alone; points beyond the last set go to sp.pre_list
+cudaError_t launch_eigen_cheb_transform(const EigArgs &a, const EigSplit &sp, int grid,
+                                        cudaStream_t s);
+// the whole schedule: the Chebyshev transform, then the rational schedule over the points it
+// handed on (sp needs de, taus, list, list_count, pre_list and pre_count)
+cudaError_t launch_eigen_chebyshev(const EigArgs &a, const EigSplit &sp, int cheb_grid,
+                                   int rat_grid, cudaStream_t s);
 
 cudaError_t eigen_prepare(int k, int *max_blocks);  // once per process and k
 cudaError_t eigen_split_prepare(int k, EigSplit *sp);

@@ -226,11 +226,13 @@ __global__ void __launch_bounds__(32 * kWarpsR) eig_rational_kernel(EigArgs a, E
     // staging slots: rows at and beyond k (and every row before its first use) hold zeros
     for (int i = lane; i < 2 * kPts * S::VS; i += 32) vbuf[i] = 0.0f;
     __syncwarp();
-    const long long ntask = ((long long)a.npts + kPts - 1) / kPts;
+    const long long npts = a.list ? *a.list_count : a.npts;   // the chunk, or the listed points
+    const long long ntask = (npts + kPts - 1) / kPts;
     const long long nw = (long long)gridDim.x * kWarpsR;
     for (long long task = (long long)blockIdx.x * kWarpsR + wib; task < ntask; task += nw) {
-        const long long lp = task * kPts + pg;
-        const bool valid = pg < kPts && lp < a.npts;
+        const long long it = task * kPts + pg;
+        const bool valid = pg < kPts && it < npts;
+        const long long lp = valid ? (a.list ? a.list[it] : it) : 0;
         const bool observed = valid && (!a.nloc || a.nloc[lp] != 0);
         float *X = valid ? a.x + (size_t)(a.pt0 + lp) * NV * k : nullptr;
         // ---- rows: perturbations of the nine populations, and c

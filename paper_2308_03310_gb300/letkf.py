@@ -41,6 +41,7 @@ LETKF_EIG_FUSED = 1
 LETKF_EIG_SPLIT = 2
 LETKF_EIG_SPLIT_CHECK = 3
 LETKF_EIG_RATIONAL = 4
+LETKF_EIG_CHEBYSHEV = 5
 
 # Every symbol include/letkf.h declares, in declaration order.
 EXPORTED = (
@@ -51,6 +52,7 @@ EXPORTED = (
     "letkf_local_analysis_noalloc", "letkf_eigh_batch", "letkf_eigh_workspace_bytes",
     "letkf_eigh_batch_ws", "letkf_group_analyze", "letkf_group_cycle",
     "letkf_fp32_peak_grid", "letkf_fp32_peak_run", "letkf_rational_coefficients",
+    "letkf_chebyshev_coefficients", "letkf_get_work_counts",
 )
 
 LETKF_NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -142,6 +144,10 @@ def load(path: str = LIB):
         "letkf_rational_coefficients": (C.c_double, [C.c_double, C.c_int32,
                                                      C.POINTER(C.c_double),
                                                      C.POINTER(C.c_double)]),
+        "letkf_chebyshev_coefficients": (C.c_double, [C.c_double, C.c_int32,
+                                                      C.POINTER(C.c_double),
+                                                      C.POINTER(C.c_double)]),
+        "letkf_get_work_counts": (C.c_int, [P, C.POINTER(C.c_int64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -299,6 +305,17 @@ def letkf_rational_coefficients(kappa_max, n):
     return np.array(p[:]), np.array(r[:]), float(err)
 
 
+def letkf_chebyshev_coefficients(kappa_max, n):
+    """(c_rsqrt, c_inv, max relative error): the library's degree-n Chebyshev interpolants of
+    t^-1/2 and t^-1 on [1, kappa_max] (host computation, no GPU needed)."""
+    a = (C.c_double * (int(n) + 1))()
+    b = (C.c_double * (int(n) + 1))()
+    err = load().letkf_chebyshev_coefficients(float(kappa_max), int(n), a, b)
+    if err < 0:
+        raise LetkfError(LETKF_EINVAL, "letkf_chebyshev_coefficients")
+    return np.array(a[:]), np.array(b[:]), float(err)
+
+
 def _group_arrays(exps, yos):
     hs = (C.c_void_p * len(exps))(*[e.h for e in exps])
     wheres, ptrs, keep = set(), [], []
@@ -416,6 +433,12 @@ class Experiment:
 
     def stats(self) -> letkf_stats:
         return letkf_get_stats(self.h)
+
+    def work_counts(self) -> dict:
+        """Cumulative counts of the Chebyshev transform (waits for the handle's stream)."""
+        c = (C.c_int64 * 3)()
+        _check(load().letkf_get_work_counts(self.h, c), "letkf_get_work_counts")
+        return {"cheb_points": c[0], "cheb_products": c[1], "cheb_handed_on": c[2]}
 
     def enable_timing(self, on=True):
         letkf_enable_timing(self.h, on)

@@ -174,3 +174,32 @@ def test_rational_coefficients_reject_bad_arguments(lib):
     for kappa, n in [(1.0, 8), (1e13, 8), (100.0, 0), (100.0, 17)]:
         with pytest.raises(L.LetkfError):
             L.letkf_rational_coefficients(kappa, n)
+
+
+@pytest.mark.parametrize("kappa,n,bound", [(1.1, 4, 2e-8), (2.0, 10, 2e-8), (16.0, 36, 2e-8),
+                                           (3.0, 6, 1e-3)])
+def test_chebyshev_coefficients_interpolate_rsqrt_and_inverse(lib, kappa, n, bound):
+    # The Chebyshev schedule's coefficients (host code in the library): the degree-n
+    # interpolants of t^-1/2 and t^-1 on [1, kappa] at the first-kind Chebyshev points, in
+    # s = (2t - kappa - 1) / (kappa - 1).  Checked against numpy's chebinterpolate (the same
+    # definition, an independent implementation) and against the error measured here.
+    cheb = np.polynomial.chebyshev
+    ca, cb, err = L.letkf_chebyshev_coefficients(kappa, n)
+    t_of = lambda s: 1.0 + 0.5 * (s + 1.0) * (kappa - 1.0)
+    ra = cheb.chebinterpolate(lambda s: t_of(s) ** -0.5, n)
+    rb = cheb.chebinterpolate(lambda s: 1.0 / t_of(s), n)
+    assert np.allclose(ca, ra, rtol=0, atol=1e-13) and np.allclose(cb, rb, rtol=0, atol=1e-13)
+    t = np.linspace(1.0, kappa, 200001)
+    s = (2 * t - kappa - 1) / (kappa - 1)
+    measured = max(np.abs(cheb.chebval(s, ca) * np.sqrt(t) - 1).max(),
+                   np.abs(cheb.chebval(s, cb) * t - 1).max())
+    assert measured < bound and abs(measured - err) < 0.05 * measured + 1e-15
+    # the degrees the schedule uses are the smallest that reach 2e-8
+    if bound == 2e-8:
+        assert L.letkf_chebyshev_coefficients(kappa, n - 1)[2] > 2e-8
+
+
+def test_chebyshev_coefficients_reject_bad_arguments(lib):
+    for kappa, n in [(1.0, 8), (1e7, 8), (2.0, 0), (2.0, 257)]:
+        with pytest.raises(L.LetkfError):
+            L.letkf_chebyshev_coefficients(kappa, n)

@@ -6,7 +6,8 @@ back-transform and update (warp per point) as three launches; SPLIT_CHECK is SPL
 rotation record of one sweep, so that nearly every point is handed back to the fused kernel,
 which recomputes it from the Gram matrix the split kernels left intact; RATIONAL (k <= 64)
 forms no eigenvectors (tridiagonal solves and a rational approximation of Q^-1/2), its
-probe eigenvalues come from an eigenvalue-only QL.  All of them must meet
+probe eigenvalues come from an eigenvalue-only QL; CHEBYSHEV (k <= 64) applies polynomial
+approximations of Q^-1/2 and Q^-1, passing ill-conditioned points to RATIONAL.  All of them must meet
 the analysis bar (1e-5 relative L2 on mean, mean increment and perturbations) and SPLIT must
 agree with FUSED to within FP32 rounding of the two summation orders.
 """
@@ -21,7 +22,9 @@ from tests import _cases as C
 pytestmark = pytest.mark.gpu
 
 UV = L.LETKF_OBS_U | L.LETKF_OBS_V
-SCHEDULES = [L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT, L.LETKF_EIG_SPLIT_CHECK, L.LETKF_EIG_RATIONAL]
+SCHEDULES = [L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT, L.LETKF_EIG_SPLIT_CHECK, L.LETKF_EIG_RATIONAL,
+             L.LETKF_EIG_CHEBYSHEV]
+EVD_FREE = (L.LETKF_EIG_RATIONAL, L.LETKF_EIG_CHEBYSHEV)   # k <= 64
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -60,7 +63,7 @@ def _run(k, nx, ny, stride, radius, seed, schedule, precision=L.LETKF_FP32):
 def test_schedules_match_oracle_and_each_other(k, nx, ny, stride, radius):
     outs = {}
     for sch in SCHEDULES:
-        if sch == L.LETKF_EIG_RATIONAL and k > 64:
+        if sch in EVD_FREE and k > 64:
             continue
         f0, yo, net, var, dev, lam, pts = _run(k, nx, ny, stride, radius, 900 + k, sch)
         outs[sch] = (dev, lam)
@@ -155,7 +158,7 @@ def test_auto_schedule_resolves_at_the_first_analysis_once_per_process():
     assert exp.stats().eig_schedule == L.LETKF_EIG_AUTO         # unresolved before analysing
     exp.analyze(yo)
     pick = exp.stats().eig_schedule
-    assert pick in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT, L.LETKF_EIG_RATIONAL)
+    assert pick in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT) + EVD_FREE
     got = exp.get_deviation()
     assert exp.sync() == 0
     # the timed runs worked on scratch: the analysis is the picked schedule's, bit for bit
@@ -174,7 +177,7 @@ def test_auto_schedule_first_cycle_runs_eagerly_then_captures():
     a.cycle(3, yo)
     assert a.stats().cycle_kernels == 0                        # eager: no graph yet
     pick = a.stats().eig_schedule
-    assert pick in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT, L.LETKF_EIG_RATIONAL)
+    assert pick in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT) + EVD_FREE
     b, _ = _auto_case(45, pick, 975)
     b.cycle(3, yo)
     for _ in range(2):
@@ -190,8 +193,8 @@ def test_auto_schedule_first_cycle_runs_eagerly_then_captures():
 def test_handles_of_different_k_coexist(k_big, k_small):
     # the kernels' shared-memory caps are process-wide: a later handle with a smaller k
     # must not lower them under an earlier handle with a larger k
-    for sch in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT, L.LETKF_EIG_RATIONAL):
-        if sch == L.LETKF_EIG_RATIONAL and k_big > 64:
+    for sch in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT) + EVD_FREE:
+        if sch in EVD_FREE and k_big > 64:
             continue
         first = _run(k_big, 10, 10, 2, 2.0, 980 + k_big, sch)          # builds handle 1
         nx = ny = 10

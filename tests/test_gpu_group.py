@@ -62,19 +62,22 @@ def _ensembles(precision, schedules=(L.LETKF_EIG_AUTO,) * 4, nx=NX, ny=NY):
 MIX = (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT, L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT)
 # the EVD-free schedule serves k <= 64
 RAT = (L.LETKF_EIG_RATIONAL, L.LETKF_EIG_RATIONAL, L.LETKF_EIG_RATIONAL, L.LETKF_EIG_FUSED)
+CHEB = (L.LETKF_EIG_CHEBYSHEV, L.LETKF_EIG_CHEBYSHEV, L.LETKF_EIG_CHEBYSHEV, L.LETKF_EIG_FUSED)
 
 
 @pytest.mark.parametrize("precision", [L.LETKF_FP32, L.LETKF_MIXED])
-@pytest.mark.parametrize("schedule", ["fused", "split", "mix", "rational", "auto"])
+@pytest.mark.parametrize("schedule", ["fused", "split", "mix", "rational", "chebyshev", "auto"])
 def test_group_analysis_equals_each_alone_analysis(precision, schedule):
     scheds = {"fused": (L.LETKF_EIG_FUSED,) * 4, "split": (L.LETKF_EIG_SPLIT,) * 4,
-              "mix": MIX, "rational": RAT, "auto": (L.LETKF_EIG_AUTO,) * 4}[schedule]
+              "mix": MIX, "rational": RAT, "chebyshev": CHEB,
+              "auto": (L.LETKF_EIG_AUTO,) * 4}[schedule]
     grouped, f0s, yos = _ensembles(precision, scheds)
     st = grouped[0].stats()
     assert 0.15 < st.n_zero_obs / st.n_points < 0.5          # a share of points sees nothing
     L.letkf_group_analyze(grouped, yos)
     picked = tuple(e.stats().eig_schedule for e in grouped)
-    assert all(p in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT, L.LETKF_EIG_RATIONAL)
+    assert all(p in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT, L.LETKF_EIG_RATIONAL,
+                     L.LETKF_EIG_CHEBYSHEV)
                for p in picked)
     if schedule != "auto":
         assert picked == scheds
@@ -105,7 +108,7 @@ def _oracle_sample_points(net, n=32, seed=1600):
 
 
 @pytest.mark.parametrize("precision", [L.LETKF_FP32, L.LETKF_MIXED])
-@pytest.mark.parametrize("schedule", ["fused", "mix", "rational"])
+@pytest.mark.parametrize("schedule", ["fused", "mix", "rational", "chebyshev"])
 def test_group_analysis_matches_oracle_at_sampled_points(precision, schedule):
     # The grouped analysis (the persistent launch over all fused-schedule ensembles, split
     # kernels for the others) of the k = 16/32/64/128 ensembles on the clustered network,
@@ -113,7 +116,8 @@ def test_group_analysis_matches_oracle_at_sampled_points(precision, schedule):
     # densest points, at points without observations and at random points, to the parity
     # tests' 1e-5 relative L2 on the mean, the mean increment and the perturbations.
     from oracle import lbm, obs as oobs
-    scheds = {"fused": (L.LETKF_EIG_FUSED,) * 4, "mix": MIX, "rational": RAT}[schedule]
+    scheds = {"fused": (L.LETKF_EIG_FUSED,) * 4, "mix": MIX, "rational": RAT,
+              "chebyshev": CHEB}[schedule]
     grouped, f0s, yos = _ensembles(precision, scheds)
     L.letkf_group_analyze(grouped, yos)
     net = _network()
@@ -191,7 +195,8 @@ def test_group_cycle_with_auto_handles_picks_then_captures():
     L.letkf_group_cycle(a, 3, yos)
     assert a[0].stats().cycle_kernels == 0
     picked = tuple(e.stats().eig_schedule for e in a)
-    assert all(p in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT, L.LETKF_EIG_RATIONAL)
+    assert all(p in (L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT, L.LETKF_EIG_RATIONAL,
+                     L.LETKF_EIG_CHEBYSHEV)
                for p in picked)
     b, _, _ = _ensembles(L.LETKF_FP32, picked, nx=46, ny=46)
     L.letkf_group_cycle(b, 3, yos)

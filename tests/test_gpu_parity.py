@@ -231,7 +231,7 @@ def test_analysis_edge_cases_match_oracle(k, nx, ny, stride, radius, obs_vars, i
 
 @pytest.mark.parametrize("k", [8, 48])
 @pytest.mark.parametrize("schedule", [L.LETKF_EIG_FUSED, L.LETKF_EIG_SPLIT,
-                                      L.LETKF_EIG_RATIONAL])
+                                      L.LETKF_EIG_RATIONAL, L.LETKF_EIG_CHEBYSHEV])
 def test_inflation_at_points_without_local_observations_matches_oracle(k, schedule):
     # with inflation rho a point without local observations keeps its mean and has its
     # perturbations scaled by sqrt(rho); observed points follow the inflated Q
