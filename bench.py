@@ -785,6 +785,8 @@ def main(argv=None):
         "lbm": head["lbm"],
         "clocks": head["clocks"],
         "local_obs": head["local_obs"],
+        **({"chebyshev_per_cycle": head["chebyshev_per_cycle"]}
+           if "chebyshev_per_cycle" in head else {}),
         "rmse_vs_truth": rmse,
         "mixed": None,
     }

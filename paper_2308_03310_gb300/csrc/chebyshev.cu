@@ -22,10 +22,11 @@
 // 1.1, 10 for 2, 36 for 16); a point beyond the last approximation goes to the rational
 // schedule (tridiagonalization and Zolotarev's approximation) through a list.
 //
-// Layout: one warp per grid point.  Lane l holds columns l and l + 32 of A in registers, staged
-// from the upper triangle of the Gram slot through shared memory (written symmetric).  A
-// product R A reads the rows as 16-byte broadcasts from shared memory: for k <= 64 five rows
-// per pass (5 loads for 40 multiply-adds), for k <= 32 all ten.
+// Layout: one warp per grid point.  Lane l holds columns l and l + 32 of A in registers, loaded
+// from the upper triangle of the Gram slot (the rows above the diagonal coalesced, the lane's
+// own row beyond it) with every load in flight at once.  A product R A reads the rows as
+// 16-byte broadcasts from shared memory: for k <= 64 five rows per pass (5 loads for 40
+// multiply-adds), for k <= 32 all ten.
 #include <math.h>
 
 #include <mutex>
@@ -121,8 +122,7 @@ struct ChebShape {
     static constexpr int NP = kRowsC / RP;         // passes per product
     static constexpr int BUF = kRowsC * KM;        // one row buffer [10][KM]
     static constexpr int off_xb = 3 * BUF;         // the rows' means [9]
-    static constexpr int stage = KM * (KM + 1);    // A staged symmetric, leading dimension k + 1
-    static constexpr int floats = ((stage > off_xb + 16 ? stage : off_xb + 16) + 3) & ~3;
+    static constexpr int floats = off_xb + 16;
 };
 
 __device__ __forceinline__ float warp_max_c(float v) {
@@ -132,7 +132,7 @@ __device__ __forceinline__ float warp_max_c(float v) {
 }
 
 template <int KM>
-__global__ void __launch_bounds__(32 * kWarpsC, KM == 64 ? 2 : 4)
+__global__ void __launch_bounds__(32 * kWarpsC, KM == 64 ? 2 : 3)
     eig_cheb_kernel(EigArgs a, EigSplit sp, const __grid_constant__ ChebTable ct) {
     using S = ChebShape<KM>;
     constexpr int NS = S::NS, RP = S::RP, BUF = S::BUF;
@@ -167,41 +167,49 @@ __global__ void __launch_bounds__(32 * kWarpsC, KM == 64 ? 2 : 4)
                 }
             continue;
         }
-        // ---- A, symmetric, from the upper triangle of the Gram slot: eight rows at a time
-        // with coalesced loads into shared memory, then every lane reads its columns
+        // ---- A, symmetric, from the upper triangle of the Gram slot straight into registers,
+        // every load of the point in flight at once: lane c takes A[i][c] for i <= c from the
+        // rows i (coalesced across the lanes) and A[c][i] = A[i][c] for i > c from its own row
         const float *Ag = a.gram + (size_t)lp * k * k;
-        const int ld = k + 1;
-        for (int i0 = 0; i0 < k; i0 += 8) {
-            float v[8][NS];
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-#pragma unroll
-                for (int q = 0; q < NS; ++q) {
-                    const int i = i0 + u, j = lane + 32 * q;
-                    v[u][q] = (i < k && j < k && j >= i) ? __ldcg(Ag + i * k + j) : 0.0f;
-                }
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-#pragma unroll
-                for (int q = 0; q < NS; ++q) {
-                    const int i = i0 + u, j = lane + 32 * q;
-                    if (i < k && j < k && j >= i) {
-                        ws[i * ld + j] = v[u][q];
-                        ws[j * ld + i] = v[u][q];
-                    }
-                }
-        }
-        __syncwarp();
         float A[NS][KM];
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            const int c = lane + 32 * q;
+#pragma unroll
+            for (int i = 0; i < KM; ++i)
+                A[q][i] = (i < k && c < k && i <= c) ? __ldg(Ag + i * k + c) : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            const int c = lane + 32 * q;
+            if (c >= k) continue;
+            const float *row = Ag + (size_t)c * k;
+            if ((k & 3) == 0) {   // 16-byte loads: the row starts on a 16-byte boundary
+#pragma unroll
+                for (int g = 0; g < KM / 4; ++g)
+                    if (4 * g + 3 > c && 4 * g < k) {
+                        const float4 v = __ldg(reinterpret_cast<const float4 *>(row) + g);
+                        if (4 * g > c) A[q][4 * g] = v.x;
+                        if (4 * g + 1 > c) A[q][4 * g + 1] = v.y;
+                        if (4 * g + 2 > c) A[q][4 * g + 2] = v.z;
+                        A[q][4 * g + 3] = v.w;
+                    }
+            } else {
+#pragma unroll
+                for (int i = 0; i < KM; ++i)
+                    if (i > c && i < k) A[q][i] = __ldg(row + i);
+            }
+        }
+        // the forecast rows and c, loaded beside A and parked in R0 (each lane its columns)
         float dg = 0.0f;
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
             const int c = lane + 32 * q;
 #pragma unroll
-            for (int i = 0; i < KM; ++i) A[q][i] = (i < k && c < k) ? ws[i * ld + c] : 0.0f;
-            if (c < k) dg += ws[c * ld + c];
+            for (int r = 0; r < NV; ++r) R0[r * KM + c] = c < k ? __ldcg(X + r * k + c) : 0.0f;
+            R0[NV * KM + c] = c < k ? __ldcg(a.cvec + (size_t)lp * k + c) : 0.0f;
+            if (c < k) dg += __ldg(Ag + (size_t)c * k + c);
         }
-        __syncwarp();   // the staging area becomes the row buffers
         // ---- kappa >= 1 + lambda_max(A) / d from min(Gershgorin, Frobenius, trace)
         float gm = 0.0f, f2 = 0.0f;
 #pragma unroll
@@ -227,28 +235,20 @@ __global__ void __launch_bounds__(32 * kWarpsC, KM == 64 ? 2 : 4)
             ++n_hand;
             continue;
         }
-        // ---- R = [dX; c^T] into R0; the means of the nine rows
+        // ---- R = [dX; c^T] in R0: the nine rows less their means
         float *Bc = ws + BUF, *Bp = ws + 2 * BUF;
-        for (int r = 0; r < NV; ++r) {
-            float v[NS], s = 0.0f;
 #pragma unroll
-            for (int q = 0; q < NS; ++q) {
-                const int c = lane + 32 * q;
-                v[q] = c < k ? __ldcg(X + r * k + c) : 0.0f;
-                s += v[q];
-            }
+        for (int r = 0; r < NV; ++r) {
+            float s = 0.0f;
+#pragma unroll
+            for (int q = 0; q < NS; ++q) s += R0[r * KM + lane + 32 * q];
             const float xb = warp_sum(s) / (float)k;
             if (lane == 0) xbs[r] = xb;
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
                 const int c = lane + 32 * q;
-                R0[r * KM + c] = c < k ? v[q] - xb : 0.0f;
+                if (c < k) R0[r * KM + c] -= xb;
             }
-        }
-#pragma unroll
-        for (int q = 0; q < NS; ++q) {
-            const int c = lane + 32 * q;
-            R0[NV * KM + c] = c < k ? __ldcg(a.cvec + (size_t)lp * k + c) : 0.0f;
         }
         // ---- Clenshaw: b_n = c_n R, b_j = c_j R + 2 b_{j+1} Z - b_{j+2}, result
         // c_0 R + b_1 Z - b_2, with b_{j+1} Z = gamma b_{j+1} A - b_{j+1}.  Bc holds b_{j+1},
