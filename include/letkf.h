@@ -65,8 +65,8 @@ extern "C" {
 
 /* Eigensolve schedules (same results up to rounding; see letkf_config.eig_schedule). */
 #define LETKF_EIG_AUTO        0  /* the handle picks one: at its first analysis the schedules
-                                    (FUSED, SPLIT and, for k <= 64, RATIONAL and CHEBYSHEV)
-                                    are timed on
+                                    (FUSED, SPLIT and, for k <= 64, CHEBYSHEV, which passes its
+                                    ill-conditioned points to RATIONAL) are timed on
                                     that analysis' first chunk of Gram matrices
                                     (applied to a scratch copy of the forecast, so the analysis
                                     itself is unaffected; one host synchronisation), and the
@@ -96,8 +96,10 @@ extern "C" {
                                     interpolants on [1, kappa_max] (relative error < 2e-8,
                                     degree 4 at kappa_max = 1.1 up to 36 at 16) and applied to
                                     [dX; c^T] by Clenshaw's recurrence, one product with A per
-                                    degree.  No factorization or tridiagonalization; a point
-                                    whose bound exceeds 16 is passed to the RATIONAL schedule.
+                                    degree.  No factorization or tridiagonalization.  Degrees
+                                    up to 9k/16 are used (kappa_max 16 at k = 64, 4 at k = 32),
+                                    about where a product costs as much as the RATIONAL
+                                    schedule; a point beyond is passed to RATIONAL.
                                     Pays where Q is well conditioned (ensemble spread small
                                     against the observation error).  A probe's eigenvalues come
                                     from a tridiagonalization and an eigenvalue-only QL.      */

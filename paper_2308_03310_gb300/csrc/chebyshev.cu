@@ -29,6 +29,7 @@
 // multiply-adds), for k <= 32 all ten.
 #include <math.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -107,6 +108,19 @@ const ChebTable &cheb_table() {
     return t;
 }
 
+// The largest set the transform uses for ensemble size k: degrees up to 9k/16 (at least 4).
+// A product with A costs ~20 k^2 flops, the rational schedule's tridiagonalization and
+// transform ~(4/3) k^3 + 40 k^2 at a lower issue efficiency; at k = 64 the two measured equal
+// near degree 36, and the break-even degree scales with k.  Points beyond go to the rational
+// schedule, so the Chebyshev schedule never costs much more than the rational one.
+int cheb_max_set(int k) {
+    const ChebTable &t = cheb_table();
+    const int nmax = std::max(4, 9 * k / 16);
+    int s = 0;
+    while (s + 1 < kChebSets && t.n[s + 1] <= nmax) ++s;
+    return s;
+}
+
 // ---- the transform kernel ---------------------------------------------------------------
 
 namespace {
@@ -133,7 +147,7 @@ __device__ __forceinline__ float warp_max_c(float v) {
 
 template <int KM>
 __global__ void __launch_bounds__(32 * kWarpsC, KM == 64 ? 2 : 3)
-    eig_cheb_kernel(EigArgs a, EigSplit sp, const __grid_constant__ ChebTable ct) {
+    eig_cheb_kernel(EigArgs a, EigSplit sp, const __grid_constant__ ChebTable ct, int max_set) {
     using S = ChebShape<KM>;
     constexpr int NS = S::NS, RP = S::RP, BUF = S::BUF;
     extern __shared__ float4 smem_c4[];
@@ -228,9 +242,9 @@ __global__ void __launch_bounds__(32 * kWarpsC, KM == 64 ? 2 : 3)
         const float e = fmaxf(fminf(gm, fminf(sqrtf(f2), dg)), 0.0f);
         const float kap = fmaf(e * inv_d, 1.0001f, 1.000001f);   // rounding margin
         int set = -1;
-        for (int s = kChebSets - 1; s >= 0; --s)
+        for (int s = max_set; s >= 0; --s)
             if (kap <= ct.kappa_max[s]) set = s;
-        if (set < 0) {   // beyond the last approximation (or not finite): the rational schedule
+        if (set < 0) {   // beyond the sets in use (or not finite): the rational schedule
             if (lane == 0) sp.pre_list[atomicAdd(sp.pre_count, 1)] = (int)lp;
             ++n_hand;
             continue;
@@ -369,8 +383,9 @@ cudaError_t cheb_launch_km(const EigArgs &a, const EigSplit &sp, int grid, cudaS
     using S = ChebShape<KM>;
     const long long need = ((long long)a.npts + kWarpsC - 1) / kWarpsC;
     const unsigned blocks = (unsigned)(need < grid ? need : grid);
+    const ChebTable &t = cheb_table();
     eig_cheb_kernel<KM><<<blocks, 32 * kWarpsC, (size_t)S::floats * sizeof(float) * kWarpsC,
-                          s>>>(a, sp, cheb_table());
+                          s>>>(a, sp, t, cheb_max_set(a.k));
     return cudaGetLastError();
 }
 

@@ -178,6 +178,7 @@ struct ChebTable {
     float2 c[kChebSets][kChebMaxDeg + 1];    // (t^-1/2, t^-1) coefficients of T_0 .. T_n
 };
 const ChebTable &cheb_table();              // computed once per process (chebyshev.cu)
+int cheb_max_set(int k);                    // the largest set used at ensemble size k
 double chebyshev_coefficients(double kappa, int n, double *ca, double *cb);
 cudaError_t eigen_cheb_prepare(int k, int *grid);
 // the Chebyshev transform alone; points beyond the last set go to sp.pre_list
