@@ -46,6 +46,8 @@ struct GramShape {
     static constexpr int TH = P / TW;
     static constexpr int NT = (P * T + 31) / 32 * 32;   // threads per CTA, whole warps (two
                                                         // CTAs resident per SM)
+    // registers per thread that keep two CTAs resident (multiples of 8, at most 255)
+    static constexpr int REG = (65536 / (2 * NT)) / 8 * 8 > 255 ? 255 : (65536 / (2 * NT)) / 8 * 8;
     static_assert(TW * TH == P, "tile");
 };
 
@@ -63,7 +65,7 @@ __device__ __forceinline__ void upper_block(int r, int &ti, int &tj) {
 
 // VV: observed variables per point (1..3), a template parameter so the per-scalar loop unrolls
 template <int KP, int VV>
-__global__ void __launch_bounds__(GramShape<KP>::NT, 2) gram_kernel(GramArgs a) {
+__global__ void __maxnreg__(GramShape<KP>::REG) gram_kernel(GramArgs a) {
     using S = GramShape<KP>;
     constexpr int KB = S::KB, T = S::T, P = S::P, TW = S::TW, TH = S::TH, NT = S::NT;
     constexpr int V = VV;
@@ -97,14 +99,15 @@ __global__ void __launch_bounds__(GramShape<KP>::NT, 2) gram_kernel(GramArgs a) 
     const bool valid = p < P && px < a.nx && py < a.y_end;
     const bool diag_block = ti == tj;
 
-    float acc[8][8];
-    float cacc[8];
+    float2 acc[8][4];    // acc[i][jp] = (A[i][2 jp], A[i][2 jp + 1]) of the block
+    float2 cacc[4];      // (c[2 ip], c[2 ip + 1])
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        cacc[i] = 0.0f;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+        for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.0f, 0.0f);
     }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) cacc[i] = make_float2(0.0f, 0.0f);
     int nl = 0;
 
     for (int base = 0; base < total; base += kChunk) {
@@ -144,19 +147,31 @@ __global__ void __launch_bounds__(GramShape<KP>::NT, 2) gram_kernel(GramArgs a) 
                 nl += (r == 0);
 #pragma unroll 1
                 for (int v = 0; v < V; ++v) {
+                    // the same multiply-adds as one fmaf per element, two per instruction
+                    // (packed FP32: identical roundings)
                     const float sw = w * rv[t * V + v];
                     const float4 *row = reinterpret_cast<const float4 *>(ys + (t * V + v) * KP);
                     const float4 a0 = row[ti], a1 = row[KB + ti];
                     const float4 b0 = row[tj], b1 = row[KB + tj];
-                    const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-                    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+                    const float2 sw2 = make_float2(sw, sw);
+                    const float2 sa2[4] = {__fmul2_rn(sw2, make_float2(a0.x, a0.y)),
+                                           __fmul2_rn(sw2, make_float2(a0.z, a0.w)),
+                                           __fmul2_rn(sw2, make_float2(a1.x, a1.y)),
+                                           __fmul2_rn(sw2, make_float2(a1.z, a1.w))};
+                    const float2 b2[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w),
+                                          make_float2(b1.x, b1.y), make_float2(b1.z, b1.w)};
                     const float dvs = dv[t * V + v];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
-                        const float sa = sw * av[i];
+                        const float sa = (i & 1) ? sa2[i >> 1].y : sa2[i >> 1].x;
+                        const float2 s2 = make_float2(sa, sa);
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(sa, bv[j], acc[i][j]);
-                        if (diag_block) cacc[i] = fmaf(sa, dvs, cacc[i]);
+                        for (int jp = 0; jp < 4; ++jp) acc[i][jp] = __ffma2_rn(s2, b2[jp], acc[i][jp]);
+                    }
+                    if (diag_block) {
+                        const float2 d2 = make_float2(dvs, dvs);
+#pragma unroll
+                        for (int ip = 0; ip < 4; ++ip) cacc[ip] = __ffma2_rn(sa2[ip], d2, cacc[ip]);
                     }
                 }
             }
@@ -175,9 +190,9 @@ __global__ void __launch_bounds__(GramShape<KP>::NT, 2) gram_kernel(GramArgs a) 
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int col = tj * 8 + j;
-            if (col < k && col >= row) A[row * k + col] = acc[i][j];
+            if (col < k && col >= row) A[row * k + col] = (j & 1) ? acc[i][j >> 1].y : acc[i][j >> 1].x;
         }
-        if (diag_block) a.cvec[lp * k + row] = cacc[i];
+        if (diag_block) a.cvec[lp * k + row] = (i & 1) ? cacc[i >> 1].y : cacc[i >> 1].x;
     }
     if (r == 0) a.nloc[lp] = nl;
 }
