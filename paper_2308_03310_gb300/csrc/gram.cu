@@ -46,8 +46,6 @@ struct GramShape {
     static constexpr int TH = P / TW;
     static constexpr int NT = (P * T + 31) / 32 * 32;   // threads per CTA, whole warps (two
                                                         // CTAs resident per SM)
-    // registers per thread that keep two CTAs resident (multiples of 8, at most 255)
-    static constexpr int REG = (65536 / (2 * NT)) / 8 * 8 > 255 ? 255 : (65536 / (2 * NT)) / 8 * 8;
     static_assert(TW * TH == P, "tile");
 };
 
@@ -65,7 +63,7 @@ __device__ __forceinline__ void upper_block(int r, int &ti, int &tj) {
 
 // VV: observed variables per point (1..3), a template parameter so the per-scalar loop unrolls
 template <int KP, int VV>
-__global__ void __maxnreg__(GramShape<KP>::REG) gram_kernel(GramArgs a) {
+__global__ void __launch_bounds__(GramShape<KP>::NT, 2) gram_kernel(GramArgs a) {
     using S = GramShape<KP>;
     constexpr int KB = S::KB, T = S::T, P = S::P, TW = S::TW, TH = S::TH, NT = S::NT;
     constexpr int V = VV;
