@@ -11,13 +11,13 @@
 // diagonal, so only the upper blocks are formed (36 of 64 at KP = 64; the diagonal blocks'
 // threads also accumulate c).  The CTA gathers the observation patch of its tile once -- the
 // observations of every bin (cs x cs cell) that the tile's cutoff disks touch -- and stages it
-// through shared memory 32 observation points at a time: their perturbation rows dy_o (k
+// through shared memory 64 observation points at a time: their perturbation rows dy_o (k
 // floats each, read from L2, where the whole dY lives), innovations and inverse variances.
 // The weight of each (point, observation) pair is computed once per chunk into shared memory;
 // a team skips observations outside its point's cutoff.  Nothing per-point is materialized in
 // HBM except the upper triangle of the k x k result (the paper's padded Y_loc[M, N_x, l_max V]
-// array is never formed).  Summation order is fixed by the bin order, so results are bitwise
-// reproducible.
+// array is never formed).  Summation order is fixed by the bin order and the interleaving of
+// the chunks, so results are bitwise reproducible.
 #include "common.cuh"
 #include "kernels.h"
 #include "patch.cuh"
@@ -108,10 +108,15 @@ __global__ void __launch_bounds__(GramShape<KP>::NT, 2) gram_kernel(GramArgs a) 
     for (int i = 0; i < 4; ++i) cacc[i] = make_float2(0.0f, 0.0f);
     int nl = 0;
 
-    for (int base = 0; base < total; base += kChunk) {
-        const int nch = min(kChunk, total - base);
+    // chunk c takes the candidates c, c + nck, c + 2 nck, ... of the patch: a uniform sample
+    // of it, so that every point of the tile finds about the same share of its local
+    // observations in every chunk (in patch order the share swings with the chunk's place, and
+    // the block barrier between chunks waits for the busiest point's team)
+    const int nck = (total + kChunk - 1) / kChunk;
+    for (int ck = 0; ck < nck; ++ck) {
+        const int nch = (total - ck + nck - 1) / nck;
         if (tid < nch) {
-            const int o = patch_obs(net, cell_base, cell_pre, nc, base + tid);
+            const int o = patch_obs(net, cell_base, cell_pre, nc, ck + tid * nck);
             oidx[tid] = o;
             opos[tid] = net.xy[o];
             for (int v = 0; v < V; ++v) {
