@@ -200,6 +200,274 @@ __global__ void __launch_bounds__(GramShape<KP>::NT, 2) gram_kernel(GramArgs a) 
     if (r == 0) a.nloc[lp] = nl;
 }
 
+// ---- the pipelined form (k >= 17: KP = 32, 64, 128) ---------------------------------------
+//
+// One CTA per SM over a TW x TH tile of points, a team of KB (KB + 1) / 2 threads per point as
+// in the team kernel, at most 16 warps: a scheduler's 16,384 registers then hold four warps
+// of up to 128 registers, room for the next entry's operands beside the 64 accumulators.  Per
+// chunk of CH candidates, one warp per point compacts its local (row, weight) entries in
+// candidate order (a ballot over the localization weights), so the multiply-add loop has no
+// branch and loads the next entry's operands while it multiplies the current ones.  The
+// candidates' indices are copied into shared memory two chunks ahead and their rows and
+// metadata one chunk ahead (cp.async, double buffered), so the copies overlap the arithmetic.
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+template <int KP>
+struct PipeShape {
+    static constexpr int KB = KP / 8;
+    static constexpr int T = KB * (KB + 1) / 2;                  // threads per point
+    static constexpr int TW = KP == 32 ? 8 : KP == 64 ? 7 : 3;
+    static constexpr int TH = KP == 32 ? 6 : KP == 64 ? 2 : 1;
+    static constexpr int P = TW * TH;                            // 48 / 14 / 3 points
+    static constexpr int NT = (P * T + 31) / 32 * 32;            // 480 / 512 / 416 threads
+    static constexpr int CH = KP == 128 ? 32 : 64;               // candidates per chunk
+    static_assert(NT <= 512, "at most 16 warps");
+    static_assert(CH <= 64, "two ballots per point");
+};
+
+template <int KP, int VV>
+struct PipeSmem {
+    using S = PipeShape<KP>;
+    static constexpr int R = S::CH * VV;                  // rows per chunk
+    static constexpr int rows = 0;                        // [2][R][KP]
+    static constexpr int ent = rows + 2 * R * KP;         // [P][R] float2 (row, sw)
+    static constexpr int entd = ent + 2 * S::P * R;       // [P][R] sw * dv
+    static constexpr int xy = entd + S::P * R;            // [2][CH] int2
+    static constexpr int yo = xy + 4 * S::CH;             // [2][R]
+    static constexpr int yb = yo + 2 * R;                 // [2][R]
+    static constexpr int ri = yb + 2 * R;                 // [2][R]
+    static constexpr int oidx = ri + 2 * R;               // [2][CH]
+    static constexpr int floats = oidx + 2 * S::CH;
+    static_assert(ent % 4 == 0 && xy % 2 == 0, "alignment");
+};
+
+template <int KP, int VV>
+__global__ void __launch_bounds__(PipeShape<KP>::NT, 1) gram_pipe_kernel(GramArgs a) {
+    using S = PipeShape<KP>;
+    using M = PipeSmem<KP, VV>;
+    constexpr int KB = S::KB, P = S::P, TW = S::TW, TH = S::TH, NT = S::NT, CH = S::CH;
+    constexpr int V = VV, R = M::R, Q4 = KP / 4;
+
+    __shared__ int cell_base[kMaxPatchCells];
+    __shared__ int cell_pre[kMaxPatchCells + 1];
+    __shared__ int warp_tot[NT / 32];
+    __shared__ int cnt[P];
+    __shared__ int nls[P];
+    extern __shared__ float4 dyn4[];
+    float *sm = reinterpret_cast<float *>(dyn4);
+    float *rows = sm + M::rows;
+    float2 *ent = reinterpret_cast<float2 *>(sm + M::ent);
+    float *entd = sm + M::entd;
+    int2 *xy = reinterpret_cast<int2 *>(sm + M::xy);
+    float *yo_s = sm + M::yo, *yb_s = sm + M::yb, *ri_s = sm + M::ri;
+    int *oidx = reinterpret_cast<int *>(sm + M::oidx);
+
+    const ObsNet &net = a.net;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int tx0 = blockIdx.x * TW;
+    const int ty0 = a.y_begin + blockIdx.y * TH;
+
+    const int nc = build_patch<NT>(net, a.nx, a.ny, tx0, ty0, TW, TH, cell_base, cell_pre,
+                                   warp_tot);
+    const int total = cell_pre[nc];
+    // chunk c holds the candidates c, c + nck, c + 2 nck, ... of the patch (a uniform sample)
+    const int nck = (total + CH - 1) / CH;
+    auto chunk_size = [&](int ck) { return (total - ck + nck - 1) / nck; };
+    if (tid < P) nls[tid] = 0;
+
+    // S1: the candidates' observation indices
+    auto stage_idx = [&](int ck, int buf) {
+        if (tid < chunk_size(ck))
+            cp_async4(oidx + buf * CH + tid,
+                      net.cell_obs + patch_slot(cell_base, cell_pre, nc, ck + tid * nck));
+    };
+    // S2: their points, innovations' parts, inverse variances and perturbation rows
+    auto stage_rows = [&](int ck, int buf) {
+        const int nch = chunk_size(ck);
+        const int *oi = oidx + buf * CH;
+        if (tid < nch) {
+            const int o = oi[tid];
+            cp_async8(xy + buf * CH + tid, net.xy + o);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const int s = o * V + v, d = buf * R + tid * V + v;
+                cp_async4(yo_s + d, a.yo + s);
+                cp_async4(yb_s + d, a.ybar + s);
+                cp_async4(ri_s + d, a.rinv + s);
+            }
+        }
+        for (int e = tid; e < nch * V * Q4; e += NT) {
+            const int row = e / Q4, c4 = e - row * Q4;
+            const int s = oi[row / V] * V + row % V;
+            cp_async16(rows + (size_t)(buf * R + row) * KP + 4 * piece_pos<KB>(c4),
+                       a.yb + (size_t)s * KP + 4 * c4);
+        }
+    };
+    // S3: each point's local entries of the chunk, in candidate order
+    auto build_entries = [&](int ck, int buf) {
+        const int nch = chunk_size(ck);
+        for (int pw = wid; pw < P; pw += NT / 32) {
+            const int qx = tx0 + pw % TW, qy = ty0 + pw / TW;
+            const bool qok = qx < a.nx && qy < a.y_end;
+            int base = 0;
+#pragma unroll
+            for (int h = 0; h < CH; h += 32) {
+                const int t = h + lane;
+                const float wt = (qok && t < nch)
+                                     ? loc_weight(net, xy[buf * CH + t], qx, qy, a.nx, a.ny)
+                                     : 0.0f;
+                const unsigned m = __ballot_sync(0xffffffffu, wt != 0.0f);
+                if (wt != 0.0f) {
+                    const int pos = base + __popc(m & ((1u << lane) - 1u));
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const int rr = buf * R + t * V + v;
+                        const float sw = wt * ri_s[rr];
+                        ent[pw * R + pos * V + v] = make_float2(__int_as_float(rr), sw);
+                        entd[pw * R + pos * V + v] = sw * ((yo_s[rr] - a.yref[v]) - yb_s[rr]);
+                    }
+                }
+                base += __popc(m);
+            }
+            if (lane == 0) {
+                cnt[pw] = base * V;
+                nls[pw] += base;
+            }
+        }
+    };
+
+    // ---- this thread's role: point p of the tile, upper 8 x 8 block (ti, tj) of A_p
+    const int p = tid / S::T;
+    int ti = 0, tj = 0;
+    upper_block<KB>(tid - p * S::T, ti, tj);
+    const bool diag = ti == tj;
+    float2 acc[8][4];   // acc[i][jp] = (A[i][2 jp], A[i][2 jp + 1]) of the block
+    float2 cacc[4];     // diagonal blocks: (c[2 ip], c[2 ip + 1])
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) cacc[i] = make_float2(0.0f, 0.0f);
+
+    // ---- the pipeline: indices two chunks ahead, rows and metadata one chunk ahead
+    if (nck > 0) stage_idx(0, 0);
+    cp_commit();
+    if (nck > 1) stage_idx(1, 1);
+    cp_commit();
+    cp_wait_all();
+    __syncthreads();
+    if (nck > 0) stage_rows(0, 0);
+    cp_commit();
+    for (int ck = 0; ck < nck; ++ck) {
+        const int buf = ck & 1;
+        cp_wait_all();      // chunk ck's rows and metadata, chunk ck + 1's indices
+        __syncthreads();    // ... visible to all; chunk ck - 1's arithmetic is done
+        build_entries(ck, buf);
+        if (ck + 1 < nck) stage_rows(ck + 1, buf ^ 1);
+        cp_commit();
+        if (ck + 2 < nck) stage_idx(ck + 2, buf);
+        cp_commit();
+        __syncthreads();    // the entries are visible
+        // acc += a (s b)^T over the point's entries (and c += a s dv on the diagonal blocks),
+        // the next entry's operands in flight
+        const int n = p < P ? cnt[p] : 0;
+        if (n > 0) {
+            const float2 *E = ent + p * R;
+            const float *ED = entd + p * R;
+            float2 e = E[0];
+            const float4 *rw = reinterpret_cast<const float4 *>(rows + __float_as_int(e.x) * KP);
+            float4 A0 = rw[ti], A1 = rw[KB + ti], B0 = rw[tj], B1 = rw[KB + tj];
+            float sw = e.y, sd = ED[0];
+            for (int i = 0; i < n; ++i) {
+                float4 nA0 = A0, nA1 = A1, nB0 = B0, nB1 = B1;
+                float nsw = sw, nsd = sd;
+                if (i + 1 < n) {
+                    const float2 en = E[i + 1];
+                    const float4 *rn =
+                        reinterpret_cast<const float4 *>(rows + __float_as_int(en.x) * KP);
+                    nA0 = rn[ti];
+                    nA1 = rn[KB + ti];
+                    nB0 = rn[tj];
+                    nB1 = rn[KB + tj];
+                    nsw = en.y;
+                    nsd = ED[i + 1];
+                }
+                // the same multiply-adds as one fmaf per element, two per instruction
+                const float2 s2 = make_float2(sw, sw);
+                const float2 b2[4] = {__fmul2_rn(s2, make_float2(B0.x, B0.y)),
+                                      __fmul2_rn(s2, make_float2(B0.z, B0.w)),
+                                      __fmul2_rn(s2, make_float2(B1.x, B1.y)),
+                                      __fmul2_rn(s2, make_float2(B1.z, B1.w))};
+                const float av[8] = {A0.x, A0.y, A0.z, A0.w, A1.x, A1.y, A1.z, A1.w};
+#pragma unroll
+                for (int ii = 0; ii < 8; ++ii) {
+                    const float2 a2 = make_float2(av[ii], av[ii]);
+#pragma unroll
+                    for (int jp = 0; jp < 4; ++jp) acc[ii][jp] = __ffma2_rn(a2, b2[jp], acc[ii][jp]);
+                }
+                if (diag) {
+                    const float2 d2 = make_float2(sd, sd);
+                    cacc[0] = __ffma2_rn(make_float2(A0.x, A0.y), d2, cacc[0]);
+                    cacc[1] = __ffma2_rn(make_float2(A0.z, A0.w), d2, cacc[1]);
+                    cacc[2] = __ffma2_rn(make_float2(A1.x, A1.y), d2, cacc[2]);
+                    cacc[3] = __ffma2_rn(make_float2(A1.z, A1.w), d2, cacc[3]);
+                }
+                A0 = nA0;
+                A1 = nA1;
+                B0 = nB0;
+                B1 = nB1;
+                sw = nsw;
+                sd = nsd;
+            }
+        }
+    }
+
+    // ---- results: the upper triangle of A (off-diagonal blocks whole), c, local counts
+    const int px = tx0 + p % TW, py = ty0 + p / TW;
+    if (p < P && px < a.nx && py < a.y_end) {
+        const size_t lp = (size_t)(py - a.y_begin) * a.nx + px;
+        const int k = a.k;
+        float *A = a.gram + lp * k * k;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int row = ti * 8 + i;
+            if (row >= k) continue;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int col = tj * 8 + j;
+                if (col < k && col >= row)
+                    A[row * k + col] = (j & 1) ? acc[i][j >> 1].y : acc[i][j >> 1].x;
+            }
+            if (diag) a.cvec[lp * k + row] = (i & 1) ? cacc[i >> 1].y : cacc[i >> 1].x;
+        }
+    }
+    __syncthreads();
+    if (tid < P) {
+        const int qx = tx0 + tid % TW, qy = ty0 + tid / TW;
+        if (qx < a.nx && qy < a.y_end) a.nloc[(size_t)(qy - a.y_begin) * a.nx + qx] = nls[tid];
+    }
+}
+
 template <int KP>
 size_t gram_smem() {
     return (size_t)(kChunk * 3 * KP + GramShape<KP>::P * kChunk) * sizeof(float);
@@ -234,24 +502,60 @@ cudaError_t launch_kp(const GramArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int KP, int VV>
+constexpr size_t pipe_smem() {
+    return (size_t)PipeSmem<KP, VV>::floats * sizeof(float);
+}
+
+template <int KP>
+cudaError_t prepare_pipe() {
+    cudaError_t e = cudaFuncSetAttribute(gram_pipe_kernel<KP, 1>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pipe_smem<KP, 1>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gram_pipe_kernel<KP, 2>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)pipe_smem<KP, 2>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gram_pipe_kernel<KP, 3>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)pipe_smem<KP, 3>());
+    return e;
+}
+
+template <int KP>
+cudaError_t launch_pipe(const GramArgs &a, cudaStream_t s) {
+    using S = PipeShape<KP>;
+    const int rows = a.y_end - a.y_begin;
+    dim3 grid((a.nx + S::TW - 1) / S::TW, (rows + S::TH - 1) / S::TH);
+    switch (a.net.V) {
+        case 1: gram_pipe_kernel<KP, 1><<<grid, S::NT, pipe_smem<KP, 1>(), s>>>(a); break;
+        case 2: gram_pipe_kernel<KP, 2><<<grid, S::NT, pipe_smem<KP, 2>(), s>>>(a); break;
+        case 3: gram_pipe_kernel<KP, 3><<<grid, S::NT, pipe_smem<KP, 3>(), s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
 
+// k <= 16: the team kernel (KP = 8, 16); k >= 17: the pipelined kernel (KP = 32, 64, 128)
 int gram_tile_height(int kp) {
     switch (kp) {
         case 8: return GramShape<8>::TH;
         case 16: return GramShape<16>::TH;
-        case 32: return GramShape<32>::TH;
-        case 64: return GramShape<64>::TH;
-        default: return GramShape<128>::TH;
+        case 32: return PipeShape<32>::TH;
+        case 64: return PipeShape<64>::TH;
+        default: return PipeShape<128>::TH;
     }
 }
 int gram_tile_width(int kp) {
     switch (kp) {
         case 8: return GramShape<8>::TW;
         case 16: return GramShape<16>::TW;
-        case 32: return GramShape<32>::TW;
-        case 64: return GramShape<64>::TW;
-        default: return GramShape<128>::TW;
+        case 32: return PipeShape<32>::TW;
+        case 64: return PipeShape<64>::TW;
+        default: return PipeShape<128>::TW;
     }
 }
 int gram_max_cells() { return kMaxPatchCells; }
@@ -260,9 +564,9 @@ cudaError_t gram_prepare(int kp) {
     switch (kp) {
         case 8: return prepare_kp<8>();
         case 16: return prepare_kp<16>();
-        case 32: return prepare_kp<32>();
-        case 64: return prepare_kp<64>();
-        case 128: return prepare_kp<128>();
+        case 32: return prepare_pipe<32>();
+        case 64: return prepare_pipe<64>();
+        case 128: return prepare_pipe<128>();
         default: return cudaErrorInvalidValue;
     }
 }
@@ -272,9 +576,9 @@ cudaError_t launch_gram(const GramArgs &a, cudaStream_t s) {
     switch (a.kp) {
         case 8: return launch_kp<8>(a, s);
         case 16: return launch_kp<16>(a, s);
-        case 32: return launch_kp<32>(a, s);
-        case 64: return launch_kp<64>(a, s);
-        case 128: return launch_kp<128>(a, s);
+        case 32: return launch_pipe<32>(a, s);
+        case 64: return launch_pipe<64>(a, s);
+        case 128: return launch_pipe<128>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }

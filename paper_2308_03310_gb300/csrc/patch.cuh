@@ -93,15 +93,21 @@ __device__ int build_patch(const ObsNet &net, int nx, int ny, int tx0, int ty0, 
     return nc;
 }
 
-// Observation index of the j-th candidate of the patch.
-__device__ __forceinline__ int patch_obs(const ObsNet &net, const int *cell_base,
-                                         const int *cell_pre, int nc, int j) {
+// Position in net.cell_obs of the j-th candidate of the patch.
+__device__ __forceinline__ int patch_slot(const int *cell_base, const int *cell_pre, int nc,
+                                          int j) {
     int lo = 0, hi = nc - 1;  // last bin whose prefix is <= j
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (cell_pre[mid] <= j) lo = mid; else hi = mid - 1;
     }
-    return net.cell_obs[cell_base[lo] + (j - cell_pre[lo])];
+    return cell_base[lo] + (j - cell_pre[lo]);
+}
+
+// Observation index of the j-th candidate of the patch.
+__device__ __forceinline__ int patch_obs(const ObsNet &net, const int *cell_base,
+                                         const int *cell_pre, int nc, int j) {
+    return net.cell_obs[patch_slot(cell_base, cell_pre, nc, j)];
 }
 
 // Localization weight (Gaussian, or Gaspari-Cohn) of observation point o seen from grid
