@@ -15,67 +15,93 @@
 // periodic halo of two nodes in shared memory, collides every staged node and pushes into a
 // second tile (halo one), collides again and pushes the second step's populations of the
 // tile's own nodes to HBM.  Per two steps a node is read ~1.3 times (the halos) and written
-// once: ~84 bytes instead of 144.  The collision of a node is the same function in both
-// kernels, so the arithmetic is the same as two single steps.
+// once: ~84 bytes instead of 144.  The collision runs on pairs of neighbouring nodes with
+// packed FP32 arithmetic; it is the same function in both kernels, so the arithmetic is the
+// same as two single steps.
 #include "common.cuh"
 #include "kernels.h"
 
 namespace lk {
 namespace {
 
+// The collision works on two nodes at once: every quantity is a float2 (node pair) and every
+// operation a packed FP32 instruction, which rounds each lane exactly as the scalar operation
+// would.  Both kernels use this function (the single-step kernel with a node in both lanes),
+// so their arithmetic is the same.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {   // a - b, one rounding
+    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+
+// 1 / x for x near 1 (the density): the hardware approximation refined by one Newton-Raphson
+// step y + y (1 - x y), which squares its relative error.
+__device__ __forceinline__ float2 rcp2(float2 x) {
+    float2 y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y.x) : "f"(x.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y.y) : "f"(x.y));
+    const float2 e = fma2(neg2(x), y, dup2(1.0f));
+    return fma2(y, e, y);
+}
+
 // c_q . v for a lattice direction known at compile time (no multiplications by 0 or +-1).
 template <int CX, int CY>
-__device__ __forceinline__ float cdot(float vx, float vy) {
-    if constexpr (CX == 0) return CY > 0 ? vy : -vy;
-    else if constexpr (CY == 0) return CX > 0 ? vx : -vx;
-    else return (CX > 0 ? vx : -vx) + (CY > 0 ? vy : -vy);
+__device__ __forceinline__ float2 cdot2(float2 vx, float2 vy) {
+    if constexpr (CX == 0) return CY > 0 ? vy : neg2(vy);
+    else if constexpr (CY == 0) return CX > 0 ? vx : neg2(vx);
+    else return add2(CX > 0 ? vx : neg2(vx), CY > 0 ? vy : neg2(vy));
 }
 
 // Direction Q (0..3) and its opposite 8 - Q: the equilibrium of the pair from its symmetric
 // and antisymmetric parts, w (a +- b) with a = base + 4.5 rho (c.u)^2 and b = 3 rho c.u, then
 // the BGK relaxation and the force term +- 3 w c.F.
 template <bool kForce, int Q>
-__device__ __forceinline__ void collide_pair(const float (&g)[NV], float ux, float uy, float base,
-                                             float r3, float r45, float f3x, float f3y,
-                                             float omega, float (&out)[NV]) {
-    constexpr float w = wq(Q);
-    const float cu = cdot<cx(Q), cy(Q)>(ux, uy);
-    const float a = fmaf(r45 * cu, cu, base);
-    const float b = r3 * cu;
-    const float gp = w * (a + b), gm = w * (a - b);  // equilibria of Q and 8 - Q
-    float sp = fmaf(omega, gp - g[Q], g[Q]);
-    float sm = fmaf(omega, gm - g[8 - Q], g[8 - Q]);
+__device__ __forceinline__ void collide_pair(const float2 (&g)[NV], float2 ux, float2 uy,
+                                             float2 base, float2 r3, float2 r45, float2 f3x,
+                                             float2 f3y, float2 omega, float2 (&out)[NV]) {
+    const float2 w = dup2(wq(Q));
+    const float2 cu = cdot2<cx(Q), cy(Q)>(ux, uy);
+    const float2 a = fma2(mul2(r45, cu), cu, base);
+    const float2 b = mul2(r3, cu);
+    const float2 gp = mul2(w, add2(a, b)), gm = mul2(w, sub2(a, b));  // equilibria of Q, 8 - Q
+    float2 sp = fma2(omega, sub2(gp, g[Q]), g[Q]);
+    float2 sm = fma2(omega, sub2(gm, g[8 - Q]), g[8 - Q]);
     if (kForce) {
-        const float fq = w * cdot<cx(Q), cy(Q)>(f3x, f3y);
-        sp += fq;
-        sm -= fq;
+        const float2 fq = mul2(w, cdot2<cx(Q), cy(Q)>(f3x, f3y));
+        sp = add2(sp, fq);
+        sm = sub2(sm, fq);
     }
     out[Q] = sp;
     out[8 - Q] = sm;
 }
 
-// BGK collision with the body-force source for one node: post-collision populations out[q]
-// from the node's deviations g[q] (Eq. 1, Sec. II-A).  f^eq_q = w_q (rho + rho (3 c.u +
+// BGK collision with the body-force source for two nodes: post-collision populations out[q]
+// from the nodes' deviations g[q] (Eq. 1, Sec. II-A).  f^eq_q = w_q (rho + rho (3 c.u +
 // 4.5 (c.u)^2 - 1.5 |u|^2)) written for the deviations: geq_q = w_q (drho - 1.5 rho |u|^2 +
 // 4.5 rho (c.u)^2 + 3 rho c.u), evaluated per pair of opposite directions (q, 8 - q), whose
 // terms differ only in the sign of c.u.
 template <bool kForce>
-__device__ __forceinline__ void collide(const float (&g)[NV], float fx, float fy, float omega,
-                                        float (&out)[NV]) {
-    const float drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
-    const float jx = ((g[2] + g[5]) + g[8]) - ((g[0] + g[3]) + g[6]);
-    const float jy = ((g[6] + g[7]) + g[8]) - ((g[0] + g[1]) + g[2]);
-    const float rho = 1.0f + drho;
-    const float rinv = __frcp_rn(rho);
-    const float ux = jx * rinv, uy = jy * rinv;
-    const float base = fmaf(-1.5f * rho, fmaf(ux, ux, uy * uy), drho);
-    const float r3 = 3.0f * rho, r45 = 4.5f * rho;
-    const float f3x = 3.0f * fx, f3y = 3.0f * fy;
+__device__ __forceinline__ void collide2(const float2 (&g)[NV], float2 fx, float2 fy,
+                                         float2 omega, float2 (&out)[NV]) {
+    const float2 g01 = add2(g[0], g[1]);
+    const float2 drho = add2(add2(add2(g01, add2(g[2], g[3])), add2(add2(g[4], g[5]),
+                                                                  add2(g[6], g[7]))), g[8]);
+    const float2 jx = sub2(add2(add2(g[2], g[5]), g[8]), add2(add2(g[0], g[3]), g[6]));
+    const float2 jy = sub2(add2(add2(g[6], g[7]), g[8]), add2(g01, g[2]));
+    const float2 rho = add2(dup2(1.0f), drho);
+    const float2 rinv = rcp2(rho);
+    const float2 ux = mul2(jx, rinv), uy = mul2(jy, rinv);
+    const float2 base = fma2(mul2(dup2(-1.5f), rho), fma2(ux, ux, mul2(uy, uy)), drho);
+    const float2 r3 = mul2(dup2(3.0f), rho), r45 = mul2(dup2(4.5f), rho);
+    const float2 f3x = mul2(dup2(3.0f), fx), f3y = mul2(dup2(3.0f), fy);
     collide_pair<kForce, 0>(g, ux, uy, base, r3, r45, f3x, f3y, omega, out);
     collide_pair<kForce, 1>(g, ux, uy, base, r3, r45, f3x, f3y, omega, out);
     collide_pair<kForce, 2>(g, ux, uy, base, r3, r45, f3x, f3y, omega, out);
     collide_pair<kForce, 3>(g, ux, uy, base, r3, r45, f3x, f3y, omega, out);
-    out[4] = fmaf(omega, wq(4) * base - g[4], g[4]);
+    out[4] = fma2(omega, sub2(mul2(dup2(wq(4)), base), g[4]), g[4]);
 }
 
 template <bool kForce>
@@ -90,16 +116,16 @@ __global__ void __launch_bounds__(256) lbm_step_kernel(const float *__restrict__
     const size_t mbase = (size_t)blockIdx.z * NV * npts;
     const size_t p = (size_t)y * nx + x;
 
-    float g[NV], out[NV];
+    float2 g[NV], out[NV];
 #pragma unroll
-    for (int q = 0; q < NV; ++q) g[q] = __ldcs(gin + mbase + q * npts + p);
-    float fx = 0.0f, fy = 0.0f;
+    for (int q = 0; q < NV; ++q) g[q] = dup2(__ldcs(gin + mbase + q * npts + p));
+    float2 fx = dup2(0.0f), fy = dup2(0.0f);
     if (kForce) {
         const float2 F = __ldg(force + p);
-        fx = F.x;
-        fy = F.y;
+        fx = dup2(F.x);
+        fy = dup2(F.y);
     }
-    collide<kForce>(g, fx, fy, omega, out);
+    collide2<kForce>(g, fx, fy, dup2(omega), out);
     const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
     const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
     float *dst = gout + mbase;
@@ -107,7 +133,7 @@ __global__ void __launch_bounds__(256) lbm_step_kernel(const float *__restrict__
     for (int q = 0; q < NV; ++q) {
         const int xd = cx(q) < 0 ? xm : (cx(q) > 0 ? xp : x);
         const int yd = cy(q) < 0 ? ym : (cy(q) > 0 ? yp : y);
-        __stcs(dst + q * npts + (size_t)yd * nx + xd, out[q]);
+        __stcs(dst + q * npts + (size_t)yd * nx + xd, out[q].x);
     }
 }
 
@@ -120,8 +146,8 @@ constexpr int kStep2Threads = 256;
 constexpr int kStep2MinBlocks = 4;
 
 template <int TX, int TY>
-constexpr size_t step2_smem() {          // staged tile (halo 2) and its force
-    return (size_t)(TX + 4) * (TY + 4) * (NV * sizeof(float) + sizeof(float2));
+constexpr size_t step2_smem() {          // staged tile (halo 2) and its force (two planes)
+    return (size_t)(TX + 4) * (TY + 4) * (NV + 2) * sizeof(float);
 }
 
 // Periodic wrap of a coordinate at most one period outside [0, n).
@@ -134,16 +160,19 @@ template <bool kForce, int TX, int TY, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) lbm_2step_kernel(const float *__restrict__ gin,
                                                              float *__restrict__ gout,
                                                              const float2 *__restrict__ force,
-                                                             int nx, int ny, float omega) {
+                                                             int nx, int ny, float omega_s) {
     constexpr int AX = TX + 4, AY = TY + 4;      // staged step-t tile, origin (x0 - 2, y0 - 2)
     constexpr int BX = TX + 2, BY = TY + 2;      // step-(t+1) nodes, origin (x0 - 1, y0 - 1)
+    static_assert(AX % 2 == 0 && BX % 2 == 0, "node pairs along x");
     extern __shared__ float sm[];
-    float *A = sm;                                              // [q][AY][AX]
-    float2 *Fs = reinterpret_cast<float2 *>(sm + NV * AX * AY); // force over A's nodes
+    float *A = sm;                               // [q][AY][AX]
+    float *Fx = sm + NV * AX * AY;               // force over A's nodes, x and y planes
+    float *Fy = Fx + AX * AY;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const size_t npts = (size_t)nx * ny;
     const size_t mbase = (size_t)blockIdx.z * NV * npts;
     const int tid = threadIdx.x;
+    const float2 omega = dup2(omega_s);
     // ---- stage the step-t populations of the tile and its halo (periodic) with cp.async:
     // every copy of the thread is in flight before the one wait
     for (int e = tid; e < AX * AY; e += NT) {
@@ -155,59 +184,75 @@ __global__ void __launch_bounds__(NT, MINB) lbm_2step_kernel(const float *__rest
                              __cvta_generic_to_shared(A + (q * AY + ay) * AX + ax)),
                          "l"(gin + mbase + q * npts + p)
                          : "memory");
-        if (kForce)
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)
-                             __cvta_generic_to_shared(Fs + e)),
-                         "l"(force + p)
+        if (kForce) {
+            const float *F = reinterpret_cast<const float *>(force + p);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)
+                             __cvta_generic_to_shared(Fx + e)),
+                         "l"(F)
                          : "memory");
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)
+                             __cvta_generic_to_shared(Fy + e)),
+                         "l"(F + 1)
+                         : "memory");
+        }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
-    // ---- collision t of every staged node, in place (a node owns its nine slots)
-    for (int e = tid; e < AX * AY; e += NT) {
-        float g[NV], out[NV];
+    // ---- collision t of every staged node, in place (a node owns its nine slots), two
+    // neighbouring nodes (ax, ax + 1), ax even, per thread
+    for (int e = tid; e < AX * AY / 2; e += NT) {
+        const int i = 2 * e;
+        float2 g[NV], out[NV];
 #pragma unroll
-        for (int q = 0; q < NV; ++q) g[q] = A[q * AY * AX + e];
-        float fx = 0.0f, fy = 0.0f;
+        for (int q = 0; q < NV; ++q) g[q] = *reinterpret_cast<const float2 *>(A + q * AY * AX + i);
+        float2 fx = dup2(0.0f), fy = dup2(0.0f);
         if (kForce) {
-            const float2 F = Fs[e];
-            fx = F.x;
-            fy = F.y;
+            fx = *reinterpret_cast<const float2 *>(Fx + i);
+            fy = *reinterpret_cast<const float2 *>(Fy + i);
         }
-        collide<kForce>(g, fx, fy, omega, out);
+        collide2<kForce>(g, fx, fy, omega, out);
 #pragma unroll
-        for (int q = 0; q < NV; ++q) A[q * AY * AX + e] = out[q];
+        for (int q = 0; q < NV; ++q) *reinterpret_cast<float2 *>(A + q * AY * AX + i) = out[q];
     }
     __syncthreads();
     // ---- streaming t -> t+1 as a pull from the collided neighbours, collision t+1, and the
-    // push of t+1 -> t+2 into the tile's own nodes in HBM
+    // push of t+1 -> t+2 into the tile's own nodes in HBM; node pairs (bx, bx + 1), bx even
     float *dst = gout + mbase;
-    for (int e = tid; e < BX * BY; e += NT) {
-        const int by = e / BX, bx = e - by * BX;
-        const int ay = by + 1, ax = bx + 1;                     // the node's slot in A
-        float g[NV], out[NV];
+    for (int e = tid; e < BX * BY / 2; e += NT) {
+        const int by = (2 * e) / BX, bx = 2 * e - by * BX;
+        const int ay = by + 1, ax = bx + 1;                     // the first node's slot in A
+        float2 g[NV], out[NV];
 #pragma unroll
-        for (int q = 0; q < NV; ++q) g[q] = A[(q * AY + ay - cy(q)) * AX + ax - cx(q)];
-        float fx = 0.0f, fy = 0.0f;
+        for (int q = 0; q < NV; ++q) {
+            const float *src = A + (q * AY + ay - cy(q)) * AX + ax - cx(q);
+            // the pair's sources are 8-byte aligned where ax - c_x is even (c_x = +-1)
+            g[q] = cx(q) != 0 ? *reinterpret_cast<const float2 *>(src)
+                              : make_float2(src[0], src[1]);
+        }
+        float2 fx = dup2(0.0f), fy = dup2(0.0f);
         if (kForce) {
-            const float2 F = Fs[ay * AX + ax];
-            fx = F.x;
-            fy = F.y;
+            fx = make_float2(Fx[ay * AX + ax], Fx[ay * AX + ax + 1]);
+            fy = make_float2(Fy[ay * AX + ax], Fy[ay * AX + ax + 1]);
         }
-        collide<kForce>(g, fx, fy, omega, out);
-        // targets (bx - 1 + c_x, by - 1 + c_y): inside the tile and the grid per axis
+        collide2<kForce>(g, fx, fy, omega, out);
+        // targets (bx - 1 + h + c_x, by - 1 + c_y) of node h: inside the tile and the grid
         const int tx0 = bx - 1, ty0 = by - 1;
-        bool vx[3], vy[3];
+        bool vx[4], vy[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < 4; ++c)
             vx[c] = (unsigned)(tx0 + c - 1) < (unsigned)TX && x0 + tx0 + c - 1 < nx;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
             vy[c] = (unsigned)(ty0 + c - 1) < (unsigned)TY && y0 + ty0 + c - 1 < ny;
-        }
         const long long at = (long long)(y0 + ty0) * nx + (x0 + tx0);
 #pragma unroll
-        for (int q = 0; q < NV; ++q)
-            if (vx[cx(q) + 1] && vy[cy(q) + 1])
-                __stcs(dst + at + (long long)q * (long long)npts + cy(q) * nx + cx(q), out[q]);
+        for (int q = 0; q < NV; ++q) {
+            float *d = dst + at + (long long)q * (long long)npts + cy(q) * nx + cx(q);
+            if (vy[cy(q) + 1]) {
+                if (vx[cx(q) + 1]) __stcs(d, out[q].x);
+                if (vx[cx(q) + 2]) __stcs(d + 1, out[q].y);
+            }
+        }
     }
 }
 
