@@ -76,7 +76,7 @@ def test_lbm_matches_oracle_after_10_steps(nx, ny, k, tau, forced, n_aux):
 
 
 @pytest.mark.parametrize("nx,ny,k,forced", [(256, 64, 3, True), (37, 29, 2, True),
-                                            (20, 12, 2, False), (130, 50, 1, True)])
+                                            (20, 12, 2, False), (130, 50, 2, True)])
 def test_two_step_launch_equals_two_single_steps(nx, ny, k, forced):
     # forecast(2) runs one temporally blocked two-step launch, forecast(1) a single-step
     # launch; the collision is the same function in both, so two single steps must give the
