@@ -12,7 +12,7 @@
 // one step moves 72 bytes per lattice update and is HBM bound.
 //
 // Two steps per launch (temporal blocking): a CTA stages a TX x TY tile of one member with a
-// periodic halo of two nodes in shared memory, collides every staged node and pushes into a
+// periodic halo of two nodes in shared memory (rows copied in 16-byte runs), collides every staged node and pushes into a
 // second tile (halo one), collides again and pushes the second step's populations of the
 // tile's own nodes to HBM.  Per two steps a node is read ~1.3 times (the halos) and written
 // once: ~84 bytes instead of 144.  The collision runs on pairs of neighbouring nodes with
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256) lbm_step_kernel(const float *__restrict__
     }
 }
 
-// Two-step tile: 64 x 12 output nodes, 256 threads, four CTAs (47 KB of shared memory each)
+// Two-step tile: 64 x 12 output nodes, 256 threads, four CTAs (51 KB of shared memory each)
 // per SM.  Measured against 64 x 8/16/20, 32 x 16 and 128 x 8 tiles and 128/512-thread CTAs:
 // the fastest at 256^2 (k = 32) and 1024^2 (k = 64).
 constexpr int kTX = 64;                  // output tile width
@@ -146,8 +146,8 @@ constexpr int kStep2Threads = 256;
 constexpr int kStep2MinBlocks = 4;
 
 template <int TX, int TY>
-constexpr size_t step2_smem() {          // staged tile (halo 2) and its force (two planes)
-    return (size_t)(TX + 4) * (TY + 4) * (NV + 2) * sizeof(float);
+constexpr size_t step2_smem() {          // staged tile (halo 2, x window widened to 16 bytes)
+    return (size_t)(TX + 8) * (TY + 4) * (NV + 2) * sizeof(float);   // and its force
 }
 
 // Periodic wrap of a coordinate at most one period outside [0, n).
@@ -156,59 +156,79 @@ __device__ __forceinline__ int wrap1(int a, int n) {
     return (unsigned)r < (unsigned)n ? r : posmod(a, n);   // grids narrower than the halo
 }
 
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)
+                     __cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)
+                     __cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+
 template <bool kForce, int TX, int TY, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) lbm_2step_kernel(const float *__restrict__ gin,
                                                              float *__restrict__ gout,
                                                              const float2 *__restrict__ force,
                                                              int nx, int ny, float omega_s) {
-    constexpr int AX = TX + 4, AY = TY + 4;      // staged step-t tile, origin (x0 - 2, y0 - 2)
+    // staged step-t window: x in [x0 - 4, x0 + TX + 4), y in [y0 - 2, y0 + TY + 2); the nodes
+    // two beyond the tile on each side are the halo, the outer two columns only align the
+    // window's rows to 16 bytes
+    constexpr int AX = TX + 8, AY = TY + 4;
     constexpr int BX = TX + 2, BY = TY + 2;      // step-(t+1) nodes, origin (x0 - 1, y0 - 1)
-    static_assert(AX % 2 == 0 && BX % 2 == 0, "node pairs along x");
+    constexpr int HX = TX + 4;                   // collided columns 2 .. AX - 3
+    static_assert(TX % 4 == 0 && HX % 2 == 0 && BX % 2 == 0, "16-byte rows, node pairs");
     extern __shared__ float sm[];
-    float *A = sm;                               // [q][AY][AX]
-    float *Fx = sm + NV * AX * AY;               // force over A's nodes, x and y planes
-    float *Fy = Fx + AX * AY;
+    float *A = sm;                                               // [q][AY][AX]
+    float2 *Fs = reinterpret_cast<float2 *>(sm + NV * AX * AY);  // force over A's nodes
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const size_t npts = (size_t)nx * ny;
     const size_t mbase = (size_t)blockIdx.z * NV * npts;
     const int tid = threadIdx.x;
     const float2 omega = dup2(omega_s);
-    // ---- stage the step-t populations of the tile and its halo (periodic) with cp.async:
-    // every copy of the thread is in flight before the one wait
-    for (int e = tid; e < AX * AY; e += NT) {
-        const int ay = e / AX, ax = e - ay * AX;
-        const size_t p = (size_t)wrap1(y0 - 2 + ay, ny) * nx + wrap1(x0 - 2 + ax, nx);
+    // ---- stage the window with cp.async, every copy of the thread in flight before the one
+    // wait: runs of four nodes (16 bytes) where nx is a multiple of 4 -- x0 is, so every run
+    // starts on a 16-byte boundary, also where it wraps -- single nodes otherwise
+    if ((nx & 3) == 0) {
+        constexpr int GX = AX / 4;
+        for (int e = tid; e < AY * GX; e += NT) {
+            const int ay = e / GX, gx = e - ay * GX;
+            const size_t p = (size_t)wrap1(y0 - 2 + ay, ny) * nx + wrap1(x0 - 4 + 4 * gx, nx);
+            float *a = A + ay * AX + 4 * gx;
 #pragma unroll
-        for (int q = 0; q < NV; ++q)
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)
-                             __cvta_generic_to_shared(A + (q * AY + ay) * AX + ax)),
-                         "l"(gin + mbase + q * npts + p)
-                         : "memory");
-        if (kForce) {
-            const float *F = reinterpret_cast<const float *>(force + p);
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)
-                             __cvta_generic_to_shared(Fx + e)),
-                         "l"(F)
-                         : "memory");
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)
-                             __cvta_generic_to_shared(Fy + e)),
-                         "l"(F + 1)
-                         : "memory");
+            for (int q = 0; q < NV; ++q) cp_async16(a + q * AY * AX, gin + mbase + q * npts + p);
+            if (kForce) {
+                cp_async16(Fs + ay * AX + 4 * gx, force + p);
+                cp_async16(Fs + ay * AX + 4 * gx + 2, force + p + 2);
+            }
+        }
+    } else {
+        for (int e = tid; e < AX * AY; e += NT) {
+            const int ay = e / AX, ax = e - ay * AX;
+            const size_t p = (size_t)wrap1(y0 - 2 + ay, ny) * nx + wrap1(x0 - 4 + ax, nx);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) cp_async4(A + (q * AY + ay) * AX + ax, gin + mbase + q * npts + p);
+            if (kForce) {
+                const float *F = reinterpret_cast<const float *>(force + p);
+                cp_async4(reinterpret_cast<float *>(Fs + e), F);
+                cp_async4(reinterpret_cast<float *>(Fs + e) + 1, F + 1);
+            }
         }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
-    // ---- collision t of every staged node, in place (a node owns its nine slots), two
+    // ---- collision t of the tile and its halo, in place (a node owns its nine slots), two
     // neighbouring nodes (ax, ax + 1), ax even, per thread
-    for (int e = tid; e < AX * AY / 2; e += NT) {
-        const int i = 2 * e;
+    for (int e = tid; e < HX * AY / 2; e += NT) {
+        const int ay = (2 * e) / HX, ax = 2 + 2 * e - ay * HX;
+        const int i = ay * AX + ax;
         float2 g[NV], out[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) g[q] = *reinterpret_cast<const float2 *>(A + q * AY * AX + i);
         float2 fx = dup2(0.0f), fy = dup2(0.0f);
         if (kForce) {
-            fx = *reinterpret_cast<const float2 *>(Fx + i);
-            fy = *reinterpret_cast<const float2 *>(Fy + i);
+            const float4 F = *reinterpret_cast<const float4 *>(Fs + i);
+            fx = make_float2(F.x, F.z);
+            fy = make_float2(F.y, F.w);
         }
         collide2<kForce>(g, fx, fy, omega, out);
 #pragma unroll
@@ -220,7 +240,7 @@ __global__ void __launch_bounds__(NT, MINB) lbm_2step_kernel(const float *__rest
     float *dst = gout + mbase;
     for (int e = tid; e < BX * BY / 2; e += NT) {
         const int by = (2 * e) / BX, bx = 2 * e - by * BX;
-        const int ay = by + 1, ax = bx + 1;                     // the first node's slot in A
+        const int ay = by + 1, ax = bx + 3;                     // the first node's slot in A
         float2 g[NV], out[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
@@ -231,8 +251,9 @@ __global__ void __launch_bounds__(NT, MINB) lbm_2step_kernel(const float *__rest
         }
         float2 fx = dup2(0.0f), fy = dup2(0.0f);
         if (kForce) {
-            fx = make_float2(Fx[ay * AX + ax], Fx[ay * AX + ax + 1]);
-            fy = make_float2(Fy[ay * AX + ax], Fy[ay * AX + ax + 1]);
+            const float2 F0 = Fs[ay * AX + ax], F1 = Fs[ay * AX + ax + 1];
+            fx = make_float2(F0.x, F1.x);
+            fy = make_float2(F0.y, F1.y);
         }
         collide2<kForce>(g, fx, fy, omega, out);
         // targets (bx - 1 + h + c_x, by - 1 + c_y) of node h: inside the tile and the grid
