@@ -681,19 +681,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int 
                             const float4 u1 = *reinterpret_cast<const float4 *>(up + 4);
                             const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
                             const float u[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+                            // pairs of slots with packed FP32 instructions (each lane rounds
+                            // as the scalar operation); c in two chains (even, odd slots)
                             uint32_t hw[4], lw[4];
+                            float2 c2 = make_float2(cacc[p], 0.0f);
 #pragma unroll
                             for (int i = 0; i < 4; ++i) {
-                                const float x0 = yv[2 * i] * w[2 * i];
-                                const float x1 = yv[2 * i + 1] * w[2 * i + 1];
-                                const __half2 h = __floats2half2_rn(x0, x1);
+                                const float2 x = __fmul2_rn(make_float2(yv[2 * i], yv[2 * i + 1]),
+                                                            make_float2(w[2 * i], w[2 * i + 1]));
+                                const __half2 h = __floats2half2_rn(x.x, x.y);
                                 const float2 hf = __half22float2(h);
-                                const __half2 l = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+                                const float2 r = __ffma2_rn(hf, make_float2(-1.0f, -1.0f), x);
+                                const __half2 l = __floats2half2_rn(r.x, r.y);
                                 hw[i] = *reinterpret_cast<const uint32_t *>(&h);
                                 lw[i] = *reinterpret_cast<const uint32_t *>(&l);
-                                cacc[p] = fmaf(x0, u[2 * i], cacc[p]);
-                                cacc[p] = fmaf(x1, u[2 * i + 1], cacc[p]);
+                                c2 = __ffma2_rn(x, make_float2(u[2 * i], u[2 * i + 1]), c2);
                             }
+                            cacc[p] = c2.x + c2.y;
                             unsigned char *tp = st + p * S::OPB;
                             *reinterpret_cast<uint4 *>(tp + core_off_b<KC>(S::KW + m, k8)) =
                                 make_uint4(hw[0], hw[1], hw[2], hw[3]);
