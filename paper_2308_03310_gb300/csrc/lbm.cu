@@ -137,18 +137,17 @@ __global__ void __launch_bounds__(256) lbm_step_kernel(const float *__restrict__
     }
 }
 
-// Two-step tile: 64 x 12 output nodes, 256 threads, two persistent CTAs per SM (two windows
-// of 51 KB of shared memory each)
+// Two-step tile: 64 x 12 output nodes, 256 threads, four CTAs (51 KB of shared memory each)
 // per SM.  Measured against 64 x 8/16/20, 32 x 16 and 128 x 8 tiles and 128/512-thread CTAs:
 // the fastest at 256^2 (k = 32) and 1024^2 (k = 64).
 constexpr int kTX = 64;                  // output tile width
 constexpr int kTY = 12;                  // output tile height
 constexpr int kStep2Threads = 256;
-constexpr int kStep2MinBlocks = 2;
+constexpr int kStep2MinBlocks = 4;
 
 template <int TX, int TY>
-constexpr size_t step2_smem() {          // two staged windows (halo 2, x window widened to 16
-    return 2 * (size_t)(TX + 8) * (TY + 4) * (NV + 2) * sizeof(float);   // bytes) and force
+constexpr size_t step2_smem() {          // staged tile (halo 2, x window widened to 16 bytes)
+    return (size_t)(TX + 8) * (TY + 4) * (NV + 2) * sizeof(float);   // and its force
 }
 
 // Periodic wrap of a coordinate at most one period outside [0, n).
@@ -166,187 +165,141 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
                      __cvta_generic_to_shared(dst)), "l"(src) : "memory");
 }
 
-// Persistent: CTA b takes the tiles b, b + G, ... (G CTAs; a tile is (x block, y block,
-// member)), and stages the next tile's window with cp.async while it computes the current one
-// (two windows per CTA).
 template <bool kForce, int TX, int TY, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) lbm_2step_kernel(const float *__restrict__ gin,
                                                              float *__restrict__ gout,
                                                              const float2 *__restrict__ force,
-                                                             int nx, int ny, int nmem,
-                                                             float omega_s) {
+                                                             int nx, int ny, float omega_s) {
     // staged step-t window: x in [x0 - 4, x0 + TX + 4), y in [y0 - 2, y0 + TY + 2); the nodes
     // two beyond the tile on each side are the halo, the outer two columns only align the
     // window's rows to 16 bytes
     constexpr int AX = TX + 8, AY = TY + 4;
     constexpr int BX = TX + 2, BY = TY + 2;      // step-(t+1) nodes, origin (x0 - 1, y0 - 1)
     constexpr int HX = TX + 4;                   // collided columns 2 .. AX - 3
-    constexpr int WIN = (NV + 2) * AX * AY;      // floats of one window: state and force
     static_assert(TX % 4 == 0 && HX % 2 == 0 && BX % 2 == 0, "16-byte rows, node pairs");
     extern __shared__ float sm[];
-    const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY;
-    const long long ntiles = (long long)ntx * nty * nmem;
+    float *A = sm;                                               // [q][AY][AX]
+    float2 *Fs = reinterpret_cast<float2 *>(sm + NV * AX * AY);  // force over A's nodes
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const size_t npts = (size_t)nx * ny;
+    const size_t mbase = (size_t)blockIdx.z * NV * npts;
     const int tid = threadIdx.x;
     const float2 omega = dup2(omega_s);
-    auto origin = [&](long long t, int &x0, int &y0, size_t &mbase) {
-        const long long per = (long long)ntx * nty;
-        const int m = (int)(t / per), r = (int)(t - (long long)m * per);
-        y0 = (r / ntx) * TY;
-        x0 = (r - (r / ntx) * ntx) * TX;
-        mbase = (size_t)m * NV * npts;
-    };
-    // the window of tile t into buffer buf, every copy in flight (one commit group)
-    auto stage = [&](long long t, int buf) {
-        int x0, y0;
-        size_t mbase;
-        origin(t, x0, y0, mbase);
-        float *A = sm + buf * WIN;
-        float2 *Fs = reinterpret_cast<float2 *>(A + NV * AX * AY);
-        if ((nx & 3) == 0) {
-            // runs of four nodes (16 bytes): x0 is a multiple of 4, so every run starts on a
-            // 16-byte boundary, also where the window wraps
-            constexpr int GX = AX / 4;
-            for (int e = tid; e < AY * GX; e += NT) {
-                const int ay = e / GX, gx = e - ay * GX;
-                const size_t p =
-                    (size_t)wrap1(y0 - 2 + ay, ny) * nx + wrap1(x0 - 4 + 4 * gx, nx);
-                float *a = A + ay * AX + 4 * gx;
+    // ---- stage the window with cp.async, every copy of the thread in flight before the one
+    // wait: runs of four nodes (16 bytes) where nx is a multiple of 4 -- x0 is, so every run
+    // starts on a 16-byte boundary, also where it wraps -- single nodes otherwise
+    if ((nx & 3) == 0) {
+        constexpr int GX = AX / 4;
+        for (int e = tid; e < AY * GX; e += NT) {
+            const int ay = e / GX, gx = e - ay * GX;
+            const size_t p = (size_t)wrap1(y0 - 2 + ay, ny) * nx + wrap1(x0 - 4 + 4 * gx, nx);
+            float *a = A + ay * AX + 4 * gx;
 #pragma unroll
-                for (int q = 0; q < NV; ++q)
-                    cp_async16(a + q * AY * AX, gin + mbase + q * npts + p);
-                if (kForce) {
-                    cp_async16(Fs + ay * AX + 4 * gx, force + p);
-                    cp_async16(Fs + ay * AX + 4 * gx + 2, force + p + 2);
-                }
-            }
-        } else {
-            for (int e = tid; e < AX * AY; e += NT) {
-                const int ay = e / AX, ax = e - ay * AX;
-                const size_t p = (size_t)wrap1(y0 - 2 + ay, ny) * nx + wrap1(x0 - 4 + ax, nx);
-#pragma unroll
-                for (int q = 0; q < NV; ++q)
-                    cp_async4(A + (q * AY + ay) * AX + ax, gin + mbase + q * npts + p);
-                if (kForce) {
-                    const float *F = reinterpret_cast<const float *>(force + p);
-                    cp_async4(reinterpret_cast<float *>(Fs + e), F);
-                    cp_async4(reinterpret_cast<float *>(Fs + e) + 1, F + 1);
-                }
-            }
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-
-    long long t = blockIdx.x;
-    if (t < ntiles) stage(t, 0);
-    for (int buf = 0; t < ntiles; t += gridDim.x, buf ^= 1) {
-        const long long tn = t + gridDim.x;
-        if (tn < ntiles) stage(tn, buf ^ 1);
-        else asm volatile("cp.async.commit_group;" ::: "memory");   // keep one group per tile
-        asm volatile("cp.async.wait_group 1;" ::: "memory");          // this tile's window
-        __syncthreads();
-        int x0, y0;
-        size_t mbase;
-        origin(t, x0, y0, mbase);
-        float *A = sm + buf * WIN;
-        const float2 *Fs = reinterpret_cast<const float2 *>(A + NV * AX * AY);
-        // ---- collision t of the tile and its halo, in place (a node owns its nine slots),
-        // two neighbouring nodes (ax, ax + 1), ax even, per thread
-        for (int e = tid; e < HX * AY / 2; e += NT) {
-            const int ay = (2 * e) / HX, ax = 2 + 2 * e - ay * HX;
-            const int i = ay * AX + ax;
-            float2 g[NV], out[NV];
-#pragma unroll
-            for (int q = 0; q < NV; ++q)
-                g[q] = *reinterpret_cast<const float2 *>(A + q * AY * AX + i);
-            float2 fx = dup2(0.0f), fy = dup2(0.0f);
+            for (int q = 0; q < NV; ++q) cp_async16(a + q * AY * AX, gin + mbase + q * npts + p);
             if (kForce) {
-                const float4 F = *reinterpret_cast<const float4 *>(Fs + i);
-                fx = make_float2(F.x, F.z);
-                fy = make_float2(F.y, F.w);
+                cp_async16(Fs + ay * AX + 4 * gx, force + p);
+                cp_async16(Fs + ay * AX + 4 * gx + 2, force + p + 2);
             }
-            collide2<kForce>(g, fx, fy, omega, out);
-#pragma unroll
-            for (int q = 0; q < NV; ++q) *reinterpret_cast<float2 *>(A + q * AY * AX + i) = out[q];
         }
-        __syncthreads();
-        // ---- streaming t -> t+1 as a pull from the collided neighbours, collision t+1, and
-        // the push of t+1 -> t+2 into the tile's own nodes in HBM; node pairs (bx, bx + 1)
-        float *dst = gout + mbase;
-        for (int e = tid; e < BX * BY / 2; e += NT) {
-            const int by = (2 * e) / BX, bx = 2 * e - by * BX;
-            const int ay = by + 1, ax = bx + 3;                     // the first node's slot in A
-            float2 g[NV], out[NV];
+    } else {
+        for (int e = tid; e < AX * AY; e += NT) {
+            const int ay = e / AX, ax = e - ay * AX;
+            const size_t p = (size_t)wrap1(y0 - 2 + ay, ny) * nx + wrap1(x0 - 4 + ax, nx);
 #pragma unroll
-            for (int q = 0; q < NV; ++q) {
-                const float *src = A + (q * AY + ay - cy(q)) * AX + ax - cx(q);
-                // the pair's sources are 8-byte aligned where ax - c_x is even (c_x = +-1)
-                g[q] = cx(q) != 0 ? *reinterpret_cast<const float2 *>(src)
-                                  : make_float2(src[0], src[1]);
-            }
-            float2 fx = dup2(0.0f), fy = dup2(0.0f);
+            for (int q = 0; q < NV; ++q) cp_async4(A + (q * AY + ay) * AX + ax, gin + mbase + q * npts + p);
             if (kForce) {
-                const float2 F0 = Fs[ay * AX + ax], F1 = Fs[ay * AX + ax + 1];
-                fx = make_float2(F0.x, F1.x);
-                fy = make_float2(F0.y, F1.y);
-            }
-            collide2<kForce>(g, fx, fy, omega, out);
-            // targets (bx - 1 + h + c_x, by - 1 + c_y) of node h: inside the tile and the grid
-            const int tx0 = bx - 1, ty0 = by - 1;
-            bool vx[4], vy[3];
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-                vx[c] = (unsigned)(tx0 + c - 1) < (unsigned)TX && x0 + tx0 + c - 1 < nx;
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-                vy[c] = (unsigned)(ty0 + c - 1) < (unsigned)TY && y0 + ty0 + c - 1 < ny;
-            const long long at = (long long)(y0 + ty0) * nx + (x0 + tx0);
-#pragma unroll
-            for (int q = 0; q < NV; ++q) {
-                float *d = dst + at + (long long)q * (long long)npts + cy(q) * nx + cx(q);
-                if (vy[cy(q) + 1]) {
-                    if (vx[cx(q) + 1]) __stcs(d, out[q].x);
-                    if (vx[cx(q) + 2]) __stcs(d + 1, out[q].y);
-                }
+                const float *F = reinterpret_cast<const float *>(force + p);
+                cp_async4(reinterpret_cast<float *>(Fs + e), F);
+                cp_async4(reinterpret_cast<float *>(Fs + e) + 1, F + 1);
             }
         }
-        __syncthreads();   // the window may be refilled by the next iteration's stage
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    // ---- collision t of the tile and its halo, in place (a node owns its nine slots), two
+    // neighbouring nodes (ax, ax + 1), ax even, per thread
+    for (int e = tid; e < HX * AY / 2; e += NT) {
+        const int ay = (2 * e) / HX, ax = 2 + 2 * e - ay * HX;
+        const int i = ay * AX + ax;
+        float2 g[NV], out[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) g[q] = *reinterpret_cast<const float2 *>(A + q * AY * AX + i);
+        float2 fx = dup2(0.0f), fy = dup2(0.0f);
+        if (kForce) {
+            const float4 F = *reinterpret_cast<const float4 *>(Fs + i);
+            fx = make_float2(F.x, F.z);
+            fy = make_float2(F.y, F.w);
+        }
+        collide2<kForce>(g, fx, fy, omega, out);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) *reinterpret_cast<float2 *>(A + q * AY * AX + i) = out[q];
+    }
+    __syncthreads();
+    // ---- streaming t -> t+1 as a pull from the collided neighbours, collision t+1, and the
+    // push of t+1 -> t+2 into the tile's own nodes in HBM; node pairs (bx, bx + 1), bx even
+    float *dst = gout + mbase;
+    for (int e = tid; e < BX * BY / 2; e += NT) {
+        const int by = (2 * e) / BX, bx = 2 * e - by * BX;
+        const int ay = by + 1, ax = bx + 3;                     // the first node's slot in A
+        float2 g[NV], out[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            const float *src = A + (q * AY + ay - cy(q)) * AX + ax - cx(q);
+            // the pair's sources are 8-byte aligned where ax - c_x is even (c_x = +-1)
+            g[q] = cx(q) != 0 ? *reinterpret_cast<const float2 *>(src)
+                              : make_float2(src[0], src[1]);
+        }
+        float2 fx = dup2(0.0f), fy = dup2(0.0f);
+        if (kForce) {
+            const float2 F0 = Fs[ay * AX + ax], F1 = Fs[ay * AX + ax + 1];
+            fx = make_float2(F0.x, F1.x);
+            fy = make_float2(F0.y, F1.y);
+        }
+        collide2<kForce>(g, fx, fy, omega, out);
+        // targets (bx - 1 + h + c_x, by - 1 + c_y) of node h: inside the tile and the grid
+        const int tx0 = bx - 1, ty0 = by - 1;
+        bool vx[4], vy[3];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            vx[c] = (unsigned)(tx0 + c - 1) < (unsigned)TX && x0 + tx0 + c - 1 < nx;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            vy[c] = (unsigned)(ty0 + c - 1) < (unsigned)TY && y0 + ty0 + c - 1 < ny;
+        const long long at = (long long)(y0 + ty0) * nx + (x0 + tx0);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            float *d = dst + at + (long long)q * (long long)npts + cy(q) * nx + cx(q);
+            if (vy[cy(q) + 1]) {
+                if (vx[cx(q) + 1]) __stcs(d, out[q].x);
+                if (vx[cx(q) + 2]) __stcs(d + 1, out[q].y);
+            }
+        }
+    }
 }
 
 template <int TX, int TY, int NT, int MINB>
-cudaError_t set_step2_smem(int *grid) {
-    const int smem = (int)step2_smem<TX, TY>();
+cudaError_t set_step2_smem() {
     cudaError_t e = cudaFuncSetAttribute(lbm_2step_kernel<true, TX, TY, NT, MINB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(lbm_2step_kernel<false, TX, TY, NT, MINB>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    int dev = 0, sms = 0, per_sm = 0;
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, lbm_2step_kernel<true, TX, TY, NT, MINB>, NT, smem);
-    if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
-    if (e == cudaSuccess) *grid = sms * per_sm;
-    return e;
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)step2_smem<TX, TY>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(lbm_2step_kernel<false, TX, TY, NT, MINB>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)step2_smem<TX, TY>());
 }
 
 template <int TX, int TY, int NT, int MINB>
 cudaError_t launch_2step(const float *gin, float *gout, const float2 *force, int nx, int ny,
-                         int nmem, float tau, int grid, cudaStream_t s) {
-    const long long tiles = (long long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY) * nmem;
-    const unsigned blocks = (unsigned)(tiles < grid ? tiles : grid);
+                         int nmem, float tau, cudaStream_t s) {
+    dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY, nmem);
     const float omega = 1.0f / tau;
     const size_t smem = step2_smem<TX, TY>();
     if (force)
-        lbm_2step_kernel<true, TX, TY, NT, MINB><<<blocks, NT, smem, s>>>(gin, gout, force, nx,
-                                                                          ny, nmem, omega);
+        lbm_2step_kernel<true, TX, TY, NT, MINB><<<grid, NT, smem, s>>>(gin, gout, force, nx,
+                                                                        ny, omega);
     else
-        lbm_2step_kernel<false, TX, TY, NT, MINB><<<blocks, NT, smem, s>>>(gin, gout, force, nx,
-                                                                           ny, nmem, omega);
+        lbm_2step_kernel<false, TX, TY, NT, MINB><<<grid, NT, smem, s>>>(gin, gout, force, nx,
+                                                                         ny, omega);
     return cudaGetLastError();
 }
 
@@ -395,18 +348,13 @@ cudaError_t launch_lbm_step(const float *gin, float *gout, const float2 *force, 
     return cudaGetLastError();
 }
 
-int g_step2_grid = 0;   // resident CTAs of the two-step kernel (lbm_prepare)
-
-cudaError_t lbm_prepare() {
-    return set_step2_smem<kTX, kTY, kStep2Threads, kStep2MinBlocks>(&g_step2_grid);
-}
+cudaError_t lbm_prepare() { return set_step2_smem<kTX, kTY, kStep2Threads, kStep2MinBlocks>(); }
 
 cudaError_t launch_lbm_2step(const float *gin, float *gout, const float2 *force, int nx, int ny,
                              int nmem, float tau, cudaStream_t s) {
     if (nmem <= 0) return cudaSuccess;
-    if (g_step2_grid < 1) return cudaErrorInvalidConfiguration;
     return launch_2step<kTX, kTY, kStep2Threads, kStep2MinBlocks>(gin, gout, force, nx, ny, nmem,
-                                                                   tau, g_step2_grid, s);
+                                                                   tau, s);
 }
 
 cudaError_t launch_f_to_g(const float *f, float *g, int nmem, size_t npts, cudaStream_t s) {
