@@ -72,6 +72,9 @@ def parse_args(argv=None):
                         "both: fp32 as the headline value, mixed reported beside it")
     p.add_argument("--serve-requests", type=int, default=60,
                    help="serve_cfg5: requests in the Poisson stream")
+    p.add_argument("--serve-compare-priority", action="store_true",
+                   help="serve_cfg5: also serve the FP32 stream with one stream priority for "
+                        "every slot, for comparison")
     p.add_argument("--serve-seconds", type=float, default=60.0,
                    help="serve_cfg5: wall-time cap of each form's run (unfinished work is "
                         "counted by completed cycles)")
@@ -1294,19 +1297,25 @@ def serve_main(args, device, rank, world):
 
     import synth
     from paper_2308_03310_gb300 import letkf as L
-    from paper_2308_03310_gb300.serve import GpuSlot, Request, Server, gpu_footprint
+    from paper_2308_03310_gb300.serve import (GpuSlot, Request, Server, gpu_footprint,
+                                              stream_priority)
 
     free, _ = torch.cuda.mem_get_info(device)
     budget = int(min(args.serve_budget_gb * 1e9, 0.85 * free))
     base = synth.poisson_requests(args.serve_requests, 20.0, 20230803 + 7919 * rank)
     out = {}
-    for name, prec in (("fp32", L.LETKF_FP32), ("mixed", L.LETKF_MIXED)):
-        # the eigensolve schedule is pinned by grid size (what the autotuner picks), so that no
-        # admission pays for timing it under load
+    forms = [("fp32", L.LETKF_FP32, True), ("mixed", L.LETKF_MIXED, True)]
+    if args.serve_compare_priority:
+        forms.append(("fp32_one_priority", L.LETKF_FP32, False))
+    for name, prec, prio in forms:
+        # the eigensolve schedule is pinned by ensemble and grid size (what the autotuner
+        # picks), so that no admission pays for timing it under load
         reqs = [Request(**d, steps_per_cycle=25, precision=prec,
-                        eig_schedule=(L.LETKF_EIG_SPLIT if d["nx"] * d["ny"] >= 16384
+                        eig_schedule=(L.LETKF_EIG_CHEBYSHEV if d["k"] <= 64
+                                      else L.LETKF_EIG_SPLIT if d["nx"] * d["ny"] >= 16384
                                       else L.LETKF_EIG_FUSED)) for d in base]
-        srv = Server(budget, lambda r: GpuSlot(r, device), gpu_footprint,
+        srv = Server(budget, (lambda r: GpuSlot(r, device, priority=stream_priority(r)))
+                     if prio else (lambda r: GpuSlot(r, device)), gpu_footprint,
                      max_active=args.serve_max_active)
         torch.cuda.synchronize(device)
         barrier()
@@ -1319,6 +1328,9 @@ def serve_main(args, device, rank, world):
             "admitted_requests": sum(1 for e in rep["timeline"] if e[1] == "admit"),
             "cycles": rep["cycles"], "p50_cycle_ms": rep["latency_ms"]["p50"],
             "p99_cycle_ms": rep["latency_ms"]["p99"],
+            "cycle_ms_by_class": rep["latency_ms"]["by_class"],
+            "stream_priorities": "small cycles (<= 256^2 x 64 point-members) on the most urgent "
+                                 "stream priority" if prio else "one priority for every slot",
             "admission_wait_s": rep["admission_wait_s"], "max_concurrent": rep["max_concurrent"],
             "peak_footprint_gb": rep["peak_footprint_bytes"] / 1e9,
             "unfinished_requests": rep["unfinished"], "errors": rep["errors"][:3],
@@ -1341,6 +1353,8 @@ def serve_main(args, device, rank, world):
         "p50_cycle_ms": head["p50_cycle_ms"], "p99_cycle_ms": head["p99_cycle_ms"],
         "serving": head, "mixed": dict(out["mixed"],
                                        speedup_vs_fp32=out["mixed"]["value"] / head["value"]),
+        **({"fp32_one_priority": out["fp32_one_priority"]}
+           if "fp32_one_priority" in out else {}),
     }
     if rank == 0:
         print(json.dumps(line))

@@ -14,9 +14,16 @@ nature run (an auxiliary member) advance by the cycle's LBM steps; the nature ru
 ensemble assimilates the observations.  All of it is enqueued asynchronously on the slot's
 stream; the host only polls completion events.
 
+Latency policy: a request whose cycle is small (grid points x members at most SMALL_WORK) gets
+a high-priority CUDA stream, the others the default priority, so that the device schedules the
+pending blocks of small cycles ahead of those of large ones: a 128^2, k = 16 cycle does not
+queue behind the blocks of a 1024^2, k = 128 analysis.  Priorities change the order in which
+blocks start, never the arithmetic.
+
 Reported: throughput (grid-point analyses per second of wall time), per-cycle latency (device
 time from a cycle's start to its end on its stream, which includes waiting for the other
-slots' work) p50 / p99, queueing delay of admissions, peak footprint and concurrency.
+slots' work) p50 / p99, overall and per size class, queueing delay of admissions, peak
+footprint and concurrency.
 
 A request's results depend only on its own inputs and seed: alone or in a mix, the same
 arithmetic runs on its stream (the eigensolve schedule that AUTO picks is fixed per process
@@ -31,7 +38,11 @@ import numpy as np
 
 from . import letkf as L
 
-__all__ = ["Request", "Server", "GpuSlot", "percentile"]
+__all__ = ["Request", "Server", "GpuSlot", "percentile", "size_class", "stream_priority",
+           "SMALL_WORK"]
+
+# grid points x members of the largest "small" cycle (256^2 x 64)
+SMALL_WORK = 256 * 256 * 64
 
 
 @dataclasses.dataclass
@@ -59,6 +70,17 @@ class Request:
         return self.nx * self.ny
 
 
+def size_class(req) -> str:
+    """'small' for a cycle of at most SMALL_WORK grid points x members, else 'large'."""
+    return "small" if req.nx * req.ny * req.k <= SMALL_WORK else "large"
+
+
+def stream_priority(req) -> int:
+    """CUDA stream priority of a request's slot (lower is more urgent): the most urgent for
+    small cycles, the default for large ones.  Out-of-range values map to the device's range."""
+    return -8 if size_class(req) == "small" else 0
+
+
 def percentile(values, q):
     v = np.sort(np.asarray(values, dtype=np.float64))
     if v.size == 0:
@@ -69,11 +91,14 @@ def percentile(values, q):
 class GpuSlot:
     """A running request: handle, stream, resident state, observation buffers, events."""
 
-    def __init__(self, req: Request, device, keep_state=False):
+    def __init__(self, req: Request, device, keep_state=False, priority=None):
         import torch
         self.torch = torch
         self.req = req
         self.device = torch.device(device)
+        stream = None
+        if priority is not None:
+            stream = torch.cuda.Stream(device=self.device, priority=int(priority))
         nx, ny, k = req.nx, req.ny, req.k
         xs = np.arange(0, nx, req.obs_stride, dtype=np.int32)
         ys = np.arange(0, ny, req.obs_stride, dtype=np.int32)
@@ -83,7 +108,8 @@ class GpuSlot:
         var = np.full(self.LV, req.obs_sigma ** 2, dtype=np.float32)
         self.exp = L.Experiment(nx, ny, k, req.tau, net, var, n_aux=1,
                                 loc_radius=req.loc_radius, precision=req.precision,
-                                eig_schedule=req.eig_schedule, device=self.device)
+                                eig_schedule=req.eig_schedule, device=self.device,
+                                stream=stream)
         self.stream = self.exp.stream
         self.gen = torch.Generator(device=self.device)
         self.gen.manual_seed(int(req.seed))
@@ -257,6 +283,12 @@ class Server:
                 errors.append(str(err))
         lat = [x for s in done for x in s.latencies_ms] + \
               [x for s, _ in active for x in s.latencies_ms]
+        by_class = {}
+        for cls in ("small", "large"):
+            cl = [x for s in done if size_class(s.req) == cls for x in s.latencies_ms] + \
+                 [x for s, _ in active if size_class(s.req) == cls for x in s.latencies_ms]
+            by_class[cls] = {"cycles": len(cl), "p50": percentile(cl, 50),
+                             "p99": percentile(cl, 99)}
         return {
             "requests": len(requests),
             "completed": len(done),
@@ -265,7 +297,8 @@ class Server:
             "wall_s": wall,
             "analyses_per_s": analyses / wall if wall > 0 else float("nan"),
             "latency_ms": {"p50": percentile(lat, 50), "p99": percentile(lat, 99),
-                           "mean": float(np.mean(lat)) if lat else float("nan")},
+                           "mean": float(np.mean(lat)) if lat else float("nan"),
+                           "by_class": by_class},
             "admission_wait_s": {"p50": percentile(waits, 50), "p99": percentile(waits, 99),
                                  "max": float(max(waits)) if waits else 0.0},
             "budget_bytes": self.budget,

@@ -103,3 +103,25 @@ def test_poisson_stream_is_seeded_and_ordered():
     assert t == sorted(t) and 1.0 < t[-1] < 5.0          # ~2.5 s for 50 arrivals at 20/s
     assert {r["nx"] for r in a} <= {128, 256, 512, 1024}
     assert all(10 <= r["cycles"] <= 100 for r in a)
+
+
+def test_small_cycles_get_the_urgent_stream_priority():
+    from paper_2308_03310_gb300.serve import SMALL_WORK, size_class, stream_priority
+    small = Request(rid=0, arrival_s=0.0, nx=256, ny=256, k=64, obs_stride=4, cycles=1)
+    large = Request(rid=1, arrival_s=0.0, nx=1024, ny=1024, k=16, obs_stride=4, cycles=1)
+    tiny = Request(rid=2, arrival_s=0.0, nx=128, ny=128, k=128, obs_stride=8, cycles=1)
+    assert 256 * 256 * 64 == SMALL_WORK
+    assert [size_class(r) for r in (small, large, tiny)] == ["small", "large", "small"]
+    assert stream_priority(small) < stream_priority(large) == 0
+
+
+def test_latency_is_reported_per_size_class():
+    reqs = [Request(rid=i, arrival_s=0.0, nx=n, ny=n, k=16, obs_stride=4, cycles=2)
+            for i, n in enumerate([64, 1024, 128])]
+    clock = Clock()
+    srv = Server(10 ** 12, lambda r: FakeSlot(r, clock), lambda r: 1, clock=clock,
+                       sleep=clock.sleep)
+    rep = srv.run(reqs)
+    by = rep["latency_ms"]["by_class"]
+    assert by["small"]["cycles"] == 4 and by["large"]["cycles"] == 2
+    assert by["small"]["p99"] == by["small"]["p99"] and by["large"]["p50"] > 0
