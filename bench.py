@@ -221,6 +221,7 @@ def measured_peaks():
 
 EIG_SCHEDULES = {"auto": 0, "fused": 1, "split": 2, "rational": 4, "chebyshev": 5}
 EIG_NAMES = {1: "fused", 2: "split", 3: "split_check", 4: "rational", 5: "chebyshev"}
+GRAM_NAMES = {0: "auto", 1: "pipe", 2: "team", 3: "tensor"}
 PEAK_NAMES = {"hbm": "hbm_gbs", "alu": "FP32 FMA peak from the unit counts at max SM clock",
               "tensor": "bf16_tflops_sustained (FP16 operands, same nominal rate)"}
 
@@ -784,6 +785,7 @@ def main(argv=None):
         "p50_cycle_ms": head["p50_cycle_ms"], "p99_cycle_ms": head["p99_cycle_ms"],
         "roofline": head["roofline"], "kernels": head["kernels"], "e2e": head["e2e"],
         "gpu_launches": head["gpu_launches"], "eig_schedule": head["eig_schedule"],
+        "gram_tile": head["gram_tile"],
         "chunks_per_analysis": head["chunks_per_analysis"],
         "lbm": head["lbm"],
         "clocks": head["clocks"],
@@ -797,7 +799,7 @@ def main(argv=None):
         mx = results[1]
         line["mixed"] = {k: mx[k] for k in ("precision", "value", "ms_per_step", "p50_cycle_ms",
                                              "p99_cycle_ms", "e2e", "gpu_launches", "eig_schedule",
-                                             "clocks")}
+                                             "gram_tile", "clocks")}
         line["mixed"]["kernels"] = {n: {"ms_per_cycle": d["ms_per_cycle"], "frac": d["frac"],
                                          "unit": d["unit"]} for n, d in mx["kernels"].items()}
         line["mixed"]["speedup_vs_fp32"] = mx["value"] / head["value"]
@@ -1557,6 +1559,7 @@ def measure(w, members, setup, yos, device, precision, steps, warm, world, eig_s
                 "d2h_bytes_per_step": exp.nmem * LV * 4},
         "gpu_launches": cycle_kernels * steps,
         "eig_schedule": EIG_NAMES.get(st_end.eig_schedule, str(st_end.eig_schedule)),
+        "gram_tile": GRAM_NAMES.get(st_end.gram_tile, str(st_end.gram_tile)),
         "chunks_per_analysis": st_end.n_chunks,
         "lbm": lbm_rates(w, ms["lbm_step"], peaks),
         "clocks": clocks,

@@ -104,6 +104,19 @@ extern "C" {
                                     against the observation error).  A probe's eigenvalues come
                                     from a tridiagonalization and an eigenvalue-only QL.      */
 
+/* FP32 Gram tile schedules for k >= 17 (letkf_config.gram_tile; k <= 16 has one schedule and
+ * LETKF_MIXED uses the tensor cores for k >= 17, so the choice applies to LETKF_FP32 only). */
+#define LETKF_GRAM_AUTO   0  /* the handle times both on its first analysis' first chunk and
+                                keeps the faster; cached per problem shape for the process,
+                                so handles of the same shape run the same arithmetic        */
+#define LETKF_GRAM_PIPE   1  /* one CTA per SM over 7 x 2 points (k <= 64; 8 x 6 for k <= 32,
+                                3 x 1 for k <= 128), per-point compacted entries, operands
+                                double-buffered by cp.async                                */
+#define LETKF_GRAM_TEAM   2  /* two CTAs per SM over 4 x 2 points (k <= 64; 8 x 4, 2 x 1), the
+                                weights of a chunk in shared memory, a weight test per
+                                candidate in the multiply-add loop                         */
+#define LETKF_GRAM_TENSOR 3  /* (reported only) the tensor-core Gram of LETKF_MIXED          */
+
 /* ---- problem statement --------------------------------------------------
  * Follows the paper's statement of the problem (Sec. II-B): the grid, the
  * ensemble size M (= k), the observation operator H (observation points and
@@ -129,6 +142,7 @@ typedef struct letkf_config {
                                   1 = none (the paper's Eq. letkf_q)                    */
     int32_t precision;         /* LETKF_FP32 or LETKF_MIXED                             */
     int32_t eig_schedule;      /* LETKF_EIG_*; 0 (AUTO) lets the handle choose          */
+    int32_t gram_tile;         /* LETKF_GRAM_*; 0 (AUTO) lets the handle choose         */
     int64_t chunk_bytes;       /* device bytes for the per-point k x k Gram buffer;
                                   0 = default (1 GiB; larger chunks give the
                                   thread-per-matrix QL kernel more matrices per launch) */
@@ -150,6 +164,8 @@ typedef struct letkf_stats {
     int32_t cycle_kernels;     /* kernel launches of the most recent letkf_cycle (or group
                                   cycle led by this handle): the kernel nodes of its
                                   captured graph; 0 before the first cycle               */
+    int32_t gram_tile;         /* LETKF_GRAM_PIPE / TEAM / TENSOR in use; AUTO (0) until the
+                                  first analysis resolves it                             */
 } letkf_stats;
 
 /* Device time of the phases of the most recent forecast and analysis (milliseconds, CUDA

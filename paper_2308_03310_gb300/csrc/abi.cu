@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <atomic>
 #include <map>
+#include <numeric>
 #include <mutex>
 #include <new>
 #include <utility>
@@ -74,6 +75,7 @@ int validate(const letkf_config *c) {
         return LETKF_EINVAL;
     if (c->eig_schedule == LETKF_EIG_RATIONAL && c->k > lk::kRationalMaxK) return LETKF_EINVAL;
     if (c->eig_schedule == LETKF_EIG_CHEBYSHEV && c->k > lk::kChebMaxK) return LETKF_EINVAL;
+    if (c->gram_tile < LETKF_GRAM_AUTO || c->gram_tile > LETKF_GRAM_TEAM) return LETKF_EINVAL;
     if (c->chunk_bytes < 0) return LETKF_EINVAL;
     const int V = popcount3(c->obs_vars);
     for (int l = 0; l < c->n_obs; ++l) {
@@ -95,8 +97,10 @@ int make_plan(const letkf_config *c, Plan *p) {
     p->V = popcount3(c->obs_vars);
     p->LV = c->n_obs * p->V;
     p->kp = kp_of(c->k);
-    p->tile_w = lk::gram_tile_width(p->kp);
-    p->tile_h = lk::gram_tile_height(p->kp);
+    // the bins must hold the patch of either FP32 tile schedule, and a chunk holds whole tiles
+    // of both
+    p->tile_w = std::max(lk::gram_tile_width(p->kp, 0), lk::gram_tile_width(p->kp, 1));
+    p->tile_h = std::lcm(lk::gram_tile_height(p->kp, 0), lk::gram_tile_height(p->kp, 1));
     // (the tensor-core kernel's records pack a point as x | y << 16 and a scalar's row with
     // its variable in bits 28..29)
     p->tensor_gram = c->precision == LETKF_MIXED && p->kp >= 32 && c->nx < 65536 &&
@@ -227,6 +231,7 @@ struct letkf_handle {
     int eig_schedule = LETKF_EIG_FUSED;  // resolved: FUSED, SPLIT, SPLIT_CHECK or RATIONAL
     int rat_grid = 0;                    // resident grid of the EVD-free transform kernel
     int cheb_grid = 0;                   // resident grid of the Chebyshev transform kernel
+    int gram_tile = LETKF_GRAM_PIPE;     // resolved: PIPE, TEAM or TENSOR; AUTO until tuned
     int tc_ctas = 0;
     letkf_stats stats;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -381,6 +386,7 @@ lk::GramArgs gram_args(letkf_handle *h, int y0, int y1) {
     g.cvec = h->cvec;
     g.nloc = h->nloc;
     g.orec = h->orec;
+    g.team = h->gram_tile == LETKF_GRAM_TEAM ? 1 : 0;
     return g;
 }
 
@@ -545,6 +551,72 @@ int tune_eig_schedule(letkf_handle *h, int y0, int y1) {
     return LETKF_OK;
 }
 
+// ---- AUTO FP32 Gram tile schedule (k >= 17) ---------------------------------------------
+// The first analysis times both tile schedules on its first chunk (each twice after a warm-up
+// run, the better of the two) and keeps the faster; the kept schedule runs last, so the chunk's
+// Gram matrices, c and local counts are its own.  The pick is cached for the process per
+// problem shape (device, kp, grid, chunk, observation network size and localization), so that
+// handles of one shape run the same arithmetic.
+
+struct GramTuneCache {
+    std::mutex mu;
+    std::map<std::vector<long long>, int> pick;
+};
+
+GramTuneCache &gram_tune_cache() {
+    static GramTuneCache c;
+    return c;
+}
+
+std::vector<long long> gram_tune_key(const letkf_handle *h) {
+    return {h->device,   h->plan.kp,   h->cfg.nx,    h->cfg.ny,      h->plan.chunk_rows,
+            h->plan.V,   h->plan.d2max, h->cfg.n_obs, h->cfg.loc_kind};
+}
+
+int cached_gram_tile(const letkf_handle *h) {
+    GramTuneCache &c = gram_tune_cache();
+    std::lock_guard<std::mutex> lock(c.mu);
+    const auto it = c.pick.find(gram_tune_key(h));
+    return it == c.pick.end() ? LETKF_GRAM_AUTO : it->second;
+}
+
+int tune_gram_tile(letkf_handle *h, int chunk, int y0, int y1) {
+    const int cached = cached_gram_tile(h);
+    if (cached != LETKF_GRAM_AUTO) {
+        h->gram_tile = h->stats.gram_tile = cached;
+        return enqueue_gram_chunk(h, chunk, y0, y1);
+    }
+    const int cand[2] = {LETKF_GRAM_TEAM, LETKF_GRAM_PIPE};   // the last one timed runs last
+    float best[2] = {0.0f, 0.0f};
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaError_t err = cudaEventCreate(&t0);
+    if (err == cudaSuccess) err = cudaEventCreate(&t1);
+    int rc = LETKF_OK;
+    for (int rep = 0; rep < 3 && err == cudaSuccess && !rc; ++rep)
+        for (int i = 0; i < 2 && err == cudaSuccess && !rc; ++i) {
+            h->gram_tile = cand[i];
+            err = cudaEventRecord(t0, h->stream);
+            if (err == cudaSuccess) rc = enqueue_gram_chunk(h, chunk, y0, y1);
+            if (err == cudaSuccess && !rc) err = cudaEventRecord(t1, h->stream);
+            if (err == cudaSuccess && !rc) err = cudaEventSynchronize(t1);
+            float ms = 0.0f;
+            if (err == cudaSuccess && !rc) err = cudaEventElapsedTime(&ms, t0, t1);
+            if (rep > 0 && (rep == 1 || ms < best[i])) best[i] = ms;   // run 0 warms up
+        }
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (rc) return rc;
+    if (err != cudaSuccess) return cuda_fail(h, err);
+    int pick = best[0] < best[1] ? cand[0] : cand[1];
+    {
+        GramTuneCache &c = gram_tune_cache();
+        std::lock_guard<std::mutex> lock(c.mu);
+        pick = c.pick.emplace(gram_tune_key(h), pick).first->second;  // the first pick wins
+    }
+    h->gram_tile = h->stats.gram_tile = pick;
+    return pick == cand[1] ? LETKF_OK : enqueue_gram_chunk(h, chunk, y0, y1);
+}
+
 int enqueue_analysis(letkf_handle *h, letkf_probe *probe) {
     const Plan &p = h->plan;
     const letkf_config &c = h->cfg;
@@ -563,7 +635,9 @@ int enqueue_analysis(letkf_handle *h, letkf_probe *probe) {
                                cudaMemcpyDeviceToHost, h->stream));
     for (int y0 = 0; y0 < c.ny; y0 += p.chunk_rows) {
         const int y1 = std::min(c.ny, y0 + p.chunk_rows);
-        if ((rc = enqueue_gram_chunk(h, chunk, y0, y1))) return rc;
+        rc = h->gram_tile == LETKF_GRAM_AUTO ? tune_gram_tile(h, chunk, y0, y1)
+                                             : enqueue_gram_chunk(h, chunk, y0, y1);
+        if (rc) return rc;
         if ((rc = mark(h, 5 + 2 * chunk))) return rc;
         const long long pt0 = (long long)y0 * c.nx;
         const int npts = (y1 - y0) * c.nx;
@@ -726,7 +800,9 @@ int enqueue_group(letkf_handle *const *hs, int n, int nsteps) {
             if (y0 >= g->cfg.ny) continue;
             const int y1 = std::min(g->cfg.ny, y0 + g->plan.chunk_rows);
             OnBranch b(g);
-            if ((rc = enqueue_gram_chunk(g, r, y0, y1))) return rc;
+            rc = g->gram_tile == LETKF_GRAM_AUTO ? tune_gram_tile(g, r, y0, y1)
+                                                 : enqueue_gram_chunk(g, r, y0, y1);
+            if (rc) return rc;
             if (g->eig_schedule == LETKF_EIG_AUTO && (rc = tune_eig_schedule(g, y0, y1)))
                 return rc;
             if (g->eig_schedule == LETKF_EIG_FUSED) {
@@ -987,6 +1063,14 @@ int letkf_init(const letkf_config *cfg, void *workspace, size_t workspace_bytes,
     h->eig_schedule =
         plan.eig_schedule == LETKF_EIG_AUTO ? cached_eig_schedule(h) : plan.eig_schedule;
     h->stats.eig_schedule = h->eig_schedule;
+    // the Gram: tensor cores (mixed), the one team schedule (k <= 16), else as configured
+    if (plan.tensor_gram)
+        h->gram_tile = LETKF_GRAM_TENSOR;
+    else if (plan.kp <= 16)
+        h->gram_tile = LETKF_GRAM_TEAM;
+    else
+        h->gram_tile = cfg->gram_tile == LETKF_GRAM_AUTO ? cached_gram_tile(h) : cfg->gram_tile;
+    h->stats.gram_tile = h->gram_tile;
     *out = h;
     return LETKF_OK;
 }
@@ -1217,7 +1301,8 @@ int letkf_cycle(letkf_handle *h, int32_t nsteps, const float *yo, int32_t where)
     int rc = device_check(h);
     if (rc) return rc;
     if ((rc = copy_in(h, h->yo, yo, (size_t)h->plan.LV * sizeof(float), where))) return rc;
-    if (h->eig_schedule == LETKF_EIG_AUTO) {  // the first analysis times the schedules: eager
+    if (h->eig_schedule == LETKF_EIG_AUTO || h->gram_tile == LETKF_GRAM_AUTO) {
+        // the first analysis times the schedules: eager
         rc = enqueue_forecast(h, nsteps);
         return rc ? rc : enqueue_analysis(h, nullptr);
     }
@@ -1286,8 +1371,10 @@ int letkf_group_cycle(letkf_handle *const *hs, int32_t n, int32_t nsteps, const 
         for (int i = 0; i < n && !rc; ++i)
             rc = copy_in(hs[i], hs[i]->yo, yo[i], (size_t)hs[i]->plan.LV * sizeof(float), where);
         if (rc) return rc;
-        bool pending = false;  // a handle still picks its eigensolve schedule: no capture
-        for (int i = 0; i < n; ++i) pending |= hs[i]->eig_schedule == LETKF_EIG_AUTO;
+        bool pending = false;  // a handle still picks a schedule: no capture
+        for (int i = 0; i < n; ++i)
+            pending |= hs[i]->eig_schedule == LETKF_EIG_AUTO ||
+                       hs[i]->gram_tile == LETKF_GRAM_AUTO;
         if (pending) {
             if ((rc = enqueue_group(hs, n, nsteps))) return rc;
             h->stats.cycle_kernels = 0;

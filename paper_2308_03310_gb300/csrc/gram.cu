@@ -539,20 +539,35 @@ cudaError_t launch_pipe(const GramArgs &a, cudaStream_t s) {
 
 }  // namespace
 
-// k <= 16: the team kernel (KP = 8, 16); k >= 17: the pipelined kernel (KP = 32, 64, 128)
-int gram_tile_height(int kp) {
+// k <= 16: the team kernel (KP = 8, 16); k >= 17: the pipelined kernel (KP = 32, 64, 128) or,
+// on request (team = 1), the team kernel
+int gram_tile_height(int kp, int team) {
+    if (kp <= 16 || team) {
+        switch (kp) {
+            case 8: return GramShape<8>::TH;
+            case 16: return GramShape<16>::TH;
+            case 32: return GramShape<32>::TH;
+            case 64: return GramShape<64>::TH;
+            default: return GramShape<128>::TH;
+        }
+    }
     switch (kp) {
-        case 8: return GramShape<8>::TH;
-        case 16: return GramShape<16>::TH;
         case 32: return PipeShape<32>::TH;
         case 64: return PipeShape<64>::TH;
         default: return PipeShape<128>::TH;
     }
 }
-int gram_tile_width(int kp) {
+int gram_tile_width(int kp, int team) {
+    if (kp <= 16 || team) {
+        switch (kp) {
+            case 8: return GramShape<8>::TW;
+            case 16: return GramShape<16>::TW;
+            case 32: return GramShape<32>::TW;
+            case 64: return GramShape<64>::TW;
+            default: return GramShape<128>::TW;
+        }
+    }
     switch (kp) {
-        case 8: return GramShape<8>::TW;
-        case 16: return GramShape<16>::TW;
         case 32: return PipeShape<32>::TW;
         case 64: return PipeShape<64>::TW;
         default: return PipeShape<128>::TW;
@@ -561,12 +576,13 @@ int gram_tile_width(int kp) {
 int gram_max_cells() { return kMaxPatchCells; }
 
 cudaError_t gram_prepare(int kp) {
+    cudaError_t e = cudaSuccess;
     switch (kp) {
         case 8: return prepare_kp<8>();
         case 16: return prepare_kp<16>();
-        case 32: return prepare_pipe<32>();
-        case 64: return prepare_pipe<64>();
-        case 128: return prepare_pipe<128>();
+        case 32: e = prepare_kp<32>(); return e == cudaSuccess ? prepare_pipe<32>() : e;
+        case 64: e = prepare_kp<64>(); return e == cudaSuccess ? prepare_pipe<64>() : e;
+        case 128: e = prepare_kp<128>(); return e == cudaSuccess ? prepare_pipe<128>() : e;
         default: return cudaErrorInvalidValue;
     }
 }
@@ -576,9 +592,9 @@ cudaError_t launch_gram(const GramArgs &a, cudaStream_t s) {
     switch (a.kp) {
         case 8: return launch_kp<8>(a, s);
         case 16: return launch_kp<16>(a, s);
-        case 32: return launch_pipe<32>(a, s);
-        case 64: return launch_pipe<64>(a, s);
-        case 128: return launch_pipe<128>(a, s);
+        case 32: return a.team ? launch_kp<32>(a, s) : launch_pipe<32>(a, s);
+        case 64: return a.team ? launch_kp<64>(a, s) : launch_pipe<64>(a, s);
+        case 128: return a.team ? launch_kp<128>(a, s) : launch_pipe<128>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }

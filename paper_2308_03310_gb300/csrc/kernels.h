@@ -75,6 +75,7 @@ struct GramArgs {
     float *gram;            // [(y_end-y_begin)*nx][k][k]
     float *cvec;            // [(y_end-y_begin)*nx][k]
     int *nloc;              // [(y_end-y_begin)*nx]
+    int team = 0;           // FP32, kp >= 32: 1 the team kernel, 0 the pipelined one
 };
 cudaError_t gram_prepare(int kp);            // once per process and kp
 // tensor-core (tcgen05) split-FP16 form for kp = 64 or 128; persistent, <= max_ctas CTAs
@@ -85,8 +86,9 @@ cudaError_t launch_obs_records(const GramArgs &a, float4 *rec, cudaStream_t s);
 int gram_tc_tile_width(int kp);
 int gram_tc_tile_height(int kp);
 cudaError_t launch_gram(const GramArgs &a, cudaStream_t s);
-int gram_tile_width(int kp);
-int gram_tile_height(int kp);
+// tile of the FP32 Gram: the team kernel (team = 1, and every kp <= 16) or the pipelined one
+int gram_tile_width(int kp, int team);
+int gram_tile_height(int kp, int team);
 int gram_max_cells();
 
 // ---- eigen.cu -----------------------------------------------------------------

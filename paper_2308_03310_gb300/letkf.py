@@ -42,6 +42,10 @@ LETKF_EIG_SPLIT = 2
 LETKF_EIG_SPLIT_CHECK = 3
 LETKF_EIG_RATIONAL = 4
 LETKF_EIG_CHEBYSHEV = 5
+LETKF_GRAM_AUTO = 0
+LETKF_GRAM_PIPE = 1
+LETKF_GRAM_TEAM = 2
+LETKF_GRAM_TENSOR = 3
 
 # Every symbol include/letkf.h declares, in declaration order.
 EXPORTED = (
@@ -65,7 +69,8 @@ class letkf_config(C.Structure):
         ("n_obs", C.c_int32), ("obs_xy", C.POINTER(C.c_int32)), ("obs_vars", C.c_int32),
         ("obs_err_var", C.POINTER(C.c_float)), ("loc_kind", C.c_int32),
         ("loc_radius", C.c_float), ("loc_cutoff2", C.c_float), ("infl", C.c_float),
-        ("precision", C.c_int32), ("eig_schedule", C.c_int32), ("chunk_bytes", C.c_int64),
+        ("precision", C.c_int32), ("eig_schedule", C.c_int32), ("gram_tile", C.c_int32),
+        ("chunk_bytes", C.c_int64),
         ("stream", C.c_void_p),
     ]
 
@@ -74,7 +79,7 @@ class letkf_stats(C.Structure):
     _fields_ = [("status", C.c_int32), ("n_points", C.c_int32), ("n_zero_obs", C.c_int32),
                 ("max_local_obs", C.c_int32), ("mean_local_obs", C.c_double),
                 ("n_chunks", C.c_int32), ("eig_schedule", C.c_int32), ("cuda_error", C.c_int32),
-                ("cycle_kernels", C.c_int32)]
+                ("cycle_kernels", C.c_int32), ("gram_tile", C.c_int32)]
 
 
 class letkf_timings(C.Structure):
@@ -373,13 +378,15 @@ class Experiment:
     force, n_aux, infl      [2][ny][nx] body force, auxiliary members (never analysed, e.g. a
                             nature run), multiplicative inflation
     precision, eig_schedule LETKF_FP32 / LETKF_MIXED, LETKF_EIG_*
+    gram_tile               LETKF_GRAM_* (FP32 Gram tile schedule for k >= 17; AUTO tunes)
     chunk_bytes, stream, device   Gram chunk budget (0: library default), torch stream, device
     """
 
     def __init__(self, nx, ny, k, tau, obs_xy, obs_err_var, obs_vars=LETKF_OBS_U | LETKF_OBS_V,
                  loc_radius=None, loc_cutoff2=0.0, force=None, n_aux=0, infl=1.0,
                  precision=LETKF_FP32, chunk_bytes=0, stream=None, device=None,
-                 eig_schedule=LETKF_EIG_AUTO, loc_kind=LETKF_LOC_GAUSS):
+                 eig_schedule=LETKF_EIG_AUTO, loc_kind=LETKF_LOC_GAUSS,
+                 gram_tile=LETKF_GRAM_AUTO):
         import torch
         self.torch = torch
         self.device = torch.device(device if device is not None else "cuda")
@@ -408,6 +415,7 @@ class Experiment:
         cfg.infl = float(infl)
         cfg.precision = int(precision)
         cfg.eig_schedule = int(eig_schedule)
+        cfg.gram_tile = int(gram_tile)
         cfg.chunk_bytes = int(chunk_bytes)
         cfg.stream = self.stream.cuda_stream
         self.cfg = cfg
