@@ -175,14 +175,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
 // Square root of the localization weight of an observation at (ox, oy) seen from grid point
 // (qx, qy): the Gaussian's exp(-d^2 / (4 r^2)) directly, or sqrt(GC(d / c)); 0 beyond the
 // cutoff.
+__device__ __forceinline__ float weight_sqrt_d2(const ObsNet &net, int d2) {
+    return net.loc_gc ? sqrtf(fmaxf(gaspari_cohn(sqrtf((float)d2) * net.inv_c), 0.0f))
+                      : __expf(-0.5f * (float)d2 * net.inv2r2);
+}
+// wtab: the same function tabulated for d2 = 0 .. d2max in shared memory (tab_n = d2max + 1
+// entries), or tab_n = 0
 __device__ __forceinline__ float loc_weight_sqrt(const ObsNet &net, int ox, int oy, int qx,
-                                                 int qy, int nx, int ny) {
+                                                 int qy, int nx, int ny, const float *wtab,
+                                                 int tab_n) {
     if (net.loc_none) return 1.0f;
     const int dx = min_image(ox - qx, nx), dy = min_image(oy - qy, ny);
     const int d2 = dx * dx + dy * dy;
     if (d2 > net.d2max) return 0.0f;
-    return net.loc_gc ? sqrtf(fmaxf(gaspari_cohn(sqrtf((float)d2) * net.inv_c), 0.0f))
-                      : __expf(-0.5f * (float)d2 * net.inv2r2);
+    return tab_n ? wtab[d2] : weight_sqrt_d2(net, d2);
 }
 
 // A_p row `row` (accumulator values v[0..31] for columns c0..c0+31) to global memory.
@@ -201,7 +207,8 @@ __device__ __forceinline__ void store_row32(float *dst, const float *v, int c0, 
 }
 
 template <int KP>
-__global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int *status) {
+__global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int *status,
+                                                                 int tab_n) {
     using S = TcShape<KP>;
     constexpr int P = S::P, TW = S::TW, TH = S::TH, KC = S::KC, SEG = S::SEG;
     constexpr int NOP = S::NOP, NY = S::NY;
@@ -227,6 +234,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int 
     float *ystage = reinterpret_cast<float *>(dyn + S::OFF_Y);
     float *E = reinterpret_cast<float *>(dyn + S::OFF_E);
     float *cred = reinterpret_cast<float *>(dyn + S::OFF_CRED);
+    float *wtab = reinterpret_cast<float *>(dyn + S::SMEM);   // tab_n localization weights
 
     // ---- set-up: barriers, tensor memory, finite contents for every staged value
     if (tid == 0) {
@@ -254,6 +262,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int 
     }
     for (int i = tid; i < (S::OFF_E - S::OFF_Y) / 4; i += kTcThreads)
         reinterpret_cast<float *>(dyn + S::OFF_Y)[i] = 0.0f;
+    for (int i = tid; i < tab_n; i += kTcThreads) wtab[i] = weight_sqrt_d2(net, i);
     if (warp == kWarpMma) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_base)),
@@ -375,7 +384,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int 
                         const int qx = tx0 + p % TW, qy = ty0 + p / TW;
                         float w = 0.0f;
                         if (in && qx < a.nx && qy < a.y_end)
-                            w = loc_weight_sqrt(net, ox, oy, qx, qy, a.nx, a.ny);
+                            w = loc_weight_sqrt(net, ox, oy, qx, qy, a.nx, a.ny, wtab, tab_n);
                         keep |= w != 0.0f;
                         if (w != 0.0f && first_var) ++cnt_p[p];
                         sw[p] = w * r.z;
@@ -779,17 +788,28 @@ int gram_tc_tile_height(int kp) {
     return kp == 32 ? TcShape<32>::TH : kp == 64 ? TcShape<64>::TH : TcShape<128>::TH;
 }
 
+// dynamic shared memory a CTA may use: the kernel's buffers plus the weight table
+constexpr int kTcDynMax = 227 * 1024 - 1024;
+
+// entries of the localization-weight table for the launch (d2max + 1 where it fits beside
+// the buffers, else 0: the weights are then evaluated per candidate)
+template <int KP>
+int wtab_entries(const GramArgs &a) {
+    if (a.net.loc_none || a.net.d2max < 0) return 0;
+    const long long n = (long long)a.net.d2max + 1;
+    return (long long)TcShape<KP>::SMEM + 4 * n <= kTcDynMax ? (int)n : 0;
+}
+
 cudaError_t gram_tc_prepare(int kp) {
     if (kp == 32)
         return cudaFuncSetAttribute(gram_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    TcShape<32>::SMEM);
+                                    kTcDynMax);
     if (kp == 64)
         return cudaFuncSetAttribute(gram_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    TcShape<64>::SMEM);
+                                    kTcDynMax);
     if (kp == 128)
         return cudaFuncSetAttribute(gram_tc_kernel<128>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    TcShape<128>::SMEM);
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kTcDynMax);
     return cudaErrorInvalidValue;
 }
 
@@ -826,15 +846,18 @@ cudaError_t launch_gram_tc(const GramArgs &a, int *status, int max_ctas, cudaStr
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (a.kp == 32) {
-        cfg.dynamicSmemBytes = TcShape<32>::SMEM;
-        return cudaLaunchKernelEx(&cfg, gram_tc_kernel<32>, a, status);
+        const int n = wtab_entries<32>(a);
+        cfg.dynamicSmemBytes = TcShape<32>::SMEM + 4 * n;
+        return cudaLaunchKernelEx(&cfg, gram_tc_kernel<32>, a, status, n);
     }
     if (a.kp == 64) {
-        cfg.dynamicSmemBytes = TcShape<64>::SMEM;
-        return cudaLaunchKernelEx(&cfg, gram_tc_kernel<64>, a, status);
+        const int n = wtab_entries<64>(a);
+        cfg.dynamicSmemBytes = TcShape<64>::SMEM + 4 * n;
+        return cudaLaunchKernelEx(&cfg, gram_tc_kernel<64>, a, status, n);
     }
-    cfg.dynamicSmemBytes = TcShape<128>::SMEM;
-    return cudaLaunchKernelEx(&cfg, gram_tc_kernel<128>, a, status);
+    const int n = wtab_entries<128>(a);
+    cfg.dynamicSmemBytes = TcShape<128>::SMEM + 4 * n;
+    return cudaLaunchKernelEx(&cfg, gram_tc_kernel<128>, a, status, n);
 }
 
 }  // namespace lk
