@@ -202,21 +202,41 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(GramArgs a, int 
                 ++segc;
                 first = 0;
             };
-            // Ranges of records: one per (bin row, x range) of the patch, in that order.  32
-            // ranges at a time, every lane fetches one range's bounds; the slots of the batch
-            // are then walked as one flat list, 32 per step, with the next step's record
-            // fetched ahead.
+            // Ranges of records: two slots per bin row of the patch (its x ranges, the second
+            // empty unless the row's range wraps), in that order.  A bin row's x range spans the
+            // bins within the cutoff at the row's distance from the tile (a disk, not the
+            // bounding square: the dropped bins hold no local observation).  32 ranges at a
+            // time, every lane fetches one
+            // range's bounds; the slots of the batch are then walked as one flat list, 32 per
+            // step, with the next step's record fetched ahead.
             const int ly0 = ry.hi[0] - ry.lo[0] + 1;
             const int nyb = ly0 + (ry.n > 1 ? ry.hi[1] - ry.lo[1] + 1 : 0);
-            const int nr = nyb * rx.n;
+            const int nr = nyb * 2;
             for (int rb = 0; rb < nr && ok; rb += 32) {
                 int j0 = 0, cnt = 0;
                 if (rb + lane < nr) {
-                    const int yi = (rb + lane) / rx.n, xr = (rb + lane) - yi * rx.n;
+                    const int yi = (rb + lane) >> 1, xr = (rb + lane) & 1;
                     const int by = yi < ly0 ? ry.lo[0] + yi : ry.lo[1] + (yi - ly0);
-                    const int c0 = by * net.ncx + rx.lo[xr];
-                    j0 = __ldg(net.cell_start + c0) * V;
-                    cnt = __ldg(net.cell_start + c0 + (rx.hi[xr] - rx.lo[xr]) + 1) * V - j0;
+                    BinRanges rr = rx;
+                    if (!net.loc_none) {
+                        const int gy = axis_gap(by * net.cs, min((by + 1) * net.cs, a.ny) - 1,
+                                                ty0, ty0 + TH - 1, a.ny);
+                        const long long rem = (long long)net.d2max - (long long)gy * gy;
+                        if (rem < 0) {
+                            rr.n = 0;
+                        } else {
+                            long long w = (long long)sqrt((double)rem);
+                            while ((w + 1) * (w + 1) <= rem) ++w;
+                            while (w * w > rem) --w;
+                            rr = bin_ranges(tx0 - (int)w, tx0 + TW - 1 + (int)w, a.nx, net.cs);
+                        }
+                    }
+                    if (xr < rr.n) {
+                        const int blo = xr ? rr.lo[1] : rr.lo[0], bhi = xr ? rr.hi[1] : rr.hi[0];
+                        const int c0 = by * net.ncx + blo;
+                        j0 = __ldg(net.cell_start + c0) * V;
+                        cnt = __ldg(net.cell_start + c0 + (bhi - blo) + 1) * V - j0;
+                    }
                 }
                 int incl = cnt;
 #pragma unroll

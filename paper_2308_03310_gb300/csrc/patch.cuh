@@ -64,6 +64,16 @@ __device__ void block_exclusive_scan(int *s, int n, int *warp_tot) {
     __syncthreads();
 }
 
+// Least periodic distance (period n) between a point of [a0, a1] and a point of [b0, b1], both
+// intervals within [0, n) except that b1 may pass n - 1 at a ragged tile edge (which only
+// shortens the distance).
+__device__ __forceinline__ int axis_gap(int a0, int a1, int b0, int b1, int n) {
+    int g = max(0, max(a0 - b1, b0 - a1));
+    g = min(g, max(0, max(a0 + n - b1, b0 - a1 - n)));
+    g = min(g, max(0, max(a0 - n - b1, b0 - a1 + n)));
+    return g;
+}
+
 // Bins of the patch of the tile [tx0, tx0+TW) x [ty0, ty0+TH): cell_base[c] is the bin's
 // first entry in net.cell_obs, cell_pre the exclusive prefix of the bin sizes.  Returns the
 // number of bins; cell_pre[nc] holds the number of candidate observations.
