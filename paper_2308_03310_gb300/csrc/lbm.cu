@@ -266,12 +266,20 @@ __global__ void __launch_bounds__(NT, MINB) lbm_2step_kernel(const float *__rest
         for (int c = 0; c < 3; ++c)
             vy[c] = (unsigned)(ty0 + c - 1) < (unsigned)TY && y0 + ty0 + c - 1 < ny;
         const long long at = (long long)(y0 + ty0) * nx + (x0 + tx0);
+        // a pair's targets are 8-byte aligned where c_x = +-1 and nx is even (x0 + bx even):
+        // one float2 store where both are inside
+        const bool pair_ok = (nx & 1) == 0;
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
             float *d = dst + at + (long long)q * (long long)npts + cy(q) * nx + cx(q);
             if (vy[cy(q) + 1]) {
-                if (vx[cx(q) + 1]) __stcs(d, out[q].x);
-                if (vx[cx(q) + 2]) __stcs(d + 1, out[q].y);
+                const bool v0 = vx[cx(q) + 1], v1 = vx[cx(q) + 2];
+                if (cx(q) != 0 && pair_ok && v0 && v1) {
+                    __stcs(reinterpret_cast<float2 *>(d), out[q]);
+                } else {
+                    if (v0) __stcs(d, out[q].x);
+                    if (v1) __stcs(d + 1, out[q].y);
+                }
             }
         }
     }
