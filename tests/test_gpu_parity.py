@@ -291,6 +291,44 @@ def test_points_without_local_observations_are_unchanged():
     assert n_far == st.n_zero_obs
 
 
+@pytest.mark.parametrize("nx,ny,k", [
+    (36, 20, 12),   # 16-byte form: 720 points (a partial 64-point tile), a partial member tile
+    (40, 24, 36),   # 16-byte form: two member tiles, the second partial
+    (37, 29, 8),    # an odd number of points: the 4-byte form
+    (32, 32, 6),    # k not a multiple of 4: the 4-byte form
+])
+def test_transposes_move_every_value_exactly(nx, ny, k):
+    # one observation point seen by few grid points: the forecast block of every sampled point
+    # arrives in grid-point-major order bit for bit, and every point that sees no observation
+    # leaves the analysis (transposed back) bit for bit unchanged
+    net = np.array([[nx // 2, ny // 2]], dtype=np.int32)
+    f0 = C.ensemble_state(k, nx, ny, seed=57)
+    exp, _, _ = make(nx, ny, k, obs_xy=net, radius=1.0)
+    exp.set_state(f0)
+    g0 = exp.get_deviation()
+    rng = synth.generator(58)
+    pts = np.unique(np.concatenate([[0, nx * ny - 1, nx - 1, nx * (ny - 1)],
+                                    rng.integers(0, nx * ny, 60)]))
+    yo = np.array([0.01, -0.01], dtype=np.float32)
+    pr = exp.analyze_probe(yo, pts, want=("nloc", "xf"))
+    assert exp.sync() == 0
+    for i, p in enumerate(pts):
+        x, y = p % nx, p // nx
+        assert np.array_equal(pr["xf"][i], g0[:, :, y, x].T), (p, x, y)
+    exp.analyze(yo)
+    g1 = exp.get_deviation()
+    assert exp.sync() == 0
+    c2 = synth.loc_cutoff2(1.0)
+    n_far = 0
+    for y in range(ny):
+        for x in range(nx):
+            if len(oletkf.local_obs(x, y, net, nx, ny, c2)[0]) == 0:
+                assert np.array_equal(g1[:, :, y, x], g0[:, :, y, x]), (x, y)
+                n_far += 1
+    assert n_far == exp.stats().n_zero_obs > 0.9 * nx * ny
+    exp.close()
+
+
 def test_no_observations_at_all_is_identity():
     nx = ny = 16
     k = 8
