@@ -18,9 +18,10 @@
 // No factorization, eigenvalue or eigenvector is formed.
 //
 // kappa comes from the cheapest upper bounds of lambda_max(A): the least of the Gershgorin
-// bound, the Frobenius norm and the trace.  The degree grows like sqrt(kappa) (4 for kappa <=
-// 1.1, 10 for 2, 36 for 16); a point beyond the last approximation goes to the rational
-// schedule (tridiagonalization and Zolotarev's approximation) through a list.
+// bound, the Frobenius norm and the trace.  The degree grows like sqrt(kappa) (1 for kappa <=
+// 1.0002, 2 for 1.005, 3 for 1.035, 4 for 1.1, 10 for 2, 36 for 16); a point beyond the last
+// approximation goes to the rational schedule (tridiagonalization and Zolotarev's
+// approximation) through a list.
 //
 // Layout: one warp per grid point.  Lane l holds columns l and l + 32 of A in registers, loaded
 // from the upper triangle of the Gram slot (the rows above the diagonal coalesced, the lane's
@@ -91,8 +92,8 @@ const ChebTable &cheb_table() {
     static ChebTable t;
     static std::once_flag once;
     std::call_once(once, [] {
-        const double kmax[kChebSets] = {1.1, 1.2, 1.35, 1.5, 1.75, 2.0,
-                                        2.5, 3.0, 4.0,  6.0, 10.0, 16.0};
+        const double kmax[kChebSets] = {1.0002, 1.005, 1.035, 1.1, 1.2,  1.35, 1.5, 1.75,
+                                        2.0,    2.5,   3.0,   4.0, 6.0, 10.0, 16.0};
         for (int s = 0; s < kChebSets; ++s) {
             double ca[kChebMaxDeg + 1], cb[kChebMaxDeg + 1];
             int n = 1;

@@ -171,7 +171,7 @@ cudaError_t launch_eigen_rational(const EigArgs &a, const EigSplit &sp, int grid
 // (LETKF_EIG_CHEBYSHEV, k <= kChebMaxK): coefficients of T_j in s = (2t - kappa_max - 1) /
 // (kappa_max - 1), FP32 copies of the FP64 interpolants, the first set that covers a point's
 // condition bound is used.
-constexpr int kChebSets = 12;
+constexpr int kChebSets = 15;
 constexpr int kChebMaxDeg = 36;
 constexpr int kChebMaxK = 64;
 struct ChebTable {

@@ -176,7 +176,8 @@ def test_rational_coefficients_reject_bad_arguments(lib):
             L.letkf_rational_coefficients(kappa, n)
 
 
-@pytest.mark.parametrize("kappa,n,bound", [(1.1, 4, 2e-8), (2.0, 10, 2e-8), (16.0, 36, 2e-8),
+@pytest.mark.parametrize("kappa,n,bound", [(1.0002, 1, 1e-8), (1.005, 2, 2e-8), (1.035, 3, 2e-8),
+                                           (1.1, 4, 2e-8), (2.0, 10, 2e-8), (16.0, 36, 2e-8),
                                            (3.0, 6, 1e-3)])
 def test_chebyshev_coefficients_interpolate_rsqrt_and_inverse(lib, kappa, n, bound):
     # The Chebyshev schedule's coefficients (host code in the library): the degree-n

@@ -12,8 +12,8 @@ through a list.  Checked:
     48 x 16 domain, so that some points are transformed by the polynomials and others are passed on
     (both counted by letkf_get_work_counts), against the oracle at every grid point, k = 16
     and 48;
-  * the products counted match the degrees of the table: every point of a well-conditioned
-    case takes the smallest set;
+  * the products counted match the degrees of the table, point by point from the probed Gram
+    matrices (the condition bound of each point selects its set);
   * the cycle through the captured graph equals forecast + analysis on this schedule.
 """
 import numpy as np
@@ -112,9 +112,31 @@ def test_polynomial_and_passed_on_points_match_oracle(k):
     assert max(errs) < 1e-5, (errs, counts)
 
 
+# the approximations' kappa_max, in the order the transform tries them (chebyshev.cu)
+CHEB_KAPPA_MAX = (1.0002, 1.005, 1.035, 1.1, 1.2, 1.35, 1.5, 1.75, 2.0, 2.5, 3.0, 4.0, 6.0, 10.0,
+                  16.0)
+
+
+def _table_degree(kappa_max):
+    # the least degree whose interpolants reach 2e-8 on [1, kappa_max]
+    n = 1
+    while L.letkf_chebyshev_coefficients(kappa_max, n)[2] > 2e-8:
+        n += 1
+    return n
+
+
+def _degree_for(kappa, degrees):
+    for km, n in zip(CHEB_KAPPA_MAX, degrees):
+        if kappa <= km:
+            return n
+    return None
+
+
 def test_products_follow_the_degree_table():
-    # a tiny ensemble spread against sigma = 0.1: every observed point has kappa <= 1.1, the
-    # smallest set (degree 4, the least degree whose interpolants reach 2e-8 there)
+    # Every observed point's bound kappa = 1 + min(Gershgorin, Frobenius, trace)(A) / d picks the
+    # first approximation that covers it, and its degree is the number of products.  Checked
+    # point by point against the probed Gram matrices of the same analysis; a bound within the
+    # device's FP32 rounding margin of a set's edge may take either neighbour.
     nx = ny = 16
     k = 32
     f0 = C.perturb_nonequilibrium(C.ensemble_state(k, nx, ny, seed=191), 1e-5, 192)
@@ -123,15 +145,33 @@ def test_products_follow_the_degree_table():
     yo = C.observations(C.ensemble_state(1, nx, ny, seed=193), net, UV, 0.1, 194)[0]
     exp = L.Experiment(nx, ny, k, 0.6, net, var, loc_radius=3.0, eig_schedule=CHEB)
     exp.set_state(f0)
-    exp.analyze(yo)
+    pts = np.arange(nx * ny)
+    pr = exp.analyze_probe(yo, pts, want=("nloc", "gram"))
     assert exp.sync() == 0
     counts = exp.work_counts()
-    observed = nx * ny - exp.stats().n_zero_obs
     exp.close()
-    ca, cb, err = L.letkf_chebyshev_coefficients(1.1, 4)
-    assert err < 2e-8 and L.letkf_chebyshev_coefficients(1.1, 3)[2] > 2e-8
-    assert counts == {"cheb_points": observed, "cheb_products": 4 * observed,
-                      "cheb_handed_on": 0}
+    degrees = [_table_degree(km) for km in CHEB_KAPPA_MAX]
+    assert degrees[:4] == [1, 2, 3, 4]
+    d = float(k - 1)
+    lo = hi = observed = exact = 0
+    seen = set()
+    for i in range(pts.size):
+        if pr["nloc"][i] == 0:
+            continue
+        observed += 1
+        A = pr["gram"][i].astype(np.float64)
+        e = max(min(np.abs(A).sum(axis=1).max(), np.sqrt((A * A).sum()), np.trace(A)), 0.0)
+        n_lo = _degree_for(1.0 + (e / d) * (1.0 - 1e-4), degrees)
+        n_hi = _degree_for(1.0 + (e / d) * (1.0 + 1e-3) + 2e-6, degrees)
+        assert n_lo is not None and n_hi is not None
+        lo += n_lo
+        hi += n_hi
+        exact += n_lo == n_hi
+        seen.add(n_lo)
+    assert counts["cheb_points"] == observed and counts["cheb_handed_on"] == 0, counts
+    assert lo <= counts["cheb_products"] <= hi, (counts, lo, hi)
+    assert exact >= 0.9 * observed                # the check is point by point, not a range
+    assert min(seen) < 4                          # the sets below kappa 1.1 are in use
 
 
 def test_chebyshev_cycle_equals_forecast_then_analysis():
