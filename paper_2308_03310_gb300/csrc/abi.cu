@@ -218,6 +218,7 @@ struct letkf_handle {
     float *state[2] = {nullptr, nullptr};
     int cur = 0;
     float2 *force = nullptr;
+    lk::LbmTma lbm_tma;           // TMA descriptors of the two-step D2Q9 staging
     float *xg = nullptr, *rinv = nullptr, *yf = nullptr, *yb = nullptr, *ybar = nullptr,
           *yo = nullptr, *gram = nullptr, *cvec = nullptr, *eigval = nullptr;
     float4 *orec = nullptr;
@@ -336,7 +337,8 @@ int enqueue_forecast(letkf_handle *h, int nsteps) {
     if (rc) return rc;
     for (int s = 0; s + 2 <= nsteps; s += 2) {
         CK(lk::launch_lbm_2step(h->state[h->cur], h->state[h->cur ^ 1], h->force, h->cfg.nx,
-                                h->cfg.ny, p.nmem, h->cfg.tau, h->stream));
+                                h->cfg.ny, p.nmem, h->cfg.tau, h->stream, &h->lbm_tma,
+                                h->status));
         h->cur ^= 1;
     }
     if (nsteps & 1) {
@@ -1017,7 +1019,10 @@ int letkf_init(const letkf_config *cfg, void *workspace, size_t workspace_bytes,
     h->net.loc_gc = cfg->loc_kind == LETKF_LOC_GC;
     h->net.inv_c = plan.inv_c;
 
-    if (lk::lbm_prepare() != cudaSuccess || lk::gram_prepare(plan.kp) != cudaSuccess ||
+    if (lk::lbm_prepare() != cudaSuccess ||
+        lk::lbm_tma_build(h->state[0], h->state[1], h->force, cfg->nx, cfg->ny, plan.nmem,
+                          &h->lbm_tma) != cudaSuccess ||
+        lk::gram_prepare(plan.kp) != cudaSuccess ||
         lk::eigen_prepare(cfg->k, &h->eig_blocks) != cudaSuccess ||
         (plan.eig_schedule != LETKF_EIG_FUSED &&
          lk::eigen_split_prepare(cfg->k, &h->eig_split) != cudaSuccess) ||

@@ -35,8 +35,26 @@ cudaError_t launch_lbm_step(const float *gin, float *gout, const float2 *force, 
                             int nmem, float tau, cudaStream_t s);
 // two steps in one launch (temporal blocking through shared memory); lbm_prepare once
 cudaError_t lbm_prepare();
+// Tensor-memory-access (TMA) descriptors of the two-step launch's staging: an opaque image of
+// the driver's 128-byte tensor map, for each of the two state buffers and the force.
+struct alignas(64) TmaMap {
+    unsigned long long w[16];
+};
+struct LbmTma {
+    TmaMap g[2];
+    TmaMap f;
+    const float *gptr[2] = {nullptr, nullptr};
+    int ok = 0;                   // 1: state maps built, 2: force map built
+};
+// builds the maps where the grid allows them (nx a multiple of 4, at least one tile plus its
+// halo); leaves ok = 0 otherwise (the staging then uses cp.async throughout)
+cudaError_t lbm_tma_build(const float *g0, const float *g1, const float2 *force, int nx, int ny,
+                          int nmem, LbmTma *out);
+// with tma (nullable) the interior tiles stage through TMA; status receives ST_TIMEOUT if a
+// staging wait runs out
 cudaError_t launch_lbm_2step(const float *gin, float *gout, const float2 *force, int nx, int ny,
-                             int nmem, float tau, cudaStream_t s);
+                             int nmem, float tau, cudaStream_t s, const LbmTma *tma = nullptr,
+                             int *status = nullptr);
 cudaError_t launch_f_to_g(const float *f, float *g, int nmem, size_t npts, cudaStream_t s);
 cudaError_t launch_g_to_f(const float *g, float *f, int nmem, size_t npts, cudaStream_t s);
 cudaError_t launch_macro_to_g(const float *rho, const float *ux, const float *uy, float *g,

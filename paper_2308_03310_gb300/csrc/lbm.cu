@@ -18,6 +18,16 @@
 // once: ~84 bytes instead of 144.  The collision runs on pairs of neighbouring nodes with
 // packed FP32 arithmetic; it is the same function in both kernels, so the arithmetic is the
 // same as two single steps.
+//
+// Staging: where the window lies inside the grid (the tile is not at a periodic edge) and nx is
+// a multiple of 4, one thread loads it with two bulk tensor copies (TMA: the nine population
+// planes of the member as one 3-D box, the force as one 2-D box of interleaved components),
+// their completion counted in bytes on an mbarrier; elsewhere every thread issues 16-byte (or
+// 4-byte) cp.async copies with the periodic wrap.  Both put the same values in the same places.
+#include <cuda.h>   // CUtensorMap and the tensor-map encoder's types
+
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -150,6 +160,35 @@ constexpr size_t step2_smem() {          // staged tile (halo 2, x window widene
     return (size_t)(TX + 8) * (TY + 4) * (NV + 2) * sizeof(float);   // and its force
 }
 
+static_assert(sizeof(TmaMap) == sizeof(CUtensorMap) && alignof(TmaMap) >= 64, "tensor map image");
+
+constexpr unsigned long long kTmaWaitNs = 2000000000ull;   // bound of a staging wait (2 s)
+
+__device__ __forceinline__ unsigned long long lbm_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool tma_bar_try(uint32_t bar) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar)
+        : "memory");
+    return done != 0;
+}
+// bounded wait for the staging barrier's first phase
+__device__ __forceinline__ bool tma_bar_wait(uint32_t bar) {
+    if (tma_bar_try(bar)) return true;
+    const unsigned long long t0 = lbm_ns();
+    for (;;) {
+        if (tma_bar_try(bar)) return true;
+        if (lbm_ns() - t0 > kTmaWaitNs) return false;
+    }
+}
+
 // Periodic wrap of a coordinate at most one period outside [0, n).
 __device__ __forceinline__ int wrap1(int a, int n) {
     const int r = a < 0 ? a + n : (a >= n ? a - n : a);
@@ -169,7 +208,10 @@ template <bool kForce, int TX, int TY, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) lbm_2step_kernel(const float *__restrict__ gin,
                                                              float *__restrict__ gout,
                                                              const float2 *__restrict__ force,
-                                                             int nx, int ny, float omega_s) {
+                                                             int nx, int ny, float omega_s,
+                                                             const __grid_constant__ TmaMap tg,
+                                                             const __grid_constant__ TmaMap tf,
+                                                             int use_tma, int *status) {
     // staged step-t window: x in [x0 - 4, x0 + TX + 4), y in [y0 - 2, y0 + TY + 2); the nodes
     // two beyond the tile on each side are the halo, the outer two columns only align the
     // window's rows to 16 bytes
@@ -177,18 +219,55 @@ __global__ void __launch_bounds__(NT, MINB) lbm_2step_kernel(const float *__rest
     constexpr int BX = TX + 2, BY = TY + 2;      // step-(t+1) nodes, origin (x0 - 1, y0 - 1)
     constexpr int HX = TX + 4;                   // collided columns 2 .. AX - 3
     static_assert(TX % 4 == 0 && HX % 2 == 0 && BX % 2 == 0, "16-byte rows, node pairs");
-    extern __shared__ float sm[];
+    extern __shared__ __align__(128) float sm[];
+    __shared__ __align__(8) uint64_t tbar;
     float *A = sm;                                               // [q][AY][AX]
     float2 *Fs = reinterpret_cast<float2 *>(sm + NV * AX * AY);  // force over A's nodes
+    static_assert((NV * AX * AY * 4) % 128 == 0, "the force box starts 128-byte aligned");
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const size_t npts = (size_t)nx * ny;
     const size_t mbase = (size_t)blockIdx.z * NV * npts;
     const int tid = threadIdx.x;
     const float2 omega = dup2(omega_s);
-    // ---- stage the window with cp.async, every copy of the thread in flight before the one
-    // wait: runs of four nodes (16 bytes) where nx is a multiple of 4 -- x0 is, so every run
-    // starts on a 16-byte boundary, also where it wraps -- single nodes otherwise
-    if ((nx & 3) == 0) {
+    // ---- stage the window: a window inside the grid by TMA (the maps exist only where nx is a
+    // multiple of 4, so x0 - 4 is a 16-byte boundary); otherwise with cp.async, every copy of
+    // the thread in flight before the one wait: runs of four nodes (16 bytes) where nx is a
+    // multiple of 4 -- x0 is, so every run starts on a 16-byte boundary, also where it wraps --
+    // single nodes otherwise
+    const bool by_tma = use_tma && x0 >= 4 && x0 + TX + 4 <= nx && y0 >= 2 && y0 + TY + 2 <= ny;
+    if (by_tma) {
+        const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&tbar);
+        if (tid == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+            asm volatile("fence.mbarrier_init.release.cluster;");
+        }
+        __syncthreads();
+        if (tid == 0) {
+            constexpr uint32_t bytes = NV * AX * AY * 4 + (kForce ? AX * AY * 8 : 0);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                         "r"(bytes)
+                         : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"((uint32_t)__cvta_generic_to_shared(A)),
+                "l"(reinterpret_cast<uint64_t>(&tg)), "r"(x0 - 4), "r"(y0 - 2),
+                "r"((int)blockIdx.z * NV), "r"(bar)
+                : "memory");
+            if (kForce)
+                asm volatile(
+                    "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::"
+                    "bytes [%0], [%1, {%2, %3}], [%4];" ::"r"((uint32_t)__cvta_generic_to_shared(Fs)),
+                    "l"(reinterpret_cast<uint64_t>(&tf)), "r"(2 * (x0 - 4)), "r"(y0 - 2), "r"(bar)
+                    : "memory");
+        }
+        // the outcome made uniform over the CTA; a timeout is never expected: report it, give
+        // the copies a second bounded wait to land, leave
+        if (__syncthreads_and(tma_bar_wait(bar)) == 0) {
+            if (tid == 0 && status) atomicOr(status, ST_TIMEOUT);
+            tma_bar_wait(bar);
+            return;
+        }
+    } else if ((nx & 3) == 0) {
         constexpr int GX = AX / 4;
         for (int e = tid; e < AY * GX; e += NT) {
             const int ay = e / GX, gx = e - ay * GX;
@@ -298,16 +377,24 @@ cudaError_t set_step2_smem() {
 
 template <int TX, int TY, int NT, int MINB>
 cudaError_t launch_2step(const float *gin, float *gout, const float2 *force, int nx, int ny,
-                         int nmem, float tau, cudaStream_t s) {
+                         int nmem, float tau, cudaStream_t s, const LbmTma *tma, int *status) {
     dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY, nmem);
     const float omega = 1.0f / tau;
     const size_t smem = step2_smem<TX, TY>();
+    // the state map of the buffer read, and the force map where the force is staged
+    const int b = !tma || !(tma->ok & 1) ? -1 : gin == tma->gptr[0] ? 0 : gin == tma->gptr[1] ? 1 : -1;
+    const int use = b >= 0 && (!force || (tma->ok & 2));
+    static const TmaMap none = {};
+    const TmaMap &tg = use ? tma->g[b] : none;
+    const TmaMap &tf = use && force ? tma->f : none;
     if (force)
         lbm_2step_kernel<true, TX, TY, NT, MINB><<<grid, NT, smem, s>>>(gin, gout, force, nx,
-                                                                        ny, omega);
+                                                                        ny, omega, tg, tf, use,
+                                                                        status);
     else
         lbm_2step_kernel<false, TX, TY, NT, MINB><<<grid, NT, smem, s>>>(gin, gout, force, nx,
-                                                                         ny, omega);
+                                                                         ny, omega, tg, tf, use,
+                                                                         status);
     return cudaGetLastError();
 }
 
@@ -359,10 +446,67 @@ cudaError_t launch_lbm_step(const float *gin, float *gout, const float2 *force, 
 cudaError_t lbm_prepare() { return set_step2_smem<kTX, kTY, kStep2Threads, kStep2MinBlocks>(); }
 
 cudaError_t launch_lbm_2step(const float *gin, float *gout, const float2 *force, int nx, int ny,
-                             int nmem, float tau, cudaStream_t s) {
+                             int nmem, float tau, cudaStream_t s, const LbmTma *tma, int *status) {
     if (nmem <= 0) return cudaSuccess;
     return launch_2step<kTX, kTY, kStep2Threads, kStep2MinBlocks>(gin, gout, force, nx, ny, nmem,
-                                                                   tau, s);
+                                                                   tau, s, tma, status);
+}
+
+namespace {
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                 const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                 const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+// the driver's tensor-map encoder, through the runtime (no link against the driver library)
+EncodeTiled encode_tiled() {
+    static EncodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    });
+    return fn;
+}
+}  // namespace
+
+cudaError_t lbm_tma_build(const float *g0, const float *g1, const float2 *force, int nx, int ny,
+                          int nmem, LbmTma *out) {
+    out->ok = 0;
+    constexpr int AX = kTX + 8, AY = kTY + 4;
+    if ((nx & 3) != 0 || nx < AX || ny < AY || nmem <= 0) return cudaSuccess;   // cp.async only
+    const EncodeTiled enc = encode_tiled();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint32_t es[3] = {1, 1, 1};
+    // state [nmem * 9 planes][ny][nx] floats; box: one member's nine planes of the window
+    const cuuint64_t gdim[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nmem * NV};
+    const cuuint64_t gstr[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
+    const cuuint32_t gbox[3] = {AX, AY, NV};
+    for (int b = 0; b < 2; ++b)
+        if (enc(reinterpret_cast<CUtensorMap *>(&out->g[b]), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                const_cast<float *>(b ? g1 : g0), gdim, gstr, gbox, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    out->gptr[0] = g0;
+    out->gptr[1] = g1;
+    out->ok = 1;
+    if (force) {   // [ny][2 nx] floats (the components interleaved); box: the window's rows
+        const cuuint64_t fdim[2] = {(cuuint64_t)2 * nx, (cuuint64_t)ny};
+        const cuuint64_t fstr[1] = {(cuuint64_t)2 * nx * 4};
+        const cuuint32_t fbox[2] = {2 * AX, AY};
+        if (enc(reinterpret_cast<CUtensorMap *>(&out->f), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                const_cast<float2 *>(force), fdim, fstr, fbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+        out->ok |= 2;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_f_to_g(const float *f, float *g, int nmem, size_t npts, cudaStream_t s) {
