@@ -477,6 +477,7 @@ cudaError_t lbm_tma_build(const float *g0, const float *g1, const float2 *force,
                           int nmem, LbmTma *out) {
     out->ok = 0;
     constexpr int AX = kTX + 8, AY = kTY + 4;
+    static_assert(2 * AX <= 256 && AY <= 256 && NV <= 256, "a TMA box has at most 256 per side");
     if ((nx & 3) != 0 || nx < AX || ny < AY || nmem <= 0) return cudaSuccess;   // cp.async only
     const EncodeTiled enc = encode_tiled();
     if (!enc) return cudaErrorNotSupported;
