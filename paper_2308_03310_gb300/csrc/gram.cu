@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(PipeShape<KP>::NT, 1) gram_pipe_kernel(GramArg
     const int ty0 = a.y_begin + blockIdx.y * TH;
 
     const int nc = build_patch<NT>(net, a.nx, a.ny, tx0, ty0, TW, TH, cell_base, cell_pre,
-                                   warp_tot);
+                                   warp_tot, VV <= 2);
     const int total = cell_pre[nc];
     // chunk c holds the candidates c, c + nck, c + 2 nck, ... of the patch (a uniform sample)
     const int nck = (total + CH - 1) / CH;
@@ -398,6 +398,8 @@ __global__ void __launch_bounds__(PipeShape<KP>::NT, 1) gram_pipe_kernel(GramArg
             const float4 *rw = reinterpret_cast<const float4 *>(rows + __float_as_int(e.x) * KP);
             float4 A0 = rw[ti], A1 = rw[KB + ti], B0 = rw[tj], B1 = rw[KB + tj];
             float sw = e.y, sd = ED[0];
+            // kept rolled: unrolled by two the kernel took 128 registers and 19 % longer
+#pragma unroll 1
             for (int i = 0; i < n; ++i) {
                 float4 nA0 = A0, nA1 = A1, nB0 = B0, nB1 = B1;
                 float nsw = sw, nsd = sd;

@@ -1,5 +1,5 @@
 // The observation patch of a tile of grid points: every bin (cs x cs cell) that the
-// cutoff disk of any point of the tile touches, laid out as a prefix-summed list of bins so
+// cutoff disk of some point of the tile reaches, laid out as a prefix-summed list of bins so
 // that the j-th candidate observation of the patch is found by a binary search.  Shared by
 // the FP32 and the tensor-core Gram kernels; the candidate order (bins in patch order,
 // observations ascending within a bin) fixes the summation order.
@@ -74,12 +74,25 @@ __device__ __forceinline__ int axis_gap(int a0, int a1, int b0, int b1, int n) {
     return g;
 }
 
+// Whether bin (bx, by) lies beyond the cutoff from every point of the tile.  Kept out of line:
+// inlined into the pipelined FP32 Gram kernel it raised its register allocation to 128 and its
+// executed instructions by a quarter (measured), which cost more than the pruning saved.  The
+// caller opts in (prune): the pipelined kernel with at most two observed variables, where it
+// measured faster; with three the kernel still went to 128 registers, and the team kernel was
+// not measured with it.
+static __device__ __noinline__ bool bin_beyond(const ObsNet &net, int bx, int by, int tx0,
+                                               int ty0, int TW, int TH, int nx, int ny) {
+    const int gx = axis_gap(bx * net.cs, min((bx + 1) * net.cs, nx) - 1, tx0, tx0 + TW - 1, nx);
+    const int gy = axis_gap(by * net.cs, min((by + 1) * net.cs, ny) - 1, ty0, ty0 + TH - 1, ny);
+    return (long long)gx * gx + (long long)gy * gy > (long long)net.d2max;
+}
+
 // Bins of the patch of the tile [tx0, tx0+TW) x [ty0, ty0+TH): cell_base[c] is the bin's
 // first entry in net.cell_obs, cell_pre the exclusive prefix of the bin sizes.  Returns the
 // number of bins; cell_pre[nc] holds the number of candidate observations.
 template <int NT>
 __device__ int build_patch(const ObsNet &net, int nx, int ny, int tx0, int ty0, int TW, int TH,
-                           int *cell_base, int *cell_pre, int *warp_tot) {
+                           int *cell_base, int *cell_pre, int *warp_tot, bool prune = false) {
     BinRanges rx, ry;
     if (net.loc_none) {
         rx.n = ry.n = 1;
@@ -93,10 +106,15 @@ __device__ int build_patch(const ObsNet &net, int nx, int ny, int tx0, int ty0, 
     const int ncx_p = range_len(rx);
     const int nc = ncx_p * range_len(ry);  // <= kMaxPatchCells by construction of the bin size
     for (int c = threadIdx.x; c < nc; c += NT) {
-        const int cell = range_at(ry, c / ncx_p) * net.ncx + range_at(rx, c % ncx_p);
+        const int bx = range_at(rx, c % ncx_p), by = range_at(ry, c / ncx_p);
+        const int cell = by * net.ncx + bx;
         const int b0 = net.cell_start[cell];
+        // with prune, a bin of the bounding square beyond the cutoff from every point of the
+        // tile (its corners) keeps its place with no candidates: it holds no local observation
+        const bool beyond =
+            prune && !net.loc_none && bin_beyond(net, bx, by, tx0, ty0, TW, TH, nx, ny);
         cell_base[c] = b0;
-        cell_pre[c] = net.cell_start[cell + 1] - b0;
+        cell_pre[c] = beyond ? 0 : net.cell_start[cell + 1] - b0;
     }
     __syncthreads();
     block_exclusive_scan<NT>(cell_pre, nc, warp_tot);
