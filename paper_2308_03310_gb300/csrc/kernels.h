@@ -47,7 +47,8 @@ struct LbmTma {
     int ok = 0;                   // 1: state maps built, 2: force map built
 };
 // builds the maps where the grid allows them (nx a multiple of 4, at least one tile plus its
-// halo); leaves ok = 0 otherwise (the staging then uses cp.async throughout)
+// halo) and the driver offers the encoder; leaves ok = 0 otherwise (the staging then uses
+// cp.async throughout); an error if the encoder rejects a map
 cudaError_t lbm_tma_build(const float *g0, const float *g1, const float2 *force, int nx, int ny,
                           int nmem, LbmTma *out);
 // with tma (nullable) the interior tiles stage through TMA; status receives ST_TIMEOUT if a
