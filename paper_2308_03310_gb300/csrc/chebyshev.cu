@@ -138,7 +138,30 @@ struct ChebShape {
     static constexpr int BUF = kRowsC * KM;        // one row buffer [10][KM]
     static constexpr int off_xb = 3 * BUF;         // the rows' means [9]
     static constexpr int floats = off_xb + 16;
+    static constexpr int SP = KM + 4;               // row stride of the prefetched Gram slot
+    static constexpr int PF = KM * SP;              // its floats (after all warps' buffers)
+    static_assert((floats * 4 * kWarpsC) % 16 == 0 && (PF * 4) % 16 == 0, "16-byte rows");
 };
+
+constexpr unsigned long long kChebWaitNs = 2000000000ull;   // bound of a prefetch wait (2 s)
+
+__device__ __forceinline__ bool cheb_bar_wait(uint32_t bar, uint32_t parity) {
+    unsigned long long t0 = 0;
+    for (bool first = true;; first = false) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (first) t0 = t;
+        else if (t - t0 > kChebWaitNs) return false;
+    }
+}
 
 __device__ __forceinline__ float warp_max_c(float v) {
 #pragma unroll
@@ -152,6 +175,7 @@ __global__ void __launch_bounds__(32 * kWarpsC, KM == 64 ? 2 : 3)
     using S = ChebShape<KM>;
     constexpr int NS = S::NS, RP = S::RP, BUF = S::BUF;
     extern __shared__ float4 smem_c4[];
+    __shared__ __align__(8) uint64_t pbar[kWarpsC];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     float *ws = reinterpret_cast<float *>(smem_c4) + (size_t)wib * S::floats;
     float *R0 = ws, *xbs = ws + S::off_xb;
@@ -160,9 +184,85 @@ __global__ void __launch_bounds__(32 * kWarpsC, KM == 64 ? 2 : 3)
     const float sc = sqrtf((float)(k - 1)) / sqrtf(a.diag);   // sqrt(k-1) d^-1/2
     unsigned long long n_pts = 0, n_prod = 0, n_hand = 0;
     const long long nw = (long long)gridDim.x * kWarpsC;
-    for (long long lp = (long long)blockIdx.x * kWarpsC + wib; lp < a.npts; lp += nw) {
+    // Where the Gram slot's rows are 16-byte multiples (k a multiple of 4) the warp prefetches
+    // its next point's slot into shared memory (rows of k floats at stride SP, one bulk copy
+    // per row, counted in bytes on the warp's mbarrier) while it works on the current point.
+    const bool pf = (k & 3) == 0;
+    float *PS = reinterpret_cast<float *>(smem_c4) + (size_t)kWarpsC * S::floats +
+                (size_t)wib * S::PF;
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&pbar[wib]);
+    uint32_t phase = 0;
+    auto prefetch = [&](long long q) {
+        if (lane == 0)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                         "r"((uint32_t)(k * k * 4))
+                         : "memory");
+        __syncwarp();
+        const float *src = a.gram + (size_t)q * k * k;
+        for (int i = lane; i < k; i += 32)
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+                "[%3];" ::"r"((uint32_t)__cvta_generic_to_shared(PS + i * S::SP)),
+                "l"(src + (size_t)i * k), "r"((uint32_t)(k * 4)), "r"(bar)
+                : "memory");
+    };
+    long long lp = (long long)blockIdx.x * kWarpsC + wib;
+    if (pf) {
+        if (lane == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+            asm volatile("fence.mbarrier_init.release.cluster;");
+        }
+        __syncwarp();
+        if (lp < a.npts) prefetch(lp);
+    }
+    for (; lp < a.npts; lp += nw) {
         float *X = a.x + (size_t)(a.pt0 + lp) * NV * k;
-        if (a.nloc && a.nloc[lp] == 0) {
+        const bool zero = a.nloc && a.nloc[lp] == 0;
+        float A[NS][KM];
+        float dg = 0.0f;
+        if (pf) {
+            // this point's slot (bounded wait; a timeout is never expected: report it, give
+            // the copies a second bounded wait, leave)
+            if (!__all_sync(kAllC, cheb_bar_wait(bar, phase))) {
+                if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
+                cheb_bar_wait(bar, phase);
+                return;
+            }
+            phase ^= 1;
+            if (!zero) {
+                // A from the staged slot: lane c takes A[i][c] for i <= c down its column and
+                // A[c][i] = A[i][c] for i > c along its own row (16-byte reads; the padded
+                // stride keeps a quarter warp's rows in distinct banks)
+#pragma unroll
+                for (int q = 0; q < NS; ++q) {
+                    const int c = lane + 32 * q;
+#pragma unroll
+                    for (int i = 0; i < KM; ++i)
+                        A[q][i] = (i < k && c < k && i <= c) ? PS[i * S::SP + c] : 0.0f;
+                }
+#pragma unroll
+                for (int q = 0; q < NS; ++q) {
+                    const int c = lane + 32 * q;
+                    if (c >= k) continue;
+                    const float4 *row = reinterpret_cast<const float4 *>(PS + c * S::SP);
+#pragma unroll
+                    for (int g = 0; g < KM / 4; ++g)
+                        if (4 * g + 3 > c && 4 * g < k) {
+                            const float4 v = row[g];
+                            if (4 * g > c) A[q][4 * g] = v.x;
+                            if (4 * g + 1 > c) A[q][4 * g + 1] = v.y;
+                            if (4 * g + 2 > c) A[q][4 * g + 2] = v.z;
+                            A[q][4 * g + 3] = v.w;
+                        }
+                    dg += PS[c * S::SP + c];
+                }
+            }
+            // the slot's reads are done before the next point's copies overwrite it
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lp + nw < a.npts) prefetch(lp + nw);
+        }
+        if (zero) {
             // Q = (k-1)/rho I: wbar = 0 and dW = sqrt(rho) I (untouched for rho = 1)
             if (a.sqrt_infl != 1.0f)
                 for (int r = 0; r < NV; ++r) {
@@ -182,11 +282,12 @@ __global__ void __launch_bounds__(32 * kWarpsC, KM == 64 ? 2 : 3)
                 }
             continue;
         }
-        // ---- A, symmetric, from the upper triangle of the Gram slot straight into registers,
-        // every load of the point in flight at once: lane c takes A[i][c] for i <= c from the
-        // rows i (coalesced across the lanes) and A[c][i] = A[i][c] for i > c from its own row
+        // ---- A, symmetric, from the upper triangle of the Gram slot straight into registers
+        // (without the prefetch), every load of the point in flight at once: lane c takes
+        // A[i][c] for i <= c from the rows i (coalesced across the lanes) and A[c][i] = A[i][c]
+        // for i > c from its own row
         const float *Ag = a.gram + (size_t)lp * k * k;
-        float A[NS][KM];
+        if (!pf) {
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
             const int c = lane + 32 * q;
@@ -215,15 +316,19 @@ __global__ void __launch_bounds__(32 * kWarpsC, KM == 64 ? 2 : 3)
                     if (i > c && i < k) A[q][i] = __ldg(row + i);
             }
         }
-        // the forecast rows and c, loaded beside A and parked in R0 (each lane its columns)
-        float dg = 0.0f;
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            const int c = lane + 32 * q;
+            if (c < k) dg += __ldg(Ag + (size_t)c * k + c);
+        }
+        }
+        // the forecast rows and c, parked in R0 (each lane its columns)
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
             const int c = lane + 32 * q;
 #pragma unroll
             for (int r = 0; r < NV; ++r) R0[r * KM + c] = c < k ? __ldcg(X + r * k + c) : 0.0f;
             R0[NV * KM + c] = c < k ? __ldcg(a.cvec + (size_t)lp * k + c) : 0.0f;
-            if (c < k) dg += __ldg(Ag + (size_t)c * k + c);
         }
         // ---- kappa >= 1 + lambda_max(A) / d from min(Gershgorin, Frobenius, trace)
         float gm = 0.0f, f2 = 0.0f;
@@ -362,7 +467,7 @@ __global__ void __launch_bounds__(32 * kWarpsC, KM == 64 ? 2 : 3)
 template <int KM>
 cudaError_t cheb_prepare_km(int *grid) {
     using S = ChebShape<KM>;
-    const size_t smem = (size_t)S::floats * sizeof(float) * kWarpsC;
+    const size_t smem = ((size_t)S::floats + S::PF) * sizeof(float) * kWarpsC;
     cudaError_t e = cudaFuncSetAttribute(eig_cheb_kernel<KM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -385,8 +490,9 @@ cudaError_t cheb_launch_km(const EigArgs &a, const EigSplit &sp, int grid, cudaS
     const long long need = ((long long)a.npts + kWarpsC - 1) / kWarpsC;
     const unsigned blocks = (unsigned)(need < grid ? need : grid);
     const ChebTable &t = cheb_table();
-    eig_cheb_kernel<KM><<<blocks, 32 * kWarpsC, (size_t)S::floats * sizeof(float) * kWarpsC,
-                          s>>>(a, sp, t, cheb_max_set(a.k));
+    eig_cheb_kernel<KM><<<blocks, 32 * kWarpsC,
+                          ((size_t)S::floats + S::PF) * sizeof(float) * kWarpsC, s>>>(
+        a, sp, t, cheb_max_set(a.k));
     return cudaGetLastError();
 }
 
