@@ -95,11 +95,15 @@ const ChebTable &cheb_table() {
         const double kmax[kChebSets] = {1.0002, 1.005, 1.035, 1.1, 1.2,  1.35, 1.5, 1.75,
                                         2.0,    2.5,   3.0,   4.0, 6.0, 10.0, 16.0};
         for (int s = 0; s < kChebSets; ++s) {
+            // the interval the kernel maps onto [-1, 1] is the FP32 kappa_max: the coefficients
+            // and the degree are those of that interval
+            const float kf = (float)kmax[s];
+            const double km = (double)kf;
             double ca[kChebMaxDeg + 1], cb[kChebMaxDeg + 1];
             int n = 1;
-            while (n < kChebMaxDeg && chebyshev_coefficients(kmax[s], n, ca, cb) > 2e-8) ++n;
-            chebyshev_coefficients(kmax[s], n, ca, cb);
-            t.kappa_max[s] = (float)kmax[s];
+            while (n < kChebMaxDeg && chebyshev_coefficients(km, n, ca, cb) > 2e-8) ++n;
+            chebyshev_coefficients(km, n, ca, cb);
+            t.kappa_max[s] = kf;
             t.n[s] = n;
             for (int j = 0; j <= kChebMaxDeg; ++j)
                 t.c[s][j] = j <= n ? make_float2((float)ca[j], (float)cb[j])
